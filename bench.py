@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Throughput of the fused IB-LBM step (arXiv 2102.01305's method) on one GB300.
+
+Workload (default): the 3D clap-and-fling wing pair - D3Q19, FP32 storage,
+256 x 192 x 160 cells, two flat elliptic wings of chord 20 and span 100
+(2 x 1576 markers at unit spacing), Re = 100, J = 1e-2, flapping period
+4000 steps; every step is the whole hot path (kinematics, interpolation,
+implicit solve, spreading, collision + streaming + faces, force reduction).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (the runs share nothing, so there is no collective
+on the data path); rank 0 prints one JSON line with the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORLD = int(os.environ.get("WORLD_SIZE", "1"))
+RANK = int(os.environ.get("RANK", "0"))
+LOCAL_RANK = int(os.environ.get("LOCAL_RANK", "0"))
+if WORLD > 1 and "CUDA_VISIBLE_DEVICES" not in os.environ:
+    # one GPU per rank; libibl uses the current device of its own runtime (device 0)
+    os.environ["CUDA_VISIBLE_DEVICES"] = str(LOCAL_RANK)
+
+METRIC = "IB-LBM D3Q19 GLUPS & % HBM roofline; sweep-serving solves/h, p50/p99 latency"
+UNIT = "GLUPS"
+FALLBACK_HBM_GBS = 6800.0
+COLLIDE_SOURCES = ["paper_2102_01305_gb300/csrc/lbm.cu", "paper_2102_01305_gb300/csrc/lbm_gather.cuh",
+                   "paper_2102_01305_gb300/csrc/ibl_internal.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16dev", "bf16dev", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-worker", default=None)   # internal: run the oracle sample
+    return ap.parse_args()
+
+
+def workload(precision="fp32", scale=1.0):
+    import workloads as W
+    n = lambda v: max(8, int(round(v * scale)))
+    cfg = W.clap_fling_3d(nx=n(256), ny=n(192), nz=n(160), chord=max(4.0, round(20.0 * scale)),
+                          precision=precision)
+    return cfg
+
+
+def describe(cfg, steps):
+    g = cfg["grid"]
+    m = [len(b["ds"]) for b in cfg["bodies"]]
+    return {"workload": (f"3D clap-and-fling wing pair, D3Q19 {g['precision'].upper()}, "
+                         f"{g['nx']}x{g['ny']}x{g['nz']} cells, 2 elliptic wings c={cfg['bodies'][0]['hinge'][0]*2:g} "
+                         f"span 5c ({m[0]}+{m[1]} markers), Re=100, J=1e-2, period 4000 steps"),
+            "cells": g["nx"] * g["ny"] * g["nz"], "markers": sum(m), "tau": round(cfg["tau"], 6),
+            "steps_timed": steps,
+            "l2": "no flush: every step streams 2 x 597 MB of populations, > 129 MB L2"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]))],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- oracle legs
+def oracle_glups(scale: float, steps: int, warm: int = 0) -> dict:
+    """Time the FP64 oracle on a scaled copy of the workload (single thread)."""
+    import numpy as np
+    from oracle.sim import Simulation
+    cfg = workload("fp32", scale)
+    sim = Simulation(cfg["lattice"], cfg["grid"], cfg["tau"])
+    sim.init_fluid(u=np.asarray(cfg["u0"])[:3])
+    for b in cfg["bodies"]:
+        sim.add_body(b)
+    r = cfg["reference"]
+    sim.set_reference(r["U_ref"], r["L"], r["rho_ref"])
+    sim.step(warm)
+    t0 = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t0
+    g = cfg["grid"]
+    cells = g["nx"] * g["ny"] * g["nz"]
+    return {"value": cells * steps / dt / 1e9, "seconds": dt, "steps": steps, "cells": cells,
+            "markers": sum(len(b["ds"]) for b in cfg["bodies"]), "box": [g["nx"], g["ny"], g["nz"]]}
+
+
+def run_oracle_subprocess(scale: float, steps: int, warm: int = 0, timeout: float = 900) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", f"{scale},{steps},{warm}"]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=timeout)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# ----------------------------------------------------------------------------- our arm
+def traffic_record(collide_hash: str):
+    path = os.path.join(ROOT, "profiles", "collide_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    if rec.get("source_sha256") != collide_hash:
+        return None
+    return rec
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for p in COLLIDE_SOURCES:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2102_01305_gb300 import ibl
+
+    if WORLD > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
+                                init_method="env://")
+    torch.cuda.set_device(0)
+    cfg = workload(args.precision)
+    g = cfg["grid"]
+    cells = g["nx"] * g["ny"] * g["nz"]
+    q = 19
+    elem = {"fp32": 4, "fp16dev": 2, "bf16dev": 2, "fp64": 8}[args.precision]
+    bytes_per_cell = 2 * q * elem
+
+    ctx = ibl.from_workload(cfg)
+    ctx.ibl_step(args.warmup)
+    ctx.ibl_sync(allow=(ibl.IBL_ENOTCONV,))
+    stream = torch.cuda.ExternalStream(ctx.ibl_stream())
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ctx.ibl_profile(True)
+    l0 = ctx.ibl_launch_count()
+    clocks = ClockSampler()
+    clocks.start()
+    time.sleep(0.3)
+    if WORLD > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ctx.ibl_step(args.steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    if WORLD > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = ctx.ibl_launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    status = "ok"
+    try:
+        ctx.ibl_sync()
+    except ibl.IblError as e:
+        status = str(e)
+    collide_ms, ib_ms, nprof = ctx.ibl_profile_read()
+    iters, res, refreshes = ctx.ibl_solver_stats(allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
+    cl = ctx.ibl_forces(0, allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED)) if status == "ok" else None
+    ctx.close()
+
+    if WORLD > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = cells * args.steps * WORLD / (ms * 1e-3) / 1e9
+
+    # end to end: host buffers through the public API, copies inside the timed region
+    e2e = None
+    if RANK == 0 and args.e2e_steps > 0:
+        e2e = run_e2e(ibl, cfg, args.e2e_steps, cells)
+
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak = float(json.load(open(peaks_path))["hbm_gbs"])
+        peak_src = "measured"
+    else:
+        peak, peak_src = FALLBACK_HBM_GBS, "fallback"
+    per_launch_s = collide_ms / max(nprof, 1) * 1e-3
+    alg_bytes = bytes_per_cell * cells
+    achieved = alg_bytes / per_launch_s / 1e9
+    rec = traffic_record(source_hash()) if args.precision == "fp32" else None
+    roofline = {"bound": "hbm", "kernel": "k_collide (collide + stream + faces, D3Q19)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "traffic": rec["traffic_bytes_per_launch"] if rec else None,
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "collide_ms_per_step": round(collide_ms / max(nprof, 1), 5),
+                "ib_chain_ms_per_step": round(ib_ms / max(nprof, 1), 5),
+                "step_ms": round(ms / args.steps, 5),
+                "step_frac_of_roofline": round(alg_bytes / (ms / args.steps * 1e-3) / 1e9 / peak, 4)}
+
+    cpu = None
+    if RANK == 0 and WORLD == 1 and not args.no_cpu_baseline:
+        try:
+            r = run_oracle_subprocess(0.5, 6, 1)
+            cpu = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": (f"6 steps (after 1 untimed) of the workload 2x coarsened: "
+                              f"{r['box'][0]}x{r['box'][1]}x{r['box'][2]} cells, {r['markers']} markers, "
+                              f"{r['seconds']:.1f} s single-threaded numpy FP64; host {cpu_model()}")}
+        except Exception as e:  # the baseline is reported, never required
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
+
+    if RANK == 0:
+        line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": WORLD,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp32": "f32", "fp16dev": "f16 storage / f32 compute",
+                          "bf16dev": "bf16 storage / f32 compute", "fp64": "f64"}[args.precision],
+                "data": "synthetic (seeded workload generator; no dataset)",
+                "config": describe(cfg, args.steps) | {"parallelism": f"replicas x{WORLD}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "status": status,
+                "solver": {"pcg_iterations_last_step": iters, "rel_residual_last_step": res,
+                           "preconditioner_rebuilds": refreshes},
+                "C_L_last_step_body0": cl[0] if cl else None}
+        print(json.dumps(line), flush=True)
+    if WORLD > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(ibl, cfg, steps, cells):
+    """Same metric through the public API with host buffers: every step uploads
+    both wings' marker positions and wall velocities and reads back the forces."""
+    import numpy as np
+    pre = ibl.from_workload(cfg)
+    ms = [len(b["ds"]) for b in cfg["bodies"]]
+    states = []
+    for _ in range(steps):
+        pre.ibl_step(1)
+        states.append([pre.ibl_get_markers(b, ms[b], allow=(ibl.IBL_ENOTCONV,))[:2] for b in range(2)])
+    pre.close()
+    ctx = ibl.from_workload(cfg)
+    ctx.ibl_sync(allow=(ibl.IBL_ENOTCONV,))
+    t0 = time.perf_counter()
+    for k in range(steps):
+        for b in range(2):
+            X, U = states[k][b]
+            ctx.ibl_set_marker_state(b, X, U)
+        ctx.ibl_step(1)
+        for b in range(2):
+            ctx.ibl_forces(b, allow=(ibl.IBL_ENOTCONV,))
+    dt = time.perf_counter() - t0
+    ctx.close()
+    h2d = sum(2 * 3 * 8 * m for m in ms)
+    d2h = 2 * (3 * 8 + 4)
+    return {"value": round(cells * steps / dt / 1e9, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps,
+            "path": "ibl_set_marker_state (host X, U of both wings) -> ibl_step(1) -> ibl_forces x2"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    if WORLD > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://")
+        if RANK != 0:
+            dist.destroy_process_group()
+            return
+    # each step: one oracle step on a copy of the workload scaled so that the
+    # whole warm-up + timed run takes about two minutes of one host core
+    budget = 120.0
+    per_step = budget / max(1, args.steps + args.warmup)
+    cells_target = max(6000.0, min(1.0e6, per_step * 4.0e5))
+    scale = (cells_target / (256 * 192 * 160)) ** (1.0 / 3.0)
+    r = run_oracle_subprocess(scale, args.steps, args.warmup, timeout=3600)
+    cfg = workload("fp32")
+    line = {"impl": "reference", "metric": METRIC, "value": round(r["value"], 6), "unit": UNIT,
+            "n_gpus": WORLD, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(r["seconds"] / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(cfg, args.steps) | {"parallelism": "oracle, rank 0 only"},
+            "cpu_baseline": {"value": round(r["value"], 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": (f"each step one oracle step of the workload scaled to "
+                                        f"{r['box'][0]}x{r['box'][1]}x{r['box'][2]} cells "
+                                        f"({r['markers']} markers); single-threaded numpy FP64; "
+                                        f"host {cpu_model()}")},
+            "e2e": {"value": round(r["value"], 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if WORLD > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.cpu_baseline_worker:
+        scale, steps, warm = args.cpu_baseline_worker.split(",")
+        print(json.dumps(oracle_glups(float(scale), int(steps), int(warm))))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

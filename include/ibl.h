@@ -1,0 +1,245 @@
+/*
+ * ibl.h - C ABI of the GB300-native immersed-boundary lattice Boltzmann library.
+ *
+ * The library implements the per-time-step hot path of the implicit
+ * velocity-correction IB-LBM of Kumar, De and Das, "Investigation of flow
+ * field of clap & fling motion using immersed boundary coupled lattice
+ * Boltzmann method" (arXiv 2102.01305):
+ *
+ *   - BGK collision (Eq. 1) with the Guo forcing term (Eqs. 7-8), fused with
+ *     streaming and moment recovery (Eqs. 2, 9, 11), on D2Q9 (Sec. 2.1,
+ *     weights Eq. 5) or D3Q19;
+ *   - the implicit immersed-boundary exchange with Lagrangian markers
+ *     (Sec. 2.2): 4-point cosine delta (Eqs. 13-14), interpolation (Eq. 17),
+ *     the per-step system A X = B for the marker velocity corrections
+ *     (Eqs. 18-19), spreading (Eq. 15), velocity correction (Eq. 16) and
+ *     force density F = 2 rho du / dt (Eq. 26);
+ *   - prescribed rigid kinematics of the wings (Eqs. 20-23, Sec. 3.3);
+ *   - the body-force, lift/thrust/drag reduction (Sec. 3.7).
+ *
+ * Conventions shared by every call
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3.  Grid nodes sit at integer
+ *     coordinates 0..n-1 on each axis; cell index (z*ny + y)*nx + x.
+ *   - All pointer arguments are HOST pointers unless a call says otherwise.
+ *     Inputs are copied before the call returns; the caller keeps ownership.
+ *     Outputs go to caller-allocated buffers of the stated size.
+ *   - Every call returns an ibl_status and never aborts the process.  On
+ *     error the context keeps its previous state and ibl_last_error() gives
+ *     a one-line reason.  A context is not thread-safe; distinct contexts are
+ *     independent.  All device memory is owned by the context and released
+ *     by ibl_destroy.
+ *   - ibl_step is asynchronous with respect to the host: it enqueues work on
+ *     the context's CUDA stream and returns.  Calls that return data
+ *     (ibl_forces, ibl_get_*, ibl_mass) synchronise that stream first and
+ *     then report any error the enqueued steps raised (divergence, solver
+ *     non-convergence, a device wait that timed out).
+ */
+#ifndef IBL_H
+#define IBL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibl_ctx ibl_ctx;   /* opaque */
+
+typedef enum {
+  IBL_OK = 0,
+  IBL_EINVAL = 1,      /* invalid argument or configuration */
+  IBL_ENOMEM = 2,      /* device allocation failed */
+  IBL_ECUDA = 3,       /* CUDA runtime error (message in ibl_last_error) */
+  IBL_EDIVERGED = 4,   /* NaN/Inf or runaway density detected; sticky until destroy */
+  IBL_ENOTCONV = 5,    /* the implicit IB solve did not reach its tolerance */
+  IBL_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+  IBL_ESTATE = 7       /* call out of order (e.g. step before the fluid is initialised) */
+} ibl_status;
+
+/* Lattice: D2Q9 (Sec. 2.1, Eq. 5) or D3Q19 (textbook weights 1/3, 1/18, 1/36). */
+typedef enum { IBL_D2Q9 = 9, IBL_D3Q19 = 19 } ibl_lattice;
+
+/* Face conditions (Sec. 2.1 bounce-back walls; Sec. 3.1 Zou-He inlet / outlet). */
+typedef enum {
+  IBL_PERIODIC = 0,     /* must be set on both faces of an axis */
+  IBL_BOUNCEBACK = 1,   /* halfway bounce-back wall, at rest */
+  IBL_VEL_INLET = 2,    /* Zou-He, velocity u_in prescribed */
+  IBL_PRESS_OUTLET = 3  /* Zou-He, density rho_out prescribed, zero tangential velocity */
+} ibl_bc;
+
+/* Storage precision of the distributions.  FP64 computes in FP64; FP32
+ * stores f_i - w_i in FP32 and collides in FP32.  FP16DEV / BF16DEV store
+ * f_i - w_i in 16 bits and collide in FP32. */
+typedef enum { IBL_FP64 = 0, IBL_FP32 = 1, IBL_FP16DEV = 2, IBL_BF16DEV = 3 } ibl_precision;
+
+typedef struct {
+  int32_t nx, ny, nz;        /* nz = 1 for D2Q9 */
+  int32_t bc[6];             /* ibl_bc per face: -x, +x, -y, +y, -z, +z */
+  double u_in[3];            /* inlet velocity (IBL_VEL_INLET faces) */
+  double rho_out;            /* outlet density (IBL_PRESS_OUTLET faces) */
+  double body_force[3];      /* uniform body force G added to F everywhere */
+  int32_t precision;         /* ibl_precision */
+} ibl_grid;
+
+/* Prescribed wave form of a body's translation A(t) or rotation alpha(t).
+ * theta(t) = 2 pi f t + phi with f and phi given to ibl_set_kinematics:
+ *   IBL_WAVE_CONST    offset
+ *   IBL_WAVE_COS      offset + amp cos(theta)       Eq. 20 (amp = A0/2)
+ *   IBL_WAVE_SIN      offset + amp sin(theta)       Eq. 21, Eq. 23
+ *   IBL_WAVE_ABS_SIN  offset + amp |sin(theta)|     opening 0..amp (clap-and-fling reading)
+ *   IBL_WAVE_TABLE    table[n mod n_table] at step n; rate by central difference */
+typedef enum {
+  IBL_WAVE_CONST = 0, IBL_WAVE_COS = 1, IBL_WAVE_SIN = 2, IBL_WAVE_ABS_SIN = 3, IBL_WAVE_TABLE = 4
+} ibl_wave_kind;
+
+typedef struct {
+  int32_t kind;            /* ibl_wave_kind */
+  double amp, offset;
+  const double* table;     /* IBL_WAVE_TABLE only: n_table samples, copied */
+  int64_t n_table;
+} ibl_wave;
+
+/* Field selectors for ibl_get_field. */
+typedef enum {
+  IBL_FIELD_RHO = 0,   /* rho = sum_i f_i, N values */
+  IBL_FIELD_U = 1,     /* u = (sum_i c_i f_i + G/2)/rho, d x N values (component-major) */
+  IBL_FIELD_FORCE = 2  /* last step's IB force density 2 rho du (Eq. 26, without G), d x N */
+} ibl_field;
+
+/* ------------------------------------------------------------------ lifecycle */
+
+/* Create a context on the current CUDA device.  tau > 1/2 is the BGK
+ * relaxation time (Eq. 3: tau = 3 nu + 1/2).  Allocates both population
+ * buffers; the fluid starts uninitialised (see ibl_init_fluid).
+ * Errors: IBL_EINVAL (sizes <= 0, nz != 1 for D2Q9, unpaired periodic faces,
+ * a Zou-He face whose lateral axes are not periodic, tau <= 1/2, unknown
+ * precision), IBL_ENOMEM, IBL_ECUDA. */
+ibl_status ibl_create(const ibl_grid* grid, double tau, int32_t lattice, ibl_ctx** out);
+
+/* Release all device memory and the stream.  NULL is accepted. */
+ibl_status ibl_destroy(ibl_ctx* ctx);
+
+/* Set f_i = f_eq(rho, u) (Eq. 4) everywhere and reset the step counter.
+ * rho: N host doubles or NULL (rho = 1); u: d x N host doubles
+ * (component-major) or NULL (u = 0). */
+ibl_status ibl_init_fluid(ibl_ctx* ctx, const double* rho, const double* u);
+
+/* Set the populations directly: f is Q x N host doubles, direction-major in
+ * the order of ibl_lattice_velocities.  Resets the step counter. */
+ibl_status ibl_set_populations(ibl_ctx* ctx, const double* f);
+
+/* ------------------------------------------------------------------ bodies */
+
+/* Add a rigid body of m Lagrangian markers (Sec. 2.2, Fig. 1).
+ * X0: m x d body-frame coordinates (marker-major); ds: m element sizes
+ * (arc length in 2D, area in 3D, the ds_l of Eq. 15); hinge: rotation centre
+ * in the body frame; axis: rotation axis (normalised internally; in 2D use
+ * +/- z); origin: world position of the body-frame origin.  The world
+ * position is X = origin + hinge + R(axis, alpha)(X0 - hinge) + A e_s.
+ * Until ibl_set_kinematics is called the body is at rest (A = alpha = 0).
+ * *body_id receives 0, 1, ... in order of creation.
+ * Errors: IBL_EINVAL (m <= 0, ds <= 0, zero axis), IBL_ENOMEM. */
+ibl_status ibl_set_markers(ibl_ctx* ctx, int32_t m, const double* X0, const double* ds,
+                           const double hinge[3], const double axis[3],
+                           const double origin[3], int32_t* body_id);
+
+/* Prescribe a body's motion (Eqs. 20-23, Sec. 3.3): translation A(t) along
+ * the stroke direction e_s = (cos beta, sin beta, 0) and rotation alpha(t)
+ * about the hinge axis; phi is the body's phase and f its frequency in
+ * cycles per step.  The wall velocity U_B = A' e_s + alpha' axis x r
+ * includes the rotational velocity (Sec. 3.3).  J is the advance ratio
+ * J = U_inf / U_tip (Eq. 24); it is recorded for reporting only, the
+ * free stream itself is the grid's inlet velocity. */
+ibl_status ibl_set_kinematics(ibl_ctx* ctx, int32_t body_id, const ibl_wave* A,
+                              const ibl_wave* alpha, double beta, double phi, double f,
+                              double J);
+
+/* Override the kinematics for the NEXT step only: X and U are m x d host
+ * doubles (marker-major), positions and wall velocities at that step. */
+ibl_status ibl_set_marker_state(ibl_ctx* ctx, int32_t body_id, const double* X,
+                                const double* U);
+
+/* Lift direction of a body (unit vector, default +y); drag is along +x. */
+ibl_status ibl_set_lift_axis(ibl_ctx* ctx, int32_t body_id, const double e[3]);
+
+/* Reference values of the coefficients C = F / (rho_ref U_ref^2 L / 2):
+ * L is a length in 2D and an area in 3D (Sec. 3.6 uses rho C S U_tip^2 / 2). */
+ibl_status ibl_set_reference(ibl_ctx* ctx, double U_ref, double L_or_S, double rho_ref);
+
+/* ------------------------------------------------------------------ stepping */
+
+/* Advance n >= 0 time steps, each the whole hot path in the paper's order
+ * (Sec. 2.2): kinematics -> moments -> interpolation (Eq. 17) -> implicit
+ * solve (Eqs. 18-19) -> spreading and force density (Eqs. 15, 16, 26) ->
+ * collision with forcing (Eqs. 7-8) and streaming with the face conditions
+ * -> body-force reduction (Sec. 3.7).  Asynchronous; returns the first
+ * sticky error already known (e.g. IBL_EDIVERGED) or IBL_OK. */
+ibl_status ibl_step(ibl_ctx* ctx, int64_t n);
+
+/* Block until the enqueued steps finish; returns their first error. */
+ibl_status ibl_sync(ibl_ctx* ctx);
+
+/* Coefficients of the last completed step for one body (Sec. 3.7):
+ * C_D along +x, C_T = -C_D, C_L along the body's lift axis. */
+ibl_status ibl_forces(ibl_ctx* ctx, int32_t body_id, double* C_L, double* C_T, double* C_D);
+
+/* Up to max most recent (C_L, C_T, C_D) triples of a body, oldest first, into
+ * out3 (3*max doubles); *n receives how many were written.  The device keeps
+ * the last 65536 steps. */
+ibl_status ibl_force_history(ibl_ctx* ctx, int32_t body_id, int64_t max, double* out3,
+                             int64_t* n);
+
+/* Copy a macroscopic field of the current populations to the host
+ * (sizes in ibl_field). */
+ibl_status ibl_get_field(ibl_ctx* ctx, int32_t what, double* out);
+
+/* Copy the current (post-streaming) populations, Q x N doubles. */
+ibl_status ibl_get_populations(ibl_ctx* ctx, double* f);
+
+/* Marker state of the last completed step: X, U_B (wall velocity) and the
+ * force each marker exerts on the fluid, 2 rho_l du_B^l ds_l; each m x d,
+ * any pointer may be NULL. */
+ibl_status ibl_get_markers(ibl_ctx* ctx, int32_t body_id, double* X, double* U, double* F);
+
+/* Total mass sum_x rho(x) of the current populations, accumulated in FP64
+ * in a fixed order. */
+ibl_status ibl_mass(ibl_ctx* ctx, double* mass);
+
+/* ------------------------------------------------------------------ introspection */
+
+/* Velocity set of a lattice: c is Q x 3 int32 (marker of direction order used by
+ * every population array of this ABI), w is Q doubles; either may be NULL.
+ * Returns Q in *q. */
+ibl_status ibl_lattice_velocities(int32_t lattice, int32_t* q, int32_t* c, double* w);
+
+/* Solver statistics of the last completed step: PCG iterations and the final
+ * relative residual of the implicit IB system; preconditioner refresh count. */
+ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_residual,
+                            int64_t* refreshes);
+
+/* Enable (1) or disable (0) CUDA-event timing, on the context's stream, of
+ * the collide-stream kernel and of the IB chain (kinematics .. spreading and
+ * the force reduction) of every step enqueued while enabled.  Enabling
+ * resets the totals.  Adds events only; the launch sequence is unchanged. */
+ibl_status ibl_profile(ibl_ctx* ctx, int32_t enable);
+
+/* Totals since the last ibl_profile(ctx, 1): milliseconds in the
+ * collide-stream kernel, milliseconds in the IB chain, steps timed.
+ * Synchronises the stream. */
+ibl_status ibl_profile_read(ibl_ctx* ctx, double* collide_ms, double* ib_ms, int64_t* steps);
+
+/* Number of kernel launches the context has enqueued since creation. */
+ibl_status ibl_launch_count(const ibl_ctx* ctx, int64_t* n);
+
+/* The CUDA stream the context enqueues on (a cudaStream_t, as void*). */
+ibl_status ibl_stream(const ibl_ctx* ctx, void** stream);
+
+/* One-line description of the context's last error ("" if none).  With
+ * ctx == NULL, the last error of a failed ibl_create. */
+const char* ibl_last_error(const ibl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBL_H */

@@ -1,0 +1,269 @@
+// Internal definitions shared by the CUDA translation units of libibl.
+//
+// Data layout in HBM (one context):
+//   populations  two buffers f[2], each Q x N of the storage type, direction
+//                major (SoA), cell index (z*ny + y)*nx + x, x contiguous.  The
+//                stored value is the deviation g_i = f_i - w_i (rho_0 = 1),
+//                which keeps FP32 / FP16 / BF16 rounding relative to the small
+//                non-rest part of f.
+//   between steps the "current" buffer holds POST-COLLISION populations of
+//                the previous step; a step pulls them along -c_i (streaming,
+//                left side of Eq. 1), applies the face conditions, recovers
+//                the moments, collides (Eq. 7) and writes the next buffer at
+//                the same cell (pull scheme).  After ibl_init_fluid the buffer
+//                holds post-streaming populations; the first step then
+//                collides without pulling.
+//   IB band      grid tiles of TILE_X x TILE_Y x TILE_Z cells touched by a
+//                marker stencil get a slot; per slot the band moments
+//                (rho, u*) and the force density F, each TILE_CELLS wide.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ibl.h"
+
+namespace ibl {
+
+// ----------------------------------------------------------------- lattices
+// Direction order: 0 rest, then pairs (c, -c) so that opp(i) = i + 1 for odd i.
+template <int Q> struct Lat;
+
+template <> struct Lat<9> {
+  static constexpr int D = 2;
+  __host__ __device__ static constexpr int cx(int i) {
+    constexpr int v[9] = {0, 1, -1, 0, 0, 1, -1, 1, -1};
+    return v[i];
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    constexpr int v[9] = {0, 0, 0, 1, -1, 1, -1, -1, 1};
+    return v[i];
+  }
+  __host__ __device__ static constexpr int cz(int) { return 0; }
+  // Eq. 5: 4/9 rest, 1/9 axis, 1/36 diagonal
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+};
+
+template <> struct Lat<19> {
+  static constexpr int D = 3;
+  __host__ __device__ static constexpr int cx(int i) {
+    constexpr int v[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return v[i];
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    constexpr int v[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return v[i];
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    constexpr int v[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return v[i];
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+  }
+};
+
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// ----------------------------------------------------------------- storage types
+template <class T> struct Store;
+template <> struct Store<double> {
+  using R = double;
+  __device__ static double ld(double v) { return v; }
+  __device__ static double st(double v) { return v; }
+};
+template <> struct Store<float> {
+  using R = float;
+  __device__ static float ld(float v) { return v; }
+  __device__ static float st(float v) { return v; }
+};
+template <> struct Store<__half> {
+  using R = float;
+  __device__ static float ld(__half v) { return __half2float(v); }
+  __device__ static __half st(float v) { return __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+  using R = float;
+  __device__ static float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ static __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+};
+
+// ----------------------------------------------------------------- tiles of the IB band
+constexpr int TILE_X = 16;
+constexpr int TILE_Y = 4;
+constexpr int TILE_Z3 = 4;        // 3D tile depth; 2D tiles are 16 x 16 x 1
+constexpr int TILE_CELLS = 256;
+constexpr int TILE_MARKER_CAP = 512;   // markers whose stencil touches one tile
+constexpr int G_MAXNNZ = 192;          // nonzeros per row of the IB system
+constexpr int HIST_LEN = 65536;        // force history ring per body
+
+// status bits raised on the device
+constexpr int ST_DIVERGED = 1;
+constexpr int ST_NOTCONV = 2;
+constexpr int ST_TIMEOUT = 4;
+constexpr int ST_OVERFLOW = 8;     // a band / list / row capacity was exceeded
+
+struct TileGeom {
+  int tx, ty, tz;        // tile extents
+  int ntx, nty, ntz;     // tiles per axis
+  int n_tiles;
+};
+
+// Everything the fluid kernels need, passed by value.
+template <class R> struct FluidParams {
+  int nx, ny, nz;
+  long long N;
+  int bc[6];
+  R u_in[3];
+  R rho_out;
+  R G[3];
+  R omega;     // 1 / tau
+  R pref;      // 1 - 1/(2 tau), Guo prefactor (Eq. 8)
+  TileGeom tg;
+  const int* tile_slot;   // n_tiles, -1 where no band slot; nullptr without markers
+  const R* band_F;        // [slot][3][TILE_CELLS] IB force density (Eq. 26)
+  int* status;
+};
+
+// ----------------------------------------------------------------- bodies
+struct Wave {
+  int kind;
+  double amp, offset;
+  const double* table;   // device copy (TABLE only)
+  long long n_table;
+};
+
+struct BodyDev {
+  int offset, m;
+  double hinge[3], axis[3], origin[3];
+  double beta, phi, f;
+  Wave A, alpha;
+  int prescribed;        // 1: use the uploaded X/U for this step
+};
+
+struct Body {
+  int offset = 0, m = 0;
+  double hinge[3] = {0, 0, 0}, axis[3] = {0, 0, 1}, origin[3] = {0, 0, 0};
+  double beta = 0, phi = 0, f = 0, J = 0;
+  Wave A{0, 0, 0, nullptr, 0}, alpha{0, 0, 0, nullptr, 0};
+  double* tableA = nullptr;
+  double* tableAlpha = nullptr;
+  double lift[3] = {0, 1, 0};
+  bool prescribed = false;
+  int precond_offset = 0;   // offset of this body's dense preconditioner (floats)
+};
+
+}  // namespace ibl
+
+// ----------------------------------------------------------------- the context
+struct ibl_ctx {
+  int Q = 0, D = 0;
+  int nx = 0, ny = 0, nz = 0;
+  long long N = 0;
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  double u_in[3] = {0, 0, 0}, rho_out = 1.0, G[3] = {0, 0, 0};
+  int prec = IBL_FP32;
+  double tau = 1.0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t elem = 4;               // bytes per stored population
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;
+  bool initialised = false;
+  bool poststream = true;        // current buffer holds post-streaming populations
+  long long step = 0;
+  long long launches = 0;
+  int* d_status = nullptr;       // device status bits
+  int sticky = 0;                // host copy of status bits seen so far
+  std::string err;
+
+  // ---- IB state
+  std::vector<ibl::Body> bodies;
+  int m_total = 0;
+  ibl::TileGeom tg{};
+  bool ib_ready = false;         // device IB buffers sized for m_total
+  int cap_slots = 0;
+  double U_ref = 1.0, L_ref = 1.0, rho_ref = 1.0;
+  // device arrays (doubles unless noted)
+  double* d_X0 = nullptr;        // m x 3 body frame
+  double* d_ds = nullptr;        // m
+  int* d_body = nullptr;         // m body index
+  double* d_X = nullptr;         // m x 3 world positions of the step
+  double* d_U = nullptr;         // m x 3 wall velocities
+  double* d_Xp = nullptr;        // m x 3 prescribed positions (ibl_set_marker_state)
+  double* d_Up = nullptr;
+  ibl::BodyDev* d_bodies = nullptr;
+  int* d_tile_slot = nullptr;    // n_tiles
+  int* d_slot_tile = nullptr;    // cap_slots
+  int* d_band_count = nullptr;   // 1 int: used slots
+  int* d_tile_mcount = nullptr;  // cap_slots
+  int* d_tile_markers = nullptr; // cap_slots x TILE_MARKER_CAP
+  void* d_band_mom = nullptr;    // cap_slots x 4 x TILE_CELLS (real)
+  void* d_band_F = nullptr;      // cap_slots x 3 x TILE_CELLS (real)
+  int* d_base = nullptr;         // m x 3 stencil base nodes (unwrapped)
+  double* d_wts = nullptr;       // m x 3 x 4 delta weights per axis (FP64)
+  double* d_rho_l = nullptr;     // m interpolated density
+  double* d_B = nullptr;         // m x 3 right-hand side
+  double* d_w = nullptr;         // m x 3 solution (du_B * ds)
+  double* d_r = nullptr;         // m x 3
+  double* d_p = nullptr;         // 2 x m x 3 (ping-pong)
+  double* d_Ap = nullptr;        // m x 3
+  double* d_z = nullptr;         // m x 3
+  int* d_Gcol = nullptr;         // m x G_MAXNNZ
+  double* d_Gval = nullptr;      // m x G_MAXNNZ
+  int* d_Gnnz = nullptr;         // m
+  double* d_Gdiag_max = nullptr; // per body, for the shift
+  float* d_M = nullptr;          // sum_b m_b^2 dense preconditioners
+  size_t M_floats = 0;
+  double* d_red = nullptr;       // reduction scratch
+  int* d_cg_info = nullptr;      // [iterations, refresh request]
+  double* d_cg_res = nullptr;    // final relative residual
+  double* d_hist = nullptr;      // bodies x HIST_LEN x 3 force vectors
+  double* d_mforce = nullptr;    // m x 3 marker forces 2 rho_l w
+  int* d_boff = nullptr;         // bodies + 1 marker offsets
+  long long refreshes = 0;
+  long long last_refresh_step = -1000000;
+  bool precond_valid = false;
+  bool warm = false;             // d_w holds the previous solution
+  // optional per-step event timing (ibl_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;   // 4 events per step: ib0, collide0, collide1, ib1
+  long long prof_steps = 0;
+  // host copies of the bodies' marker sets (uploaded when the IB buffers are sized)
+  std::vector<double> h_X0;      // m x 3
+  std::vector<double> h_ds;      // m
+  // pinned staging ring for ibl_set_marker_state
+  double* h_stage = nullptr;
+  cudaEvent_t stage_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int stage_next = 0;
+  size_t stage_doubles = 0;
+};
+
+namespace ibl {
+
+// error helpers (api.cu)
+ibl_status fail(ibl_ctx* c, ibl_status s, const std::string& msg);
+ibl_status cuda_check(ibl_ctx* c, cudaError_t e, const char* what);
+
+// fluid launches (lbm.cu)
+cudaError_t launch_init_eq(ibl_ctx* c, const double* d_rho, const double* d_u);
+cudaError_t launch_set_pop(ibl_ctx* c, const double* d_f);
+cudaError_t launch_collide(ibl_ctx* c, bool with_ib);
+cudaError_t launch_fields(ibl_ctx* c, double* d_rho, double* d_u, double* d_pop);
+cudaError_t launch_mass(ibl_ctx* c, double* d_partials, int nparts, double* d_out);
+
+// IB launches (ib.cu)
+cudaError_t ib_alloc(ibl_ctx* c);
+void ib_free(ibl_ctx* c);
+cudaError_t ib_step(ibl_ctx* c);          // kinematics .. spreading, before the collision
+cudaError_t ib_after_collide(ibl_ctx* c); // force reduction
+cudaError_t launch_force_field(ibl_ctx* c, double* d_out);
+
+}  // namespace ibl

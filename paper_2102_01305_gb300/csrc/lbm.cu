@@ -1,0 +1,297 @@
+// Fluid kernels: fused streaming + face conditions + moments + BGK/Guo collision.
+//
+// One thread per cell, x fastest across a warp so that every population read
+// and write is a coalesced 128-byte row segment (the +/-1 x-shifted pulls
+// straddle one extra segment that the neighbouring warp also touches; L1/L2
+// absorb it).  Per cell the kernel moves exactly Q loads and Q stores of the
+// storage type: the bytes-per-cell roofline of a streaming stencil.
+//
+// Paper passages: Eq. 1 (BGK + streaming), Eq. 4 (equilibrium), Eqs. 7-8
+// (Guo forcing), Eq. 9 (rho u = sum c_i f_i + F/2), Sec. 2.1 bounce-back,
+// Sec. 3.1 Zou-He inlet / outlet.
+#include "ibl_internal.cuh"
+#include "lbm_gather.cuh"
+
+namespace ibl {
+
+// IB force density of a cell from the band buffers (Eq. 26), zero elsewhere.
+template <class R>
+__device__ __forceinline__ void band_force(int x, int y, int z, const FluidParams<R>& p, R F[3]) {
+  const TileGeom& t = p.tg;
+  const int tile = ((z / t.tz) * t.nty + (y / t.ty)) * t.ntx + (x / t.tx);
+  const int slot = p.tile_slot[tile];
+  if (slot >= 0) {
+    const int local = ((z % t.tz) * t.ty + (y % t.ty)) * t.tx + (x % t.tx);
+    const R* b = p.band_F + (long long)slot * 3 * TILE_CELLS + local;
+    F[0] += b[0];
+    F[1] += b[TILE_CELLS];
+    F[2] += b[2 * TILE_CELLS];
+  }
+}
+
+// BGK collision with the Guo source in deviation form; returns rho.
+template <int Q, class R>
+__device__ __forceinline__ R collide(R g[Q], const R F[3], const FluidParams<R>& p) {
+  R drho = R(0), m0 = R(0), m1 = R(0), m2 = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    drho += g[i];
+    if (Lat<Q>::cx(i)) m0 += R(Lat<Q>::cx(i)) * g[i];
+    if (Lat<Q>::cy(i)) m1 += R(Lat<Q>::cy(i)) * g[i];
+    if (Lat<Q>::cz(i)) m2 += R(Lat<Q>::cz(i)) * g[i];
+  }
+  const R rho = R(1) + drho;
+  const R inv = R(1) / rho;
+  const R u0 = (m0 + R(0.5) * F[0]) * inv;      // Eq. 9
+  const R u1 = (m1 + R(0.5) * F[1]) * inv;
+  const R u2 = (m2 + R(0.5) * F[2]) * inv;
+  const R usq = u0 * u0 + u1 * u1 + u2 * u2;
+  const R uF = u0 * F[0] + u1 * F[1] + u2 * F[2];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R cu = R(Lat<Q>::cx(i)) * u0 + R(Lat<Q>::cy(i)) * u1 + R(Lat<Q>::cz(i)) * u2;
+    const R cF = R(Lat<Q>::cx(i)) * F[0] + R(Lat<Q>::cy(i)) * F[1] + R(Lat<Q>::cz(i)) * F[2];
+    const R w = R(Lat<Q>::w(i));
+    // f_eq - w_i  (Eq. 4, second-order expansion)
+    const R geq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq));
+    // Guo term (Eq. 8)
+    const R S = p.pref * w * (R(3) * (cF - uF) + R(9) * cu * cF);
+    g[i] = g[i] - p.omega * (g[i] - geq) + S;
+  }
+  return rho;
+}
+
+template <int Q, class T, bool PULL, bool IB>
+__global__ void __launch_bounds__(256) k_collide(const T* __restrict__ src, T* __restrict__ dst,
+                                                 FluidParams<typename Store<T>::R> p) {
+  using R = typename Store<T>::R;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= p.nx || y >= p.ny) return;
+  const long long cell = ((long long)z * p.ny + y) * p.nx + x;
+  R g[Q];
+  gather_q<Q, T, PULL, R>(src, x, y, z, cell, p, g);
+  R F[3] = {p.G[0], p.G[1], p.G[2]};
+  if (IB) band_force<R>(x, y, z, p, F);
+  const R rho = collide<Q, R>(g, F, p);
+  if (!(rho > R(0) && rho < R(100))) atomicOr(p.status, ST_DIVERGED);
+  const long long N = p.N;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) dst[i * N + cell] = Store<T>::st(g[i]);
+}
+
+// rho, u = (sum c_i f_i + G/2)/rho and optionally f itself (FP64) of the
+// current post-streaming populations.
+template <int Q, class T, bool PULL>
+__global__ void k_fields(const T* __restrict__ src, FluidParams<typename Store<T>::R> p,
+                         double* __restrict__ rho_out, double* __restrict__ u_out,
+                         double* __restrict__ pop_out) {
+  using R = typename Store<T>::R;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= p.nx || y >= p.ny) return;
+  const long long cell = ((long long)z * p.ny + y) * p.nx + x;
+  R g[Q];
+  gather_q<Q, T, PULL, R>(src, x, y, z, cell, p, g);
+  double drho = 0, m[3] = {0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double gi = (double)g[i];
+    drho += gi;
+    m[0] += Lat<Q>::cx(i) * gi;
+    m[1] += Lat<Q>::cy(i) * gi;
+    m[2] += Lat<Q>::cz(i) * gi;
+    if (pop_out) pop_out[i * p.N + cell] = gi + Lat<Q>::w(i);
+  }
+  const double rho = 1.0 + drho;
+  if (rho_out) rho_out[cell] = rho;
+  if (u_out)
+    for (int a = 0; a < Lat<Q>::D; ++a)
+      u_out[a * p.N + cell] = (m[a] + 0.5 * (double)p.G[a]) / rho;
+}
+
+template <int Q, class T>
+__global__ void k_init_eq(T* __restrict__ dst, long long N, const double* __restrict__ rho_in,
+                          const double* __restrict__ u_in) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= N) return;
+  const double rho = rho_in ? rho_in[cell] : 1.0;
+  double u[3] = {0, 0, 0};
+  if (u_in)
+    for (int a = 0; a < Lat<Q>::D; ++a) u[a] = u_in[a * N + cell];
+  const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const double cu = Lat<Q>::cx(i) * u[0] + Lat<Q>::cy(i) * u[1] + Lat<Q>::cz(i) * u[2];
+    const double w = Lat<Q>::w(i);
+    // f_eq - w, Eq. 4
+    const double geq = w * ((rho - 1.0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+    dst[i * N + cell] = Store<T>::st((typename Store<T>::R)geq);
+  }
+}
+
+template <int Q, class T>
+__global__ void k_set_pop(T* __restrict__ dst, long long N, const double* __restrict__ f) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= N) return;
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    dst[i * N + cell] = Store<T>::st((typename Store<T>::R)(f[i * N + cell] - Lat<Q>::w(i)));
+}
+
+// Fixed-order FP64 mass: block b sums cells [b*chunk, (b+1)*chunk) in a fixed
+// strided pattern and a fixed tree; the host-side second pass is a fixed loop.
+template <int Q, class T, bool PULL>
+__global__ void k_mass(const T* __restrict__ src, FluidParams<typename Store<T>::R> p,
+                       double* __restrict__ partials, long long chunk) {
+  using R = typename Store<T>::R;
+  __shared__ double sh[256];
+  const long long start = (long long)blockIdx.x * chunk;
+  long long end = start + chunk;
+  if (end > p.N) end = p.N;
+  double acc = 0;
+  for (long long cell = start + threadIdx.x; cell < end; cell += blockDim.x) {
+    const int x = (int)(cell % p.nx);
+    const long long yz = cell / p.nx;
+    const int y = (int)(yz % p.ny);
+    const int z = (int)(yz / p.ny);
+    R g[Q];
+    gather_q<Q, T, PULL, R>(src, x, y, z, cell, p, g);
+    double drho = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) drho += (double)g[i];
+    acc += 1.0 + drho;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+// ----------------------------------------------------------------- host side
+template <class R>
+FluidParams<R> make_params(ibl_ctx* c, bool with_ib) {
+  FluidParams<R> p;
+  p.nx = c->nx; p.ny = c->ny; p.nz = c->nz; p.N = c->N;
+  for (int i = 0; i < 6; ++i) p.bc[i] = c->bc[i];
+  for (int a = 0; a < 3; ++a) {
+    p.u_in[a] = (R)c->u_in[a];
+    p.G[a] = (R)c->G[a];
+  }
+  p.rho_out = (R)c->rho_out;
+  p.omega = (R)(1.0 / c->tau);
+  p.pref = (R)(1.0 - 0.5 / c->tau);
+  p.tg = c->tg;
+  p.tile_slot = with_ib ? c->d_tile_slot : nullptr;
+  p.band_F = with_ib ? (const R*)c->d_band_F : nullptr;
+  p.status = c->d_status;
+  return p;
+}
+
+static dim3 cell_block(ibl_ctx* c) {
+  (void)c;
+  return dim3(64, 4, 1);
+}
+static dim3 cell_grid(ibl_ctx* c, dim3 b) {
+  return dim3((c->nx + b.x - 1) / b.x, (c->ny + b.y - 1) / b.y, c->nz);
+}
+
+template <int Q, class T>
+cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
+  using R = typename Store<T>::R;
+  auto p = make_params<R>(c, with_ib);
+  const T* src = (const T*)c->f[c->cur];
+  T* dst = (T*)c->f[c->cur ^ 1];
+  dim3 b = cell_block(c), g = cell_grid(c, b);
+  if (c->poststream) {
+    if (with_ib) k_collide<Q, T, false, true><<<g, b, 0, c->stream>>>(src, dst, p);
+    else k_collide<Q, T, false, false><<<g, b, 0, c->stream>>>(src, dst, p);
+  } else {
+    if (with_ib) k_collide<Q, T, true, true><<<g, b, 0, c->stream>>>(src, dst, p);
+    else k_collide<Q, T, true, false><<<g, b, 0, c->stream>>>(src, dst, p);
+  }
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int Q, class T>
+cudaError_t fields_q(ibl_ctx* c, double* d_rho, double* d_u, double* d_pop) {
+  using R = typename Store<T>::R;
+  auto p = make_params<R>(c, false);
+  const T* src = (const T*)c->f[c->cur];
+  dim3 b = cell_block(c), g = cell_grid(c, b);
+  if (c->poststream) k_fields<Q, T, false><<<g, b, 0, c->stream>>>(src, p, d_rho, d_u, d_pop);
+  else k_fields<Q, T, true><<<g, b, 0, c->stream>>>(src, p, d_rho, d_u, d_pop);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int Q, class T>
+cudaError_t mass_q(ibl_ctx* c, double* d_partials, int nparts) {
+  using R = typename Store<T>::R;
+  auto p = make_params<R>(c, false);
+  const T* src = (const T*)c->f[c->cur];
+  long long chunk = (c->N + nparts - 1) / nparts;
+  if (c->poststream) k_mass<Q, T, false><<<nparts, 256, 0, c->stream>>>(src, p, d_partials, chunk);
+  else k_mass<Q, T, true><<<nparts, 256, 0, c->stream>>>(src, p, d_partials, chunk);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int Q, class T>
+cudaError_t init_q(ibl_ctx* c, const double* d_rho, const double* d_u) {
+  const int bs = 256;
+  const long long nb = (c->N + bs - 1) / bs;
+  k_init_eq<Q, T><<<(unsigned)nb, bs, 0, c->stream>>>((T*)c->f[c->cur], c->N, d_rho, d_u);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int Q, class T>
+cudaError_t setpop_q(ibl_ctx* c, const double* d_f) {
+  const int bs = 256;
+  const long long nb = (c->N + bs - 1) / bs;
+  k_set_pop<Q, T><<<(unsigned)nb, bs, 0, c->stream>>>((T*)c->f[c->cur], c->N, d_f);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+// Dispatch on (lattice, storage precision).
+#define IBL_DISPATCH(FN, ...)                                                       \
+  do {                                                                              \
+    if (c->Q == 9) {                                                                \
+      switch (c->prec) {                                                            \
+        case IBL_FP64: return FN<9, double>(c, ##__VA_ARGS__);                      \
+        case IBL_FP32: return FN<9, float>(c, ##__VA_ARGS__);                       \
+        case IBL_FP16DEV: return FN<9, __half>(c, ##__VA_ARGS__);                  \
+        default: return FN<9, __nv_bfloat16>(c, ##__VA_ARGS__);                     \
+      }                                                                             \
+    } else {                                                                        \
+      switch (c->prec) {                                                            \
+        case IBL_FP64: return FN<19, double>(c, ##__VA_ARGS__);                     \
+        case IBL_FP32: return FN<19, float>(c, ##__VA_ARGS__);                      \
+        case IBL_FP16DEV: return FN<19, __half>(c, ##__VA_ARGS__);                  \
+        default: return FN<19, __nv_bfloat16>(c, ##__VA_ARGS__);                    \
+      }                                                                             \
+    }                                                                               \
+  } while (0)
+
+cudaError_t launch_collide(ibl_ctx* c, bool with_ib) { IBL_DISPATCH(collide_q, with_ib); }
+cudaError_t launch_fields(ibl_ctx* c, double* d_rho, double* d_u, double* d_pop) {
+  IBL_DISPATCH(fields_q, d_rho, d_u, d_pop);
+}
+cudaError_t launch_mass(ibl_ctx* c, double* d_partials, int nparts, double* d_out) {
+  (void)d_out;
+  IBL_DISPATCH(mass_q, d_partials, nparts);
+}
+cudaError_t launch_init_eq(ibl_ctx* c, const double* d_rho, const double* d_u) {
+  IBL_DISPATCH(init_q, d_rho, d_u);
+}
+cudaError_t launch_set_pop(ibl_ctx* c, const double* d_f) { IBL_DISPATCH(setpop_q, d_f); }
+
+}  // namespace ibl

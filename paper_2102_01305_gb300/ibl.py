@@ -1,0 +1,315 @@
+"""Thin ctypes binding of libibl (the C ABI in include/ibl.h), same names.
+
+Only argument marshalling happens here: numpy arrays are passed as host
+pointers and every step of the IB-LBM path runs in the library's CUDA
+kernels.  There is no fallback: if ``libibl.so`` is missing or fails to load,
+importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libibl.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2102_01305_gb300.build.build() "
+                      "(nvcc, sm_103a); there is no CPU fallback")
+_lib = C.CDLL(LIB_PATH)
+
+# ------------------------------------------------------------------ enums (ibl.h)
+IBL_OK, IBL_EINVAL, IBL_ENOMEM, IBL_ECUDA, IBL_EDIVERGED, IBL_ENOTCONV, IBL_ETIMEOUT, IBL_ESTATE = range(8)
+IBL_D2Q9, IBL_D3Q19 = 9, 19
+IBL_PERIODIC, IBL_BOUNCEBACK, IBL_VEL_INLET, IBL_PRESS_OUTLET = range(4)
+IBL_FP64, IBL_FP32, IBL_FP16DEV, IBL_BF16DEV = range(4)
+IBL_WAVE_CONST, IBL_WAVE_COS, IBL_WAVE_SIN, IBL_WAVE_ABS_SIN, IBL_WAVE_TABLE = range(5)
+IBL_FIELD_RHO, IBL_FIELD_U, IBL_FIELD_FORCE = range(3)
+STATUS_NAMES = ["IBL_OK", "IBL_EINVAL", "IBL_ENOMEM", "IBL_ECUDA", "IBL_EDIVERGED",
+                "IBL_ENOTCONV", "IBL_ETIMEOUT", "IBL_ESTATE"]
+PRECISIONS = {"fp64": IBL_FP64, "fp32": IBL_FP32, "fp16dev": IBL_FP16DEV, "bf16dev": IBL_BF16DEV}
+
+
+class ibl_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("bc", C.c_int32 * 6), ("u_in", C.c_double * 3), ("rho_out", C.c_double),
+                ("body_force", C.c_double * 3), ("precision", C.c_int32)]
+
+
+class ibl_wave(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("amp", C.c_double), ("offset", C.c_double),
+                ("table", C.POINTER(C.c_double)), ("n_table", C.c_int64)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+
+_SIGS = {
+    "ibl_create": ([C.POINTER(ibl_grid), C.c_double, C.c_int32, C.POINTER(_P)], C.c_int),
+    "ibl_destroy": ([_P], C.c_int),
+    "ibl_init_fluid": ([_P, _D, _D], C.c_int),
+    "ibl_set_populations": ([_P, _D], C.c_int),
+    "ibl_set_markers": ([_P, C.c_int32, _D, _D, _D, _D, _D, _I32], C.c_int),
+    "ibl_set_kinematics": ([_P, C.c_int32, C.POINTER(ibl_wave), C.POINTER(ibl_wave), C.c_double,
+                            C.c_double, C.c_double, C.c_double], C.c_int),
+    "ibl_set_marker_state": ([_P, C.c_int32, _D, _D], C.c_int),
+    "ibl_set_lift_axis": ([_P, C.c_int32, _D], C.c_int),
+    "ibl_set_reference": ([_P, C.c_double, C.c_double, C.c_double], C.c_int),
+    "ibl_step": ([_P, C.c_int64], C.c_int),
+    "ibl_sync": ([_P], C.c_int),
+    "ibl_forces": ([_P, C.c_int32, _D, _D, _D], C.c_int),
+    "ibl_force_history": ([_P, C.c_int32, C.c_int64, _D, _I64], C.c_int),
+    "ibl_get_field": ([_P, C.c_int32, _D], C.c_int),
+    "ibl_get_populations": ([_P, _D], C.c_int),
+    "ibl_get_markers": ([_P, C.c_int32, _D, _D, _D], C.c_int),
+    "ibl_mass": ([_P, _D], C.c_int),
+    "ibl_lattice_velocities": ([C.c_int32, _I32, _I32, _D], C.c_int),
+    "ibl_solver_stats": ([_P, _I32, _D, _I64], C.c_int),
+    "ibl_profile": ([_P, C.c_int32], C.c_int),
+    "ibl_profile_read": ([_P, _D, _D, _I64], C.c_int),
+    "ibl_launch_count": ([_P, _I64], C.c_int),
+    "ibl_stream": ([_P, C.POINTER(_P)], C.c_int),
+    "ibl_last_error": ([_P], C.c_char_p),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+
+class IblError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(ctx, status, allow=()):
+    if status != IBL_OK and status not in allow:
+        raise IblError(status, last_error(ctx))
+    return status
+
+
+def last_error(ctx=None) -> str:
+    return (_lib.ibl_last_error(ctx) or b"").decode()
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def lattice_velocities(lattice: int):
+    q = C.c_int32()
+    c = np.zeros((lattice, 3), dtype=np.int32)
+    w = np.zeros(lattice)
+    _check(None, _lib.ibl_lattice_velocities(lattice, C.byref(q), c.ctypes.data_as(_I32), _dptr(w)))
+    return c, w
+
+
+def _wave(w: dict | None):
+    if w is None:
+        return None, None
+    wv = ibl_wave()
+    wv.kind = int(w.get("kind", IBL_WAVE_CONST))
+    wv.amp = float(w.get("amp", 0.0))
+    wv.offset = float(w.get("offset", 0.0))
+    keep = None
+    if wv.kind == IBL_WAVE_TABLE:
+        keep = _f64(w["table"])
+        wv.table = _dptr(keep)
+        wv.n_table = keep.size
+    return wv, keep
+
+
+class Context:
+    """Owning wrapper around an ibl_ctx*; methods map 1:1 onto the C calls."""
+
+    def __init__(self, grid: dict, tau: float, lattice: int):
+        g = ibl_grid()
+        g.nx, g.ny, g.nz = int(grid["nx"]), int(grid["ny"]), int(grid["nz"])
+        for i, b in enumerate(grid["bc"]):
+            g.bc[i] = int(b)
+        for a in range(3):
+            g.u_in[a] = float(grid.get("u_in", (0, 0, 0))[a])
+            g.body_force[a] = float(grid.get("body_force", (0, 0, 0))[a])
+        g.rho_out = float(grid.get("rho_out", 1.0))
+        prec = grid.get("precision", "fp32")
+        g.precision = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        self.lattice = int(lattice)
+        self.d = 2 if self.lattice == IBL_D2Q9 else 3
+        self.shape = (g.nz, g.ny, g.nx)
+        self.N = g.nx * g.ny * g.nz
+        h = _P()
+        _check(None, _lib.ibl_create(C.byref(g), float(tau), self.lattice, C.byref(h)))
+        self.h = h
+        self.nbodies = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ibl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- set-up
+    def ibl_init_fluid(self, rho=None, u=None):
+        r = None if rho is None else _f64(np.broadcast_to(rho, self.shape))
+        uu = None
+        if u is not None:
+            u = np.asarray(u, dtype=np.float64)
+            if u.ndim == 1:
+                u = np.broadcast_to(u[:self.d, None, None, None], (self.d,) + self.shape)
+            uu = _f64(u.reshape((self.d,) + self.shape))
+        _check(self.h, _lib.ibl_init_fluid(self.h, _dptr(r), _dptr(uu)))
+
+    def ibl_set_populations(self, f):
+        f = _f64(f)
+        assert f.size == self.lattice * self.N
+        _check(self.h, _lib.ibl_set_populations(self.h, _dptr(f)))
+
+    def ibl_set_markers(self, X0, ds, hinge, axis, origin) -> int:
+        X0 = _f64(np.asarray(X0)[:, :self.d])
+        ds = _f64(ds)
+        bid = C.c_int32()
+        _check(self.h, _lib.ibl_set_markers(self.h, X0.shape[0], _dptr(X0), _dptr(ds),
+                                            _dptr(_f64(hinge)), _dptr(_f64(axis)), _dptr(_f64(origin)),
+                                            C.byref(bid)))
+        self.nbodies += 1
+        return bid.value
+
+    def ibl_set_kinematics(self, body_id, A, alpha, beta=0.0, phi=0.0, f=0.0, J=0.0):
+        wa, ka = _wave(A)
+        wb, kb = _wave(alpha)
+        _check(self.h, _lib.ibl_set_kinematics(self.h, body_id, C.byref(wa) if wa else None,
+                                               C.byref(wb) if wb else None, float(beta), float(phi),
+                                               float(f), float(J)))
+        del ka, kb
+
+    def ibl_set_marker_state(self, body_id, X, U):
+        X = _f64(np.asarray(X)[:, :self.d])
+        U = _f64(np.asarray(U)[:, :self.d])
+        _check(self.h, _lib.ibl_set_marker_state(self.h, body_id, _dptr(X), _dptr(U)))
+
+    def ibl_set_lift_axis(self, body_id, e):
+        _check(self.h, _lib.ibl_set_lift_axis(self.h, body_id, _dptr(_f64(e))))
+
+    def ibl_set_reference(self, U_ref, L_or_S, rho_ref=1.0):
+        _check(self.h, _lib.ibl_set_reference(self.h, float(U_ref), float(L_or_S), float(rho_ref)))
+
+    def add_body(self, body: dict) -> int:
+        """Convenience: markers + kinematics (+ lift axis) from a workload body dict."""
+        bid = self.ibl_set_markers(body["X0"], body["ds"], body["hinge"], body["axis"], body["origin"])
+        self.ibl_set_kinematics(bid, body["A"], body["alpha"], body.get("beta", 0.0), body.get("phi", 0.0),
+                                body.get("f", 0.0), body.get("J", 0.0))
+        if "lift_axis" in body:
+            self.ibl_set_lift_axis(bid, body["lift_axis"])
+        return bid
+
+    # ---------------------------------------------------------------- stepping
+    def ibl_step(self, n: int = 1, allow=()):
+        return _check(self.h, _lib.ibl_step(self.h, int(n)), allow)
+
+    def ibl_sync(self, allow=()):
+        return _check(self.h, _lib.ibl_sync(self.h), allow)
+
+    # ---------------------------------------------------------------- outputs
+    def ibl_forces(self, body_id, allow=()):
+        cl, ct, cd = C.c_double(), C.c_double(), C.c_double()
+        _check(self.h, _lib.ibl_forces(self.h, body_id, C.byref(cl), C.byref(ct), C.byref(cd)), allow)
+        return cl.value, ct.value, cd.value
+
+    def ibl_force_history(self, body_id, max_n, allow=()):
+        out = np.zeros((max(int(max_n), 1), 3))
+        n = C.c_int64()
+        _check(self.h, _lib.ibl_force_history(self.h, body_id, int(max_n), _dptr(out), C.byref(n)), allow)
+        return out[:n.value]
+
+    def ibl_get_field(self, what, allow=()):
+        comps = 1 if what == IBL_FIELD_RHO else self.d
+        out = np.zeros((comps,) + self.shape)
+        _check(self.h, _lib.ibl_get_field(self.h, int(what), _dptr(out)), allow)
+        return out[0] if what == IBL_FIELD_RHO else out
+
+    def ibl_get_populations(self, allow=()):
+        out = np.zeros((self.lattice,) + self.shape)
+        _check(self.h, _lib.ibl_get_populations(self.h, _dptr(out)), allow)
+        return out
+
+    def ibl_get_markers(self, body_id, m, allow=()):
+        X = np.zeros((m, self.d))
+        U = np.zeros((m, self.d))
+        F = np.zeros((m, self.d))
+        _check(self.h, _lib.ibl_get_markers(self.h, body_id, _dptr(X), _dptr(U), _dptr(F)), allow)
+        return X, U, F
+
+    def ibl_mass(self, allow=()):
+        m = C.c_double()
+        _check(self.h, _lib.ibl_mass(self.h, C.byref(m)), allow)
+        return m.value
+
+    def ibl_solver_stats(self, allow=()):
+        it, res, ref = C.c_int32(), C.c_double(), C.c_int64()
+        _check(self.h, _lib.ibl_solver_stats(self.h, C.byref(it), C.byref(res), C.byref(ref)), allow)
+        return it.value, res.value, ref.value
+
+    def ibl_profile(self, enable: bool):
+        _check(self.h, _lib.ibl_profile(self.h, 1 if enable else 0))
+
+    def ibl_profile_read(self):
+        a, b, n = C.c_double(), C.c_double(), C.c_int64()
+        _check(self.h, _lib.ibl_profile_read(self.h, C.byref(a), C.byref(b), C.byref(n)))
+        return a.value, b.value, n.value
+
+    def ibl_launch_count(self):
+        n = C.c_int64()
+        _check(self.h, _lib.ibl_launch_count(self.h, C.byref(n)))
+        return n.value
+
+    def ibl_stream(self):
+        s = _P()
+        _check(self.h, _lib.ibl_stream(self.h, C.byref(s)))
+        return s.value
+
+
+def ibl_create(grid: dict, tau: float, lattice: int) -> Context:
+    return Context(grid, tau, lattice)
+
+
+def from_workload(cfg: dict, init: bool = True) -> Context:
+    """Create a context for a workload dict of ``workloads`` and initialise it."""
+    ctx = Context(cfg["grid"], cfg["tau"], cfg["lattice"])
+    for b in cfg.get("bodies", []):
+        ctx.add_body(b)
+    if "reference" in cfg:
+        r = cfg["reference"]
+        ctx.ibl_set_reference(r["U_ref"], r["L"], r.get("rho_ref", 1.0))
+    if init:
+        if "u_field" in cfg:
+            ctx.ibl_init_fluid(None, cfg["u_field"][:ctx.d])
+        else:
+            ctx.ibl_init_fluid(None, np.asarray(cfg.get("u0", (0.0, 0.0, 0.0)))[:ctx.d])
+    return ctx

@@ -1,0 +1,141 @@
+"""GPU parity of the whole IB-LBM step (kinematics, interpolation, implicit
+solve, spreading, forcing, collision, forces) against the oracle, through the
+C ABI, on seeded synthetic workloads shaped like the paper's cases."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.parity import (TOL_COEF_FP32, TOL_FIELD_FP32, TOL_FIELD_FP64, compare_fields,
+                          oracle_from_workload, rel_err)
+
+pytestmark = pytest.mark.gpu
+
+
+def _coef_err(ctx, sim, body, steps):
+    hist = ctx.ibl_force_history(body, steps)
+    ref = np.array(sim.history[body][-len(hist):])
+    assert len(hist) == min(steps, len(sim.history[body]))
+    e_l = rel_err(hist[:, 0], ref[:, 0])
+    e_t = rel_err(hist[:, 1], ref[:, 1])
+    return e_l, e_t
+
+
+def test_cylinder_channel_fp64_full_run(ibl):
+    """2D D2Q9 FP64 cylinder in a body-force channel: 200 x 100, 63 markers, 5000 steps."""
+    cfg = W.cylinder_channel()
+    ctx = ibl.from_workload(cfg)
+    sim = oracle_from_workload(cfg)
+    ctx.ibl_step(5000)
+    sim.step(5000)
+    eu, er = compare_fields(ctx, sim, ibl, TOL_FIELD_FP64)
+    e_l, e_t = _coef_err(ctx, sim, 0, 5000)
+    print(f"cylinder FP64 5000 steps: u {eu:.2e} rho {er:.2e} CL {e_l:.2e} CD {e_t:.2e}")
+    assert e_l < 1e-7 and e_t < 1e-7
+    it, res, _ = ctx.ibl_solver_stats()
+    assert res < 1e-9
+
+
+def _small_wings(precision, nx=48, ny=40, nz=40):
+    return W.clap_fling_3d(nx=nx, ny=ny, nz=nz, chord=6.0, Re=5.0, J=0.1, period=1200.0,
+                           precision=precision)
+
+
+def test_wings_fp32_600_steps(ibl):
+    cfg = _small_wings("fp32")
+    ctx = ibl.from_workload(cfg)
+    sim = oracle_from_workload(cfg)
+    ctx.ibl_step(600)
+    sim.step(600)
+    eu, er = compare_fields(ctx, sim, ibl, TOL_FIELD_FP32)
+    worst = 0.0
+    for b in range(2):
+        e_l, e_t = _coef_err(ctx, sim, b, 600)
+        worst = max(worst, e_l, e_t)
+    print(f"wings FP32 600 steps: u {eu:.2e} rho {er:.2e} coef {worst:.2e}")
+    assert worst < TOL_COEF_FP32
+
+
+def test_wings_fp64_tight(ibl):
+    cfg = _small_wings("fp64")
+    ctx = ibl.from_workload(cfg)
+    sim = oracle_from_workload(cfg)
+    ctx.ibl_step(80)
+    sim.step(80)
+    compare_fields(ctx, sim, ibl, TOL_FIELD_FP64)
+    for b in range(2):
+        e_l, e_t = _coef_err(ctx, sim, b, 80)
+        assert e_l < 1e-7 and e_t < 1e-7
+        X, U, F = ctx.ibl_get_markers(b, len(cfg["bodies"][b]["ds"]))
+        m0 = 0 if b == 0 else len(cfg["bodies"][0]["ds"])
+        m = len(cfg["bodies"][b]["ds"])
+        assert np.abs(X - sim.last["X"][m0:m0 + m]).max() < 1e-12
+        assert np.abs(U - sim.last["U"][m0:m0 + m]).max() < 1e-15
+
+
+def test_prescribed_marker_state_and_periodic_wrap(ibl):
+    """Markers driven through ibl_set_marker_state, straddling periodic faces."""
+    n = 24
+    grid = W.grid(n, n, n, [W.PERIODIC] * 6, precision="fp64")
+    X0, ds = W.elliptic_planform_markers(6.0, 10.0)
+    body = {"X0": X0, "ds": ds, "hinge": (0, 0, 0), "axis": (0, 0, 1), "origin": (0.5, 12.3, 0.7),
+            "A": {"kind": W.WAVE_CONST}, "alpha": {"kind": W.WAVE_CONST}, "beta": 0, "phi": 0, "f": 0}
+    cfg = {"lattice": 19, "tau": 0.7, "grid": grid, "bodies": [body],
+           "u_field": W.tgv3d_velocity(n, n, n, 0.02)}
+    ctx = ibl.from_workload(cfg)
+    sim = oracle_from_workload(cfg)
+    rng = np.random.default_rng(5)
+    for k in range(15):
+        shift = np.array([0.37 * k, 0.05 * k, -0.21 * k])
+        X = (X0 + np.array([0.5, 12.3, 0.7]) + shift) % n
+        U = np.tile(rng.uniform(-0.01, 0.01, 3), (len(ds), 1))
+        ctx.ibl_set_marker_state(0, X, U)
+        sim.set_marker_state(0, X, U)
+        ctx.ibl_step(1)
+        sim.step(1)
+    compare_fields(ctx, sim, ibl, TOL_FIELD_FP64)
+    F = ctx.ibl_get_field(ibl.IBL_FIELD_FORCE)
+    Fo = sim.last_F
+    assert rel_err(F, Fo) < TOL_FIELD_FP64
+
+
+def test_no_slip_and_force_balance_on_gpu(ibl):
+    """Properties that hold at any size: the corrected velocity interpolates to
+    U_B (Eq. 17) and the marker forces sum to the Eulerian IB force."""
+    from oracle import ib
+    cfg = _small_wings("fp64")
+    ctx = ibl.from_workload(cfg)
+    ctx.ibl_step(30)
+    F = ctx.ibl_get_field(ibl.IBL_FIELD_FORCE)
+    lag = np.zeros(3)
+    for b in range(2):
+        m = len(cfg["bodies"][b]["ds"])
+        _, _, Fm = ctx.ibl_get_markers(b, m)
+        lag += Fm.sum(0)
+    assert np.allclose(lag, F.reshape(3, -1).sum(1), rtol=1e-9, atol=1e-15)
+    del ib
+
+
+def test_determinism_bitwise(ibl):
+    cfg = _small_wings("fp32")
+    outs = []
+    for _ in range(2):
+        ctx = ibl.from_workload(cfg)
+        ctx.ibl_step(40)
+        outs.append((ctx.ibl_get_field(ibl.IBL_FIELD_U), ctx.ibl_force_history(0, 40)))
+        ctx.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_stencil_leaving_a_wall_is_an_error(ibl):
+    grid = W.grid(40, 30, 1, [W.PERIODIC, W.PERIODIC, W.BOUNCEBACK, W.BOUNCEBACK, 0, 0], precision="fp64")
+    X0, ds = W.cylinder_markers(6.0, 19)
+    body = {"X0": X0, "ds": ds, "hinge": (0, 0, 0), "axis": (0, 0, 1), "origin": (20.0, 3.5, 0.0),
+            "A": {"kind": W.WAVE_CONST}, "alpha": {"kind": W.WAVE_CONST}, "beta": 0, "phi": 0, "f": 0}
+    ctx = ibl.from_workload({"lattice": 9, "tau": 0.8, "grid": grid, "bodies": [body]})
+    ctx.ibl_step(1)
+    with pytest.raises(ibl.IblError) as e:
+        ctx.ibl_sync()
+    assert e.value.status == ibl.IBL_EINVAL

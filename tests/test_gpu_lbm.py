@@ -1,0 +1,171 @@
+"""GPU parity of the fluid path (collide + stream + faces) against the oracle.
+
+Element-by-element comparisons on seeded inputs at sizes the oracle runs in
+seconds, ragged with respect to the kernels' 64 x 4 thread blocks and the
+16 x 4 x 4 band tiles; every call goes through the C ABI.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.parity import (TOL_FIELD_FP32, TOL_FIELD_FP64_LBM, compare_fields, gpu_to_oracle_order,
+                          oracle_from_workload, rel_err)
+
+pytestmark = pytest.mark.gpu
+
+
+def _tgv(n=(40, 36, 34), precision="fp32", tau=0.6, u0=0.05):
+    nx, ny, nz = n
+    return {"lattice": 19, "tau": tau, "grid": W.grid(nx, ny, nz, [W.PERIODIC] * 6, precision=precision),
+            "bodies": [], "u_field": W.tgv3d_velocity(nx, ny, nz, u0)}
+
+
+def test_tgv3d_fp32_1000_steps(ibl):
+    cfg = _tgv()
+    ctx = ibl.from_workload(cfg)
+    sim = oracle_from_workload(cfg)
+    ctx.ibl_step(1000)
+    sim.step(1000)
+    eu, er = compare_fields(ctx, sim, ibl, TOL_FIELD_FP32, 1e-6)
+    print(f"TGV FP32 1000 steps: u {eu:.2e} rho {er:.2e}")
+
+
+def test_tgv3d_fp64_exact(ibl):
+    cfg = _tgv(n=(21, 18, 19), precision="fp64")
+    ctx = ibl.from_workload(cfg)
+    sim = oracle_from_workload(cfg)
+    ctx.ibl_step(60)
+    sim.step(60)
+    compare_fields(ctx, sim, ibl, TOL_FIELD_FP64_LBM)
+
+
+def test_mass_is_conserved_periodic(ibl):
+    cfg = _tgv(n=(33, 20, 17), precision="fp64")
+    ctx = ibl.from_workload(cfg)
+    m0 = ctx.ibl_mass()
+    ctx.ibl_step(50)
+    assert abs(ctx.ibl_mass() - m0) < 1e-9 * m0
+    assert abs(m0 - 33 * 20 * 17) < 1e-9 * m0
+
+
+@pytest.mark.parametrize("q,prec", [(9, "fp64"), (19, "fp64"), (19, "fp32"), (9, "fp32")])
+def test_one_step_from_random_populations(ibl, q, prec):
+    """Populations after one step from an arbitrary (non-equilibrium) state, every face kind."""
+    rng = np.random.default_rng(11)
+    if q == 9:
+        shape = (1, 23, 37)
+        bcs = [[W.PERIODIC, W.PERIODIC, W.BOUNCEBACK, W.BOUNCEBACK, 0, 0],
+               [W.VEL_INLET, W.PRESS_OUTLET, W.PERIODIC, W.PERIODIC, 0, 0]]
+    else:
+        shape = (13, 11, 21)
+        bcs = [[W.PERIODIC, W.PERIODIC, W.BOUNCEBACK, W.BOUNCEBACK, W.BOUNCEBACK, W.BOUNCEBACK],
+               [W.VEL_INLET, W.PRESS_OUTLET, W.PERIODIC, W.PERIODIC, W.PERIODIC, W.PERIODIC],
+               [W.PERIODIC] * 6]
+    from oracle.lattice import get
+    lat = get(q)
+    perm = gpu_to_oracle_order(ibl, q)
+    for bc in bcs:
+        grid = W.grid(shape[2], shape[1], shape[0], bc, u_in=(0.02, -0.01, 0.005), rho_out=1.01,
+                      body_force=(1e-5, -2e-5, 3e-6), precision=prec)
+        f_ora = lat.w[:, None, None, None] * (1 + 0.05 * rng.uniform(-1, 1, size=(q,) + shape))
+        cfg = {"lattice": q, "tau": 0.7, "grid": grid, "bodies": []}
+        ctx = ibl.from_workload(cfg, init=False)
+        f_gpu = np.empty_like(f_ora)
+        f_gpu[perm] = f_ora
+        ctx.ibl_set_populations(f_gpu)
+        sim = oracle_from_workload(cfg)
+        sim.set_populations(f_ora)
+        ctx.ibl_step(2)
+        sim.step(2)
+        out = ctx.ibl_get_populations()[perm]
+        tol = 1e-14 if prec == "fp64" else 2e-7
+        err = np.abs(out - sim.f).max()
+        assert err < tol, (bc, err)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL_FIELD_FP64_LBM), ("fp32", TOL_FIELD_FP32)])
+def test_channel_with_body_force_and_walls(ibl, prec, tol):
+    nx, ny = 37, 23
+    grid = W.grid(nx, ny, 1, [W.PERIODIC, W.PERIODIC, W.BOUNCEBACK, W.BOUNCEBACK, 0, 0],
+                  body_force=(2e-6, 0, 0), precision=prec)
+    u = W.random_velocity((1, ny, nx), 2, 0.02)
+    cfg = {"lattice": 9, "tau": 0.8, "grid": grid, "bodies": []}
+    ctx = ibl.from_workload(cfg, init=False)
+    ctx.ibl_init_fluid(None, u)
+    sim = oracle_from_workload(cfg, u_field=u)
+    ctx.ibl_step(500)
+    sim.step(500)
+    compare_fields(ctx, sim, ibl, tol)
+
+
+@pytest.mark.parametrize("q,prec,tol", [(19, "fp32", TOL_FIELD_FP32), (9, "fp64", TOL_FIELD_FP64_LBM)])
+def test_inlet_outlet(ibl, q, prec, tol):
+    if q == 19:
+        nx, ny, nz = 45, 18, 14
+    else:
+        nx, ny, nz = 60, 27, 1
+    grid = W.grid(nx, ny, nz, [W.VEL_INLET, W.PRESS_OUTLET, W.PERIODIC, W.PERIODIC, W.PERIODIC, W.PERIODIC],
+                  u_in=(0.03, 0.0, 0.0), rho_out=1.0, precision=prec)
+    d = 3 if q == 19 else 2
+    u = 0.03 * np.ones((d, nz, ny, nx)) * np.array([1, 0, 0][:d])[:, None, None, None]
+    u = u + W.random_velocity((nz, ny, nx), d, 0.005)
+    cfg = {"lattice": q, "tau": 0.65, "grid": grid, "bodies": []}
+    ctx = ibl.from_workload(cfg, init=False)
+    ctx.ibl_init_fluid(None, u)
+    sim = oracle_from_workload(cfg, u_field=u)
+    ctx.ibl_step(300)
+    sim.step(300)
+    compare_fields(ctx, sim, ibl, tol)
+
+
+def test_full_size_box_one_step_sampled(ibl):
+    """The bench's full 256 x 192 x 160 D3Q19 FP32 box, in the bench's launch
+    configuration: one step from a random state, checked on sampled cells
+    computed one by one by the oracle's collision + streaming."""
+    from oracle import lbm
+    from oracle.lattice import D3Q19
+    nx, ny, nz = 256, 192, 160
+    grid = W.grid(nx, ny, nz, [W.VEL_INLET, W.PRESS_OUTLET] + [W.PERIODIC] * 4,
+                  u_in=(2.1e-4, 0, 0), precision="fp32")
+    cfg = {"lattice": 19, "tau": 0.5126, "grid": grid, "bodies": []}
+    ctx = ibl.from_workload(cfg, init=False)
+    u = W.random_velocity((nz, ny, nx), 3, 0.03)
+    ctx.ibl_init_fluid(None, u)
+    ctx.ibl_step(1)                           # collide-only first step
+    perm = gpu_to_oracle_order(ibl, 19)
+    f1 = ctx.ibl_get_populations()[perm]      # post-stream state after step 1
+    ctx.ibl_step(1)
+    f2 = ctx.ibl_get_populations()[perm]
+    rng = np.random.default_rng(3)
+    xs = np.concatenate([[0, 1, nx - 2, nx - 1], rng.integers(0, nx, 60)])
+    ys = np.concatenate([[0, ny - 1, 5, 100], rng.integers(0, ny, 60)])
+    zs = np.concatenate([[nz - 1, 0, 0, 80], rng.integers(0, nz, 60)])
+    worst = 0.0
+    for x, y, z in zip(xs, ys, zs):
+        # oracle: collide the 3x3x3 neighbourhood of step-1 populations, then stream into (x,y,z)
+        sl = np.ix_(range(19), [(z + k) % nz for k in (-1, 0, 1)], [(y + k) % ny for k in (-1, 0, 1)],
+                    [min(max(x + k, 0), nx - 1) for k in (-1, 0, 1)])
+        loc = f1[sl]
+        post = lbm.collide(D3Q19, loc, np.zeros((3, 3, 3, 3)), cfg["tau"])
+        if x in (0, nx - 1):
+            # rebuild the face exactly as the full-domain oracle would: pull into the
+            # face node, then apply the face's Zou-He rule
+            want = np.empty(19)
+            for i in range(19):
+                cx, cy, cz = D3Q19.c[i]
+                src_x = x - cx
+                if 0 <= src_x < nx:
+                    want[i] = post[i, 1 - cz, 1 - cy, 1 - cx]
+                else:
+                    want[i] = np.nan
+            # unknown populations: rebuild with the oracle's Zou-He on a 1-node slab
+            slab = want.reshape(19, 1, 1, 1).copy()
+            face = 0 if x == 0 else 1
+            lbm.zou_he(D3Q19, slab, face, W.VEL_INLET if x == 0 else W.PRESS_OUTLET, (2.1e-4, 0, 0), 1.0)
+            want = slab[:, 0, 0, 0]
+        else:
+            want = np.array([post[i, 1 - D3Q19.c[i, 2], 1 - D3Q19.c[i, 1], 1 - D3Q19.c[i, 0]]
+                             for i in range(19)])
+        err = np.abs(f2[:, z, y, x] - want).max()
+        worst = max(worst, err)
+    assert worst < 2e-7, worst
