@@ -49,26 +49,43 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16dev", "bf16dev", "fp64"])
+    ap.add_argument("--workload", default="wings", choices=["wings", "tgv"],
+                    help="wings: the clap-and-fling wing pair (default); tgv: pure D3Q19 periodic "
+                         "Taylor-Green vortex, u0=0.05, tau=0.6 (roofline sweep)")
+    ap.add_argument("--size", type=int, default=256, help="cube edge of the tgv workload")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-worker", default=None)   # internal: run the oracle sample
     return ap.parse_args()
 
 
-def workload(precision="fp32", scale=1.0):
+def workload(precision="fp32", scale=1.0, kind="wings", size=256):
     import workloads as W
+    if kind == "tgv":
+        n = max(8, int(round(size * scale)))
+        return W.taylor_green_3d(n=n, u0=0.05, tau=0.6, precision=precision)
     n = lambda v: max(8, int(round(v * scale)))
+    # x-periodic box: Zou-He inlet/outlet faces at this tau (0.5126) diverge
+    # within a few hundred steps on this 12.8c-long box, on the oracle and the GPU alike
     cfg = W.clap_fling_3d(nx=n(256), ny=n(192), nz=n(160), chord=max(4.0, round(20.0 * scale)),
-                          precision=precision)
+                          precision=precision, faces="periodic")
     return cfg
 
 
 def describe(cfg, steps):
     g = cfg["grid"]
     m = [len(b["ds"]) for b in cfg["bodies"]]
+    if not m:
+        return {"workload": (f"pure D3Q19 periodic Taylor-Green vortex, {g['precision'].upper()}, "
+                             f"{g['nx']}^3 cells, u0=0.05, tau=0.6"),
+                "cells": g["nx"] * g["ny"] * g["nz"], "markers": 0, "tau": cfg["tau"],
+                "steps_timed": steps,
+                "l2": ("no flush: populations exceed L2" if g["nx"] ** 3 * 152 > 129e6
+                       else "populations fit in L2 (small cube): numbers include L2 reuse")}
     return {"workload": (f"3D clap-and-fling wing pair, D3Q19 {g['precision'].upper()}, "
                          f"{g['nx']}x{g['ny']}x{g['nz']} cells, 2 elliptic wings c={cfg['bodies'][0]['hinge'][0]*2:g} "
-                         f"span 5c ({m[0]}+{m[1]} markers), Re=100, J=1e-2, period 4000 steps"),
+                         f"span 5c ({m[0]}+{m[1]} markers), Re=100, J=1e-2 (uniform initial free stream, periodic box), "
+                         f"period 4000 steps"),
             "cells": g["nx"] * g["ny"] * g["nz"], "markers": sum(m), "tau": round(cfg["tau"], 6),
             "steps_timed": steps,
             "l2": "no flush: every step streams 2 x 597 MB of populations, > 129 MB L2"}
@@ -118,17 +135,21 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle legs
-def oracle_glups(scale: float, steps: int, warm: int = 0) -> dict:
+def oracle_glups(scale: float, steps: int, warm: int = 0, kind: str = "wings", size: int = 256) -> dict:
     """Time the FP64 oracle on a scaled copy of the workload (single thread)."""
     import numpy as np
     from oracle.sim import Simulation
-    cfg = workload("fp32", scale)
+    cfg = workload("fp32", scale, kind, size)
     sim = Simulation(cfg["lattice"], cfg["grid"], cfg["tau"])
-    sim.init_fluid(u=np.asarray(cfg["u0"])[:3])
+    if "u_field" in cfg:
+        sim.init_fluid(u=cfg["u_field"])
+    else:
+        sim.init_fluid(u=np.asarray(cfg["u0"])[:3])
     for b in cfg["bodies"]:
         sim.add_body(b)
-    r = cfg["reference"]
-    sim.set_reference(r["U_ref"], r["L"], r["rho_ref"])
+    if "reference" in cfg:
+        r = cfg["reference"]
+        sim.set_reference(r["U_ref"], r["L"], r["rho_ref"])
     sim.step(warm)
     t0 = time.perf_counter()
     sim.step(steps)
@@ -139,12 +160,14 @@ def oracle_glups(scale: float, steps: int, warm: int = 0) -> dict:
             "markers": sum(len(b["ds"]) for b in cfg["bodies"]), "box": [g["nx"], g["ny"], g["nz"]]}
 
 
-def run_oracle_subprocess(scale: float, steps: int, warm: int = 0, timeout: float = 900) -> dict:
+def run_oracle_subprocess(scale: float, steps: int, warm: int = 0, timeout: float = 900,
+                          kind: str = "wings", size: int = 256) -> dict:
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", f"{scale},{steps},{warm}"]
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker",
+           f"{scale},{steps},{warm},{kind},{size}"]
     out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=timeout)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -189,7 +212,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
                                 init_method="env://")
     torch.cuda.set_device(0)
-    cfg = workload(args.precision)
+    cfg = workload(args.precision, 1.0, args.workload, args.size)
     g = cfg["grid"]
     cells = g["nx"] * g["ny"] * g["nz"]
     q = 19
@@ -227,7 +250,18 @@ def run_ours(args):
         status = str(e)
     collide_ms, ib_ms, nprof = ctx.ibl_profile_read()
     iters, res, refreshes = ctx.ibl_solver_stats(allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
-    cl = ctx.ibl_forces(0, allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED)) if status == "ok" else None
+    trace = None
+    if cfg["bodies"]:
+        tr = ctx.ibl_solver_trace(allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
+        if tr[0] and tr[3]:
+            per_it = [(tr[5 + 2 * k] - tr[3 + 2 * k if k else 2]) / 1e3 for k in range(iters) if tr[5 + 2 * k]]
+            trace = {"total_us": (tr[3] - tr[0]) / 1e3, "rebuild_us": (tr[1] - tr[0]) / 1e3,
+                     "setup_us": (tr[2] - tr[1]) / 1e3,
+                     "iteration_us_median": statistics.median(per_it) if per_it else None,
+                     "phase1_us_median": statistics.median([(tr[4 + 2 * k] - (tr[3 + 2 * k] if k else tr[2])) / 1e3
+                                                             for k in range(iters) if tr[4 + 2 * k]]) if iters else None}
+    cl = (ctx.ibl_forces(0, allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
+          if status == "ok" and cfg["bodies"] else None)
     ctx.close()
 
     if WORLD > 1:
@@ -238,7 +272,7 @@ def run_ours(args):
 
     # end to end: host buffers through the public API, copies inside the timed region
     e2e = None
-    if RANK == 0 and args.e2e_steps > 0:
+    if RANK == 0 and args.e2e_steps > 0 and cfg["bodies"]:
         e2e = run_e2e(ibl, cfg, args.e2e_steps, cells)
 
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -264,7 +298,7 @@ def run_ours(args):
     cpu = None
     if RANK == 0 and WORLD == 1 and not args.no_cpu_baseline:
         try:
-            r = run_oracle_subprocess(0.5, 6, 1)
+            r = run_oracle_subprocess(0.5, 6, 1, kind=args.workload, size=args.size)
             cpu = {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": (f"6 steps (after 1 untimed) of the workload 2x coarsened: "
                               f"{r['box'][0]}x{r['box'][1]}x{r['box'][2]} cells, {r['markers']} markers, "
@@ -283,7 +317,7 @@ def run_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "status": status,
                 "solver": {"pcg_iterations_last_step": iters, "rel_residual_last_step": res,
-                           "preconditioner_rebuilds": refreshes},
+                           "preconditioner_rebuilds": refreshes, "trace_last_step": trace},
                 "C_L_last_step_body0": cl[0] if cl else None}
         print(json.dumps(line), flush=True)
     if WORLD > 1:
@@ -333,9 +367,11 @@ def run_reference(args):
     budget = 120.0
     per_step = budget / max(1, args.steps + args.warmup)
     cells_target = max(6000.0, min(1.0e6, per_step * 4.0e5))
-    scale = (cells_target / (256 * 192 * 160)) ** (1.0 / 3.0)
-    r = run_oracle_subprocess(scale, args.steps, args.warmup, timeout=3600)
-    cfg = workload("fp32")
+    full = args.size ** 3 if args.workload == "tgv" else 256 * 192 * 160
+    scale = (cells_target / full) ** (1.0 / 3.0)
+    r = run_oracle_subprocess(scale, args.steps, args.warmup, timeout=3600, kind=args.workload,
+                              size=args.size)
+    cfg = workload("fp32", 1.0, args.workload, args.size)
     line = {"impl": "reference", "metric": METRIC, "value": round(r["value"], 6), "unit": UNIT,
             "n_gpus": WORLD, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(r["seconds"] / args.steps * 1e3, 3), "higher_is_better": True,
@@ -356,8 +392,8 @@ def run_reference(args):
 def main():
     args = parse()
     if args.cpu_baseline_worker:
-        scale, steps, warm = args.cpu_baseline_worker.split(",")
-        print(json.dumps(oracle_glups(float(scale), int(steps), int(warm))))
+        scale, steps, warm, kind, size = args.cpu_baseline_worker.split(",")
+        print(json.dumps(oracle_glups(float(scale), int(steps), int(warm), kind, int(size))))
         return
     if args.impl == "reference":
         run_reference(args)

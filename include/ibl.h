@@ -217,6 +217,12 @@ ibl_status ibl_lattice_velocities(int32_t lattice, int32_t* q, int32_t* c, doubl
 ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_residual,
                             int64_t* refreshes);
 
+/* Phase timestamps (GPU global timer, ns) of the last implicit solve:
+ * [0] start, [1] after the optional preconditioner rebuild, [2] after set-up,
+ * [3] end, [4 + 2k] / [5 + 2k] after the two grid barriers of iteration k.
+ * Unused slots are 0.  Copies min(max, 256) values into ns. */
+ibl_status ibl_solver_trace(ibl_ctx* ctx, int64_t* ns, int32_t max, int32_t* n);
+
 /* Enable (1) or disable (0) CUDA-event timing, on the context's stream, of
  * the collide-stream kernel and of the IB chain (kinematics .. spreading and
  * the force reduction) of every step enqueued while enabled.  Enabling

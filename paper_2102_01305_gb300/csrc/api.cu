@@ -74,6 +74,8 @@ ibl_status ibl_create(const ibl_grid* grid, double tau, int32_t lattice, ibl_ctx
   if (lattice != IBL_D2Q9 && lattice != IBL_D3Q19) return fail(nullptr, IBL_EINVAL, "unknown lattice");
   if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0) return fail(nullptr, IBL_EINVAL, "grid sizes must be > 0");
   if (lattice == IBL_D2Q9 && grid->nz != 1) return fail(nullptr, IBL_EINVAL, "D2Q9 needs nz == 1");
+  if ((long long)grid->nx * grid->ny * grid->nz >= (1LL << 31))
+    return fail(nullptr, IBL_EINVAL, "at most 2^31 - 1 cells per context");
   if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, IBL_EINVAL, "tau must be > 1/2");
   if (grid->precision < IBL_FP64 || grid->precision > IBL_BF16DEV)
     return fail(nullptr, IBL_EINVAL, "unknown precision");
@@ -557,6 +559,18 @@ ibl_status ibl_profile_read(ibl_ctx* c, double* collide_ms, double* ib_ms, int64
   if (ib_ms) *ib_ms = ti;
   if (steps) *steps = c->prof_steps;
   return IBL_OK;
+}
+
+ibl_status ibl_solver_trace(ibl_ctx* c, int64_t* ns, int32_t max, int32_t* n) {
+  if (!c || (!ns && max > 0)) return IBL_EINVAL;
+  ibl_status s = sync_and_collect(c);
+  if (s != IBL_OK && s != IBL_ENOTCONV) return s;
+  unsigned long long t[256] = {0};
+  if (c->ib_ready) CK(cudaMemcpy(t, c->d_trace, sizeof(t), cudaMemcpyDeviceToHost), "trace read");
+  const int k = std::min<int>(max, 256);
+  for (int i = 0; i < k; ++i) ns[i] = (int64_t)t[i];
+  if (n) *n = k;
+  return s;
 }
 
 ibl_status ibl_launch_count(const ibl_ctx* c, int64_t* n) {

@@ -29,9 +29,10 @@ namespace cg = cooperative_groups;
 namespace ibl {
 
 constexpr int MAX_BODIES = 16;
-constexpr int GJ_NB = 32;          // Gauss-Jordan pivot block
+constexpr int GJ_NB = 64;          // Gauss-Jordan pivot block
 constexpr int PCG_MAX_ITERS = 200;
-constexpr double PCG_TOL = 1e-10;  // relative preconditioned residual (field A-norm)
+constexpr double PCG_TOL = 1e-10;      // relative preconditioned residual (field A-norm), FP64 storage
+constexpr double PCG_TOL_LOW = 1e-8;   // FP32 / 16-bit storage: two decades under their rounding
 constexpr int REFRESH_EVERY = 64;  // steps between preconditioner rebuilds
 constexpr int REFRESH_ITERS = 40;  // rebuild early if a solve needed more
 
@@ -48,14 +49,10 @@ struct Geo {
 };
 
 __device__ __forceinline__ int wrap(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
-}
-
-__device__ __forceinline__ double phi_cos(double r) {
-  // Eq. 14: (1 + cos(pi |r| / 2)) / 4 for |r| <= 2
-  const double a = fabs(r);
-  return a <= 2.0 ? 0.25 * (1.0 + cospi(0.5 * a)) : 0.0;
+  // stencil offsets stay within one period of the axis (n >= 8 is enforced)
+  if (v < 0) v += n;
+  else if (v >= n) v -= n;
+  return v;
 }
 
 __device__ void wave_eval(const Wave& w, double t, double f, double phi, double& v, double& vd) {
@@ -84,7 +81,28 @@ __device__ void wave_eval(const Wave& w, double t, double f, double phi, double&
 }
 
 // ------------------------------------------------------------------ kinematics + stencil
-__global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ body_of,
+// One thread per body: wave values and rates (Eqs. 20-23) and the rotation's
+// cosine and sine at time t, shared by all of the body's markers.
+__global__ void k_body_state(BodyTable bt, double t, double* __restrict__ bstate) {
+  const int b = threadIdx.x;
+  if (b >= bt.n) return;
+  const BodyDev& B = bt.b[b];
+  double A, Ad, al, ald;
+  wave_eval(B.A, t, B.f, B.phi, A, Ad);
+  wave_eval(B.alpha, t, B.f, B.phi, al, ald);
+  double* st = bstate + 8 * b;
+  st[0] = A;
+  st[1] = Ad;
+  st[2] = ald;
+  st[3] = cos(al);
+  st[4] = sin(al);
+  st[5] = cos(B.beta);
+  st[6] = sin(B.beta);
+  st[7] = al;
+}
+
+__global__ void k_kinematics(BodyTable bt, const double* __restrict__ bstate, int m_total,
+                             const int* __restrict__ body_of,
                              const double* __restrict__ X0, const double* __restrict__ Xp,
                              const double* __restrict__ Up, double* __restrict__ X,
                              double* __restrict__ U, int* __restrict__ base,
@@ -96,15 +114,14 @@ __global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ 
   if (B.prescribed) {
     for (int a = 0; a < 3; ++a) { x[a] = Xp[3 * l + a]; u[a] = Up[3 * l + a]; }
   } else {
-    double A, Ad, al, ald;
-    wave_eval(B.A, t, B.f, B.phi, A, Ad);
-    wave_eval(B.alpha, t, B.f, B.phi, al, ald);
-    const double es[3] = {cos(B.beta), sin(B.beta), 0.0};
+    // per-body motion state of this step (k_body_state): A, A', alpha', cos, sin, e_s
+    const double* st = bstate + 8 * body_of[l];
+    const double A = st[0], Ad = st[1], ald = st[2], c = st[3], s = st[4];
+    const double es[3] = {st[5], st[6], 0.0};
     const double* e = B.axis;
     double d[3];
     for (int a = 0; a < 3; ++a) d[a] = X0[3 * l + a] - B.hinge[a];
     // Rodrigues: r = d cos + (e x d) sin + e (e.d)(1 - cos)
-    const double c = cos(al), s = sin(al);
     const double ed = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
     const double exd[3] = {e[1] * d[2] - e[2] * d[1], e[2] * d[0] - e[0] * d[2],
                            e[0] * d[1] - e[1] * d[0]};
@@ -128,10 +145,19 @@ __global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ 
       wts[12 * l + 4 * a + 3] = 0.0;
       continue;
     }
-    const int b0 = (int)floor(x[a]) - 1;
+    const double fl = floor(x[a]);
+    const int b0 = (int)fl - 1;
     if (!geo.per[a] && (b0 < 0 || b0 + 3 >= geo.n[a])) atomicOr(status, ST_OVERFLOW);
-    base[3 * l + a] = b0;
-    for (int k = 0; k < 4; ++k) wts[12 * l + 4 * a + k] = phi_cos((double)(b0 + k) - x[a]);
+    // Eq. 14 at the four nodes b0..b0+3, |r| = 1+s, s, 1-s, 2-s with s = x - floor(x):
+    // cos(pi|r|/2) = -sin, cos, sin, -cos of (pi s / 2).  The stored base is
+    // reduced into [0, n) on periodic axes so that later offsets wrap once at most.
+    double sn, cs;
+    sincospi(0.5 * (x[a] - fl), &sn, &cs);
+    wts[12 * l + 4 * a + 0] = 0.25 * (1.0 - sn);
+    wts[12 * l + 4 * a + 1] = 0.25 * (1.0 + cs);
+    wts[12 * l + 4 * a + 2] = 0.25 * (1.0 + sn);
+    wts[12 * l + 4 * a + 3] = 0.25 * (1.0 - cs);
+    base[3 * l + a] = geo.per[a] ? ((b0 % geo.n[a]) + geo.n[a]) % geo.n[a] : b0;
   }
 }
 
@@ -165,11 +191,12 @@ __device__ int touched_tiles(const Geo& g, const int* b, int out[8]) {
 
 __global__ void k_clear_tiles(int* __restrict__ tile_slot, const int* __restrict__ slot_tile,
                               const int* __restrict__ band_count, int* __restrict__ tile_mcount,
-                              int cap) {
+                              int* __restrict__ slot_body, int cap) {
   const int n = min(*band_count, cap);
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     tile_slot[slot_tile[s]] = -1;
     tile_mcount[s] = 0;
+    slot_body[s] = -1;
   }
 }
 
@@ -200,14 +227,18 @@ __global__ void k_assign_slots(int n_tiles, int* __restrict__ tile_slot, int* __
 
 __global__ void k_append_markers(int m_total, const int* __restrict__ base, Geo g,
                                  const int* __restrict__ tile_slot, int* __restrict__ tile_mcount,
-                                 int* __restrict__ tile_markers, int* status) {
+                                 int* __restrict__ tile_markers, int* status, const int* __restrict__ body_of,
+                                 int* __restrict__ slot_body, int* __restrict__ mixed) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= m_total) return;
   int t[8];
   const int n = touched_tiles(g, base + 3 * l, t);
+  const int bl = body_of[l];
   for (int i = 0; i < n; ++i) {
     const int s = tile_slot[t[i]];
     if (s < 0) continue;
+    const int prev = atomicCAS(&slot_body[s], -1, bl);
+    if (prev != -1 && prev != bl) *mixed = 1;   // two bodies' stencils share a tile
     const int pos = atomicAdd(&tile_mcount[s], 1);
     if (pos < TILE_MARKER_CAP) tile_markers[s * TILE_MARKER_CAP + pos] = l;
     else atomicOr(status, ST_OVERFLOW);
@@ -252,10 +283,15 @@ __global__ void k_band_moments(const T* __restrict__ src, FluidParams<typename S
         if (Lat<Q>::cz(i)) m2 += R(Lat<Q>::cz(i)) * g[i];
       }
       rho = R(1) + drho;
-      const R inv = R(1) / rho;
-      u0 = (m0 + R(0.5) * p.G[0]) * inv;    // Eq. 11 with the uniform body force
-      u1 = (m1 + R(0.5) * p.G[1]) * inv;
-      u2 = (m2 + R(0.5) * p.G[2]) * inv;
+      // Eq. 11 with the uniform body force; u = m - m drho/(1 + drho) keeps
+      // drho's low bits (as the collision does)
+      const R q = drho / rho;
+      u0 = m0 + R(0.5) * p.G[0];
+      u1 = m1 + R(0.5) * p.G[1];
+      u2 = m2 + R(0.5) * p.G[2];
+      u0 -= u0 * q;
+      u1 -= u1 * q;
+      u2 -= u2 * q;
     }
     R* o = band_mom + (long long)s * 4 * TILE_CELLS + local;
     o[0] = rho;
@@ -304,6 +340,44 @@ __global__ void k_interpolate(int m_total, const int* __restrict__ base, const d
 }
 
 // ------------------------------------------------------------------ system assembly
+// Markers of one rigid body keep their mutual distances.  Two stencils
+// overlap only if every coordinate differs by less than 4, hence only if the
+// Euclidean distance is below 4 sqrt(D): that set, computed once from the
+// body-frame coordinates, holds every possible partner of a marker forever.
+constexpr int CAND_MAX = 320;
+
+__global__ void k_build_candidates(int m_total, const double* __restrict__ X0, const int* __restrict__ body_of,
+                                   const int* __restrict__ boff, int D, int* __restrict__ cand,
+                                   int* __restrict__ ncand, int* __restrict__ status) {
+  const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (l >= m_total) return;
+  const int b = body_of[l];
+  const int o = boff[b], e = boff[b + 1];
+  const double r2 = 16.0 * D * (1.0 + 1e-12);
+  int count = 0;
+  for (int k0 = o; k0 < e; k0 += 32) {
+    const int k = k0 + lane;
+    bool take = false;
+    if (k < e) {
+      double d2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double d = X0[3 * k + a] - X0[3 * l + a];
+        d2 += d * d;
+      }
+      take = d2 < r2;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, take);
+    const int pos = count + __popc(mask & ((1u << lane) - 1));
+    if (take && pos < CAND_MAX) cand[(long long)l * CAND_MAX + pos] = k;
+    count += __popc(mask);
+  }
+  if (lane == 0) {
+    ncand[l] = min(count, CAND_MAX);
+    if (count > CAND_MAX) *status = 1;   // too dense for the lists: always use the tile search
+  }
+}
+
 // Minimal-image difference of stencil bases along an axis.
 __device__ __forceinline__ int base_diff(int bk, int bl, int n, int per) {
   int d = bk - bl;
@@ -318,11 +392,33 @@ __device__ __forceinline__ int base_diff(int bk, int bl, int n, int per) {
 // a pair is counted in the tile holding the lowest node of the two stencils'
 // overlap box, so every k appears once.  Rows are sorted by column so that
 // the SpMV sums in a fixed order.
+// Overlap product of the two stencils of markers l and k (Eq. 18 entry
+// without ds_k); false if the stencils do not share a node.
+__device__ __forceinline__ bool pair_entry(const Geo& g, const int* bl, const double* wl, const int* bk,
+                                           const double* wk, double& val, int lo[3]) {
+  double prod = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.D) { lo[a] = 0; continue; }
+    const int d = base_diff(bk[a], bl[a], g.n[a], g.per[a]);   // base_k - base_l
+    if (d < -3 || d > 3) return false;
+    const int o0 = d > 0 ? d : 0, o1 = d < 0 ? 3 + d : 3;
+    double s1 = 0.0;
+    for (int o = o0; o <= o1; ++o) s1 += wl[4 * a + o] * wk[4 * a + (o - d)];
+    prod *= s1;
+    const int node = bl[a] + o0;
+    lo[a] = g.per[a] ? wrap(node, g.n[a]) : node;
+  }
+  val = prod;
+  return true;
+}
+
 __global__ void k_assemble(int m_total, const int* __restrict__ base, const double* __restrict__ wts,
                            const int* __restrict__ tile_slot, const int* __restrict__ tile_mcount,
                            const int* __restrict__ tile_markers, Geo g, const int* __restrict__ body_of,
                            int* __restrict__ Gcol, double* __restrict__ Gval, int* __restrict__ Gnnz,
-                           unsigned long long* __restrict__ rowsum_max, int* status) {
+                           unsigned long long* __restrict__ rowsum_max, int* status,
+                           const int* __restrict__ cand, const int* __restrict__ ncand,
+                           const int* __restrict__ use_tiles, const int* __restrict__ cand_bad) {
   __shared__ int s_col[8][G_MAXNNZ];
   __shared__ double s_val[8][G_MAXNNZ];
   const int wib = threadIdx.x >> 5;
@@ -331,6 +427,41 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
   if (l >= m_total) return;
   const int* bl = base + 3 * l;
   const double* wl = wts + 12 * l;
+  if (cand && !*use_tiles && !*cand_bad) {
+    // rigid-body path: precomputed candidates, already in ascending order
+    const int nc = ncand[l];
+    int count = 0;
+    double rowsum = 0.0;
+    for (int j0 = 0; j0 < nc; j0 += 32) {
+      const int j = j0 + lane;
+      bool take = false;
+      double val = 0.0;
+      int k = -1;
+      if (j < nc) {
+        k = cand[(long long)l * CAND_MAX + j];
+        int lo[3];
+        take = pair_entry(g, bl, wl, base + 3 * k, wts + 12 * k, val, lo);
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, take);
+      const int pos = count + __popc(mask & ((1u << lane) - 1));
+      if (take) {
+        if (pos < G_MAXNNZ) {
+          Gcol[(long long)l * G_MAXNNZ + pos] = k;
+          Gval[(long long)l * G_MAXNNZ + pos] = val;
+        } else {
+          atomicOr(status, ST_OVERFLOW);
+        }
+        rowsum += fabs(val);
+      }
+      count += __popc(mask);
+    }
+    for (int o = 16; o > 0; o >>= 1) rowsum += __shfl_xor_sync(0xffffffffu, rowsum, o);
+    if (lane == 0) {
+      Gnnz[l] = min(count, G_MAXNNZ);
+      atomicMax(&rowsum_max[body_of[l]], (unsigned long long)__double_as_longlong(rowsum));
+    }
+    return;
+  }
   int tiles[8];
   const int nt = touched_tiles(g, bl, tiles);
   int count = 0;
@@ -347,27 +478,10 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
       int k = -1;
       if (j < cnt) {
         k = tile_markers[s * TILE_MARKER_CAP + j];
-        const int* bk = base + 3 * k;
-        const double* wk = wts + 12 * k;
-        take = true;
         int lo[3];
-        double prod = 1.0;
-        for (int a = 0; a < 3 && take; ++a) {
-          if (a >= g.D) { lo[a] = 0; continue; }
-          const int d = base_diff(bk[a], bl[a], g.n[a], g.per[a]);   // base_k - base_l
-          if (d < -3 || d > 3) { take = false; break; }
-          // overlap nodes in l's frame: o in [max(0,d), min(3,3+d)]
-          const int o0 = d > 0 ? d : 0, o1 = d < 0 ? 3 + d : 3;
-          double s1 = 0.0;
-          for (int o = o0; o <= o1; ++o) s1 += wl[4 * a + o] * wk[4 * a + (o - d)];
-          prod *= s1;
-          int node = bl[a] + o0;
-          lo[a] = g.per[a] ? wrap(node, g.n[a]) : node;
-        }
-        if (take) {
-          if (tile_of(g, lo[0], lo[1], g.D == 3 ? lo[2] : 0) != t) take = false;
-          val = prod;
-        }
+        take = pair_entry(g, bl, wl, base + 3 * k, wts + 12 * k, val, lo);
+        // count the pair only in the tile of the lowest node both stencils share
+        if (take && tile_of(g, lo[0], lo[1], g.D == 3 ? lo[2] : 0) != t) take = false;
       }
       const unsigned mask = __ballot_sync(0xffffffffu, take);
       const int pos = count + __popc(mask & ((1u << lane) - 1));
@@ -401,12 +515,17 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
 }
 
 // ------------------------------------------------------------------ PCG with in-kernel preconditioner rebuild
+constexpr int PCG_THREADS = 1024;
+constexpr int TRACE_SLOTS = 256;
+constexpr int PCG_WARPS = PCG_THREADS / 32;
+
 struct PcgArgs {
   int m_total;
   int D;
   int nbodies;
   int boff[MAX_BODIES + 1];     // marker offsets
-  long long poff[MAX_BODIES];   // preconditioner offsets (floats)
+  long long poff[MAX_BODIES];   // preconditioner offsets (floats, 16-byte aligned)
+  int voff[MAX_BODIES];         // offset of each body's slice in the padded FP32 vectors
   const int* body_of;
   const int* Gcol;
   const double* Gval;
@@ -415,189 +534,262 @@ struct PcgArgs {
   const double* B;
   double* w;
   double* r;
-  double* p;
+  double* p;        // 2 x m x 3 ping-pong search directions
   double* Ap;
   double* z;
+  float* rf;        // FP32 copies feeding the preconditioner: r, A p, B
+  float* Apf;
+  float* Bf;
   float* M;
   double* red;      // [gridDim][8] partials
-  int* info;        // [0] iterations, [1] refresh request, [2] converged flag
+  int* info;        // [0] iterations, [1] rebuild request, [2] converged flag
   double* res;      // final relative residual
+  double tol;
   int warm;
   int refresh;      // host-scheduled rebuild
   int* status;
+  unsigned long long* trace;   // optional phase timestamps (ns), see ibl_solver_trace
 };
 
-// Deterministic block reduction of nv doubles; result valid in thread 0.
+__device__ __forceinline__ void trace_mark(const PcgArgs& A, int slot) {
+  if (A.trace && blockIdx.x == 0 && threadIdx.x == 0 && slot < TRACE_SLOTS) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    A.trace[slot] = t;
+  }
+}
+
+// Fixed-order block sum of one double per warp (lane 0 holds it); the total
+// is returned to every thread.
+__device__ double block_total(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < PCG_WARPS ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) sh[PCG_WARPS] = t;
+  }
+  __syncthreads();
+  t = sh[PCG_WARPS];
+  return t;
+}
+
+// Sum of the per-block partials in a fixed order by warp 0; every block
+// computes bitwise the same totals, returned to all threads.
 template <int NV>
-__device__ void block_sum(double v[NV], double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int o = 16; o > 0; o >>= 1)
-    for (int c = 0; c < NV; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+__device__ void grid_total(const double* red, int slot, double out[NV], double* sh) {
   __syncthreads();
-  if (lane == 0)
-    for (int c = 0; c < NV; ++c) sh[wid * NV + c] = v[c];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < NV; ++c) {
-      double s = 0;
-      for (int w = 0; w < nw; ++w) s += sh[w * NV + c];
-      v[c] = s;
-    }
+  if (threadIdx.x < 32) {
+    double v[NV];
+    for (int c = 0; c < NV; ++c) v[c] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
+      for (int c = 0; c < NV; ++c) v[c] += red[b * 8 + slot + c];
+    for (int o = 16; o > 0; o >>= 1)
+      for (int c = 0; c < NV; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < NV; ++c) sh[c] = v[c];
   }
   __syncthreads();
+  for (int c = 0; c < NV; ++c) out[c] = sh[c];
 }
 
-// Sum of the per-block partials in block order (every block gets the same bits).
-template <int NV>
-__device__ void grid_total(const double* red, int slot, double out[NV]) {
-  for (int c = 0; c < NV; ++c) out[c] = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b)
-    for (int c = 0; c < NV; ++c) out[c] += red[b * 8 + slot + c];
-}
+// Row stride of a body's dense preconditioner: padded to 4 floats so rows
+// start 16-byte aligned for 128-bit loads.
+__host__ __device__ __forceinline__ int precond_ld(int mb) { return (mb + 3) & ~3; }
 
-// y = G x for the rows of this warp (strided over all warps).
-__device__ void spmv_rows(const PcgArgs& A, const double* __restrict__ x, double* __restrict__ y,
-                          int gwarp, int nwarps, int lane) {
-  for (int l = gwarp; l < A.m_total; l += nwarps) {
-    const int nnz = A.Gnnz[l];
-    double s0 = 0, s1 = 0, s2 = 0;
-    for (int j = lane; j < nnz; j += 32) {
-      const int k = A.Gcol[(long long)l * G_MAXNNZ + j];
-      const double v = A.Gval[(long long)l * G_MAXNNZ + j];
-      s0 += v * x[3 * k];
-      s1 += v * x[3 * k + 1];
-      s2 += v * x[3 * k + 2];
+// One row of the preconditioner: sum_j M_lj x_j with x_j = a_j - s * b_j formed
+// in FP32 (b may be null); 128-bit loads of M and of the interleaved xyz
+// vectors, lane-parallel over the row; the result is returned in every lane.
+__device__ __forceinline__ void precond_row(const PcgArgs& A, int l, const float* __restrict__ a,
+                                            const float* __restrict__ b, const float s[3], float out[3],
+                                            int lane) {
+  const int bd = A.body_of[l];
+  const int o = A.boff[bd], mb = A.boff[bd + 1] - o;
+  const int ld = precond_ld(mb);
+  const float* row = A.M + A.poff[bd] + (long long)(l - o) * ld;
+  // the vectors are padded per body so that 3*o is a multiple of 4 floats
+  const float* ab = a + A.voff[bd];
+  const float* bb = b ? b + A.voff[bd] : nullptr;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  const int nq = ld >> 2;
+#pragma unroll 2
+  for (int q = lane; q < nq; q += 32) {
+    const float4 mv = reinterpret_cast<const float4*>(row)[q];
+    const float4* av = reinterpret_cast<const float4*>(ab + 12 * q);
+    float4 x0 = av[0], x1 = av[1], x2 = av[2];
+    if (bb) {
+      const float4* bv = reinterpret_cast<const float4*>(bb + 12 * q);
+      const float4 y0 = bv[0], y1 = bv[1], y2 = bv[2];
+      x0.x = fmaf(-s[0], y0.x, x0.x); x0.y = fmaf(-s[1], y0.y, x0.y); x0.z = fmaf(-s[2], y0.z, x0.z);
+      x0.w = fmaf(-s[0], y0.w, x0.w); x1.x = fmaf(-s[1], y1.x, x1.x); x1.y = fmaf(-s[2], y1.y, x1.y);
+      x1.z = fmaf(-s[0], y1.z, x1.z); x1.w = fmaf(-s[1], y1.w, x1.w); x2.x = fmaf(-s[2], y2.x, x2.x);
+      x2.y = fmaf(-s[0], y2.y, x2.y); x2.z = fmaf(-s[1], y2.z, x2.z); x2.w = fmaf(-s[2], y2.w, x2.w);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    if (lane == 0) { y[3 * l] = s0; y[3 * l + 1] = s1; y[3 * l + 2] = s2; }
+    // columns 4q .. 4q+3: (x0.x x0.y x0.z) (x0.w x1.x x1.y) (x1.z x1.w x2.x) (x2.y x2.z x2.w)
+    s0 = fmaf(mv.x, x0.x, s0); s1 = fmaf(mv.x, x0.y, s1); s2 = fmaf(mv.x, x0.z, s2);
+    s0 = fmaf(mv.y, x0.w, s0); s1 = fmaf(mv.y, x1.x, s1); s2 = fmaf(mv.y, x1.y, s2);
+    s0 = fmaf(mv.z, x1.z, s0); s1 = fmaf(mv.z, x1.w, s1); s2 = fmaf(mv.z, x2.x, s2);
+    s0 = fmaf(mv.w, x2.y, s0); s1 = fmaf(mv.w, x2.z, s1); s2 = fmaf(mv.w, x2.w, s2);
   }
-}
-
-// y = M_b x (FP32 dense preconditioner of the row's body, FP64 accumulation per lane).
-__device__ void precond_rows(const PcgArgs& A, const double* __restrict__ x, double* __restrict__ y,
-                             int gwarp, int nwarps, int lane) {
-  for (int l = gwarp; l < A.m_total; l += nwarps) {
-    const int b = A.body_of[l];
-    const int o = A.boff[b], mb = A.boff[b + 1] - o;
-    const float* row = A.M + A.poff[b] + (long long)(l - o) * mb;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-    for (int j = lane; j < mb; j += 32) {
-      const float v = row[j];
-      const int k = o + j;
-      s0 = fmaf(v, (float)x[3 * k], s0);
-      s1 = fmaf(v, (float)x[3 * k + 1], s1);
-      s2 = fmaf(v, (float)x[3 * k + 2], s2);
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-    }
-    if (lane == 0) { y[3 * l] = s0; y[3 * l + 1] = s1; y[3 * l + 2] = s2; }
+  for (int off = 16; off > 0; off >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, off);
   }
+  out[0] = s0; out[1] = s1; out[2] = s2;
 }
 
+// ---------------------------------------------------------------- dense rebuild
 // In-place blocked Gauss-Jordan inverse of every body's dense SPD matrix
-// (no pivoting; the matrix is G_b + sigma I).  For the pivot block P:
+// (no pivoting; the matrix is G_b + sigma I, row stride precond_ld(m_b)).
+// For the pivot block P (GJ_NB wide):
 //   P <- P^-1;  row panel R <- P^-1 R;  rest S <- S - C R;  column panel C <- -C P^-1.
-__device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sh) {
+// The three panel products run through one register-tiled shared-memory
+// routine (128 x 128 output tiles, 4 x 4 outputs per thread, K <= GJ_NB).
+constexpr int GT = 128;                 // output tile edge
+constexpr int GS = GT + 4;              // padded shared-memory row
+constexpr size_t GJ_SMEM = sizeof(float) * 2 * GJ_NB * GS;
+
+// out[i0+r][j0+c] = (acc ? out : 0) + alpha * sum_q A[r][q] B[q][j0+c] over one
+// tile (r < nr, c < nc), skipping output rows in [sk0, sk1) and columns in
+// [ck0, ck1).  Ag points at the tile's first A row; Bg at B's row 0 (its
+// columns are absolute).  Inputs are staged in shared memory before any
+// output is written, so out may alias A or B within the tile.
+__device__ void tile_gemm(float* out, int ldo, const float* Ag, int lda, const float* Bg, int ldb, int i0,
+                          int j0, int nr, int nc, int K, float alpha, bool acc, int sk0, int sk1, int ck0,
+                          int ck1, float* sm) {
+  float* As = sm;               // [q][r], GJ_NB x GS
+  float* Bs = sm + GJ_NB * GS;  // [q][c], GJ_NB x GS
+  __syncthreads();
+  for (int e = threadIdx.x; e < GT * GJ_NB; e += blockDim.x) {
+    const int r = e / GJ_NB, q = e % GJ_NB;
+    As[q * GS + r] = (r < nr && q < K) ? Ag[(long long)r * lda + q] : 0.f;
+  }
+  for (int e = threadIdx.x; e < GJ_NB * GT; e += blockDim.x) {
+    const int q = e / GT, c = e % GT;
+    Bs[q * GS + c] = (q < K && c < nc) ? Bg[(long long)q * ldb + j0 + c] : 0.f;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+  float a4[4][4];
+  for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < 4; ++v) a4[u][v] = 0.f;
+  for (int q = 0; q < K; ++q) {
+    const float4 av = *reinterpret_cast<const float4*>(As + q * GS + 4 * ty);
+    const float4 bv = *reinterpret_cast<const float4*>(Bs + q * GS + 4 * tx);
+    const float ar[4] = {av.x, av.y, av.z, av.w};
+    const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+    for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < 4; ++v) a4[u][v] = fmaf(ar[u], br[v], a4[u][v]);
+  }
+  for (int u = 0; u < 4; ++u) {
+    const int r = 4 * ty + u, i = i0 + r;
+    if (r >= nr || (i >= sk0 && i < sk1)) continue;
+    for (int v = 0; v < 4; ++v) {
+      const int c = 4 * tx + v, j = j0 + c;
+      if (c >= nc || (j >= ck0 && j < ck1)) continue;
+      float* o = out + (long long)i * ldo + j;
+      *o = (acc ? *o : 0.f) + alpha * a4[u][v];
+    }
+  }
+}
+
+__device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
   int maxnb = 0;
   for (int b = 0; b < A.nbodies; ++b) {
     const int mb = A.boff[b + 1] - A.boff[b];
     maxnb = max(maxnb, (mb + GJ_NB - 1) / GJ_NB);
   }
-  const int nthreads = gridDim.x * blockDim.x;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  float* piv = sh;                          // GJ_NB x GJ_NB
   for (int kb = 0; kb < maxnb; ++kb) {
-    // phase 1: invert the pivot blocks (block b of the grid handles body b)
+    const int k0 = kb * GJ_NB;
+    // phase 1: invert the pivot block of body b in block b (Gauss-Jordan in shared memory)
     for (int b = blockIdx.x; b < A.nbodies; b += gridDim.x) {
       const int mb = A.boff[b + 1] - A.boff[b];
-      const int k0 = kb * GJ_NB;
       if (k0 >= mb) continue;
-      const int kn = min(GJ_NB, mb - k0);
+      const int kn = min(GJ_NB, mb - k0), ld = precond_ld(mb);
       float* Mb = A.M + A.poff[b];
+      float* piv = sm;                    // kn x kn
+      float* rowk = sm + GJ_NB * GJ_NB;   // pivot row and column copies
+      float* colk = rowk + GJ_NB;
+      __syncthreads();
       for (int e = threadIdx.x; e < kn * kn; e += blockDim.x)
-        piv[e] = Mb[(long long)(k0 + e / kn) * mb + k0 + e % kn];
+        piv[e] = Mb[(long long)(k0 + e / kn) * ld + k0 + e % kn];
       __syncthreads();
       for (int k = 0; k < kn; ++k) {
-        const float pk = 1.0f / piv[k * kn + k];
+        if (threadIdx.x < kn) {
+          rowk[threadIdx.x] = piv[k * kn + threadIdx.x];
+          colk[threadIdx.x] = piv[threadIdx.x * kn + k];
+        }
         __syncthreads();
-        // row k scaled, other rows eliminated (unblocked Gauss-Jordan)
+        const float pk = 1.0f / rowk[k];
         for (int e = threadIdx.x; e < kn * kn; e += blockDim.x) {
           const int i = e / kn, j = e % kn;
           float v;
           if (i == k && j == k) v = pk;
-          else if (i == k) v = piv[k * kn + j] * pk;
-          else if (j == k) v = -piv[i * kn + k] * pk;
-          else v = piv[i * kn + j] - piv[i * kn + k] * piv[k * kn + j] * pk;
-          sh[GJ_NB * GJ_NB + e] = v;
+          else if (i == k) v = rowk[j] * pk;
+          else if (j == k) v = -colk[i] * pk;
+          else v = piv[e] - colk[i] * rowk[j] * pk;
+          piv[e] = v;
         }
-        __syncthreads();
-        for (int e = threadIdx.x; e < kn * kn; e += blockDim.x) piv[e] = sh[GJ_NB * GJ_NB + e];
         __syncthreads();
       }
       for (int e = threadIdx.x; e < kn * kn; e += blockDim.x)
-        Mb[(long long)(k0 + e / kn) * mb + k0 + e % kn] = piv[e];
-      __syncthreads();
+        Mb[(long long)(k0 + e / kn) * ld + k0 + e % kn] = piv[e];
     }
     grid.sync();
-    // phase 2: row panel R <- P^-1 R (one thread per column outside the pivot block)
-    for (int b = 0; b < A.nbodies; ++b) {
-      const int mb = A.boff[b + 1] - A.boff[b];
-      const int k0 = kb * GJ_NB;
-      if (k0 >= mb) continue;
-      const int kn = min(GJ_NB, mb - k0);
-      float* Mb = A.M + A.poff[b];
-      for (int j = gtid; j < mb; j += nthreads) {
-        if (j >= k0 && j < k0 + kn) continue;
-        float col[GJ_NB];
-        for (int i = 0; i < kn; ++i) col[i] = Mb[(long long)(k0 + i) * mb + j];
-        for (int i = 0; i < kn; ++i) {
-          float s = 0.f;
-          for (int q = 0; q < kn; ++q) s = fmaf(Mb[(long long)(k0 + i) * mb + k0 + q], col[q], s);
-          Mb[(long long)(k0 + i) * mb + j] = s;
+    // phase 2: row panel R <- P^-1 R (tiles of GJ_NB rows x GT columns)
+    {
+      int done = 0;
+      for (int b = 0; b < A.nbodies; ++b) {
+        const int mb = A.boff[b + 1] - A.boff[b];
+        if (k0 >= mb) continue;
+        const int kn = min(GJ_NB, mb - k0), ld = precond_ld(mb);
+        float* Mb = A.M + A.poff[b];
+        const int nt = (mb + GT - 1) / GT;
+        for (int t = 0; t < nt; ++t, ++done) {
+          if (done % gridDim.x != blockIdx.x) continue;
+          const int j0 = t * GT;
+          tile_gemm(Mb, ld, Mb + (long long)k0 * ld + k0, ld, Mb + (long long)k0 * ld, ld, k0, j0, kn,
+                    min(GT, mb - j0), kn, 1.0f, false, -1, -1, k0, k0 + kn, sm);
         }
       }
     }
     grid.sync();
     // phase 3a: S <- S - C R (rows and columns outside the pivot block)
-    for (int b = 0; b < A.nbodies; ++b) {
-      const int mb = A.boff[b + 1] - A.boff[b];
-      const int k0 = kb * GJ_NB;
-      if (k0 >= mb) continue;
-      const int kn = min(GJ_NB, mb - k0);
-      float* Mb = A.M + A.poff[b];
-      const long long total = (long long)mb * mb;
-      for (long long e = gtid; e < total; e += nthreads) {
-        const int i = (int)(e / mb), j = (int)(e % mb);
-        if ((i >= k0 && i < k0 + kn) || (j >= k0 && j < k0 + kn)) continue;
-        float s = Mb[e];
-        const float* ci = Mb + (long long)i * mb + k0;
-        for (int q = 0; q < kn; ++q) s = fmaf(-ci[q], Mb[(long long)(k0 + q) * mb + j], s);
-        Mb[e] = s;
+    {
+      int done = 0;
+      for (int b = 0; b < A.nbodies; ++b) {
+        const int mb = A.boff[b + 1] - A.boff[b];
+        if (k0 >= mb) continue;
+        const int kn = min(GJ_NB, mb - k0), ld = precond_ld(mb);
+        float* Mb = A.M + A.poff[b];
+        const int nt = (mb + GT - 1) / GT;
+        for (int t = 0; t < nt * nt; ++t, ++done) {
+          if (done % gridDim.x != blockIdx.x) continue;
+          const int i0 = (t / nt) * GT, j0 = (t % nt) * GT;
+          tile_gemm(Mb, ld, Mb + (long long)i0 * ld + k0, ld, Mb + (long long)k0 * ld, ld, i0, j0,
+                    min(GT, mb - i0), min(GT, mb - j0), kn, -1.0f, true, k0, k0 + kn, k0, k0 + kn, sm);
+        }
       }
     }
     grid.sync();
     // phase 3b: C <- -C P^-1 (rows outside, columns inside the pivot block)
-    for (int b = 0; b < A.nbodies; ++b) {
-      const int mb = A.boff[b + 1] - A.boff[b];
-      const int k0 = kb * GJ_NB;
-      if (k0 >= mb) continue;
-      const int kn = min(GJ_NB, mb - k0);
-      float* Mb = A.M + A.poff[b];
-      for (int i = gtid; i < mb; i += nthreads) {
-        if (i >= k0 && i < k0 + kn) continue;
-        float row[GJ_NB];
-        for (int q = 0; q < kn; ++q) row[q] = Mb[(long long)i * mb + k0 + q];
-        for (int j = 0; j < kn; ++j) {
-          float s = 0.f;
-          for (int q = 0; q < kn; ++q) s = fmaf(row[q], Mb[(long long)(k0 + q) * mb + k0 + j], s);
-          Mb[(long long)i * mb + k0 + j] = -s;
+    {
+      int done = 0;
+      for (int b = 0; b < A.nbodies; ++b) {
+        const int mb = A.boff[b + 1] - A.boff[b];
+        if (k0 >= mb) continue;
+        const int kn = min(GJ_NB, mb - k0), ld = precond_ld(mb);
+        float* Mb = A.M + A.poff[b];
+        const int nt = (mb + GT - 1) / GT;
+        for (int t = 0; t < nt; ++t, ++done) {
+          if (done % gridDim.x != blockIdx.x) continue;
+          const int i0 = t * GT;
+          tile_gemm(Mb, ld, Mb + (long long)i0 * ld + k0, ld, Mb + (long long)k0 * ld, ld, i0, k0,
+                    min(GT, mb - i0), kn, kn, -1.0f, false, k0, k0 + kn, -1, -1, sm);
         }
       }
     }
@@ -605,29 +797,37 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sh) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_pcg(PcgArgs A) {
+// Preconditioned CG on G w = B, three right-hand sides (velocity components)
+// at once, two grid barriers per iteration.  A p is updated by the
+// recurrence A p = G z + beta A p_old, so the FP64 SpMV reads z only and
+// no direction is recomputed by its neighbours; r - alpha A p is formed in
+// FP32 inside the preconditioner product.  Row l belongs to one warp of
+// block l mod gridDim, which spreads the FP64 work over all SMs.
+__global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ float sh[2 * GJ_NB * GJ_NB];
-  __shared__ double shd[8 * 8];
+  extern __shared__ __align__(16) float sm[];
+  __shared__ double shd[64];
   const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int wib = threadIdx.x >> 5;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nthreads = gridDim.x * blockDim.x;
-  const int m3 = 3 * A.m_total;
+  const int m = A.m_total;
+  const int row0 = blockIdx.x + gridDim.x * wib;       // this warp's first row
+  const int rstep = gridDim.x * PCG_WARPS;
 
   // ---- optional preconditioner rebuild: M_b <- (G_b + sigma_b I)^-1 in FP32
+  trace_mark(A, 0);
   const bool rebuild = A.refresh || A.info[1];
   if (rebuild) {
     for (int b = 0; b < A.nbodies; ++b) {
       const int mb = A.boff[b + 1] - A.boff[b];
-      const long long tot = (long long)mb * mb;
+      const long long tot = (long long)mb * precond_ld(mb);
       for (long long e = gtid; e < tot; e += nthreads) A.M[A.poff[b] + e] = 0.f;
     }
     grid.sync();
-    for (int l = gtid; l < A.m_total; l += nthreads) {
+    for (int l = gtid; l < m; l += nthreads) {
       const int b = A.body_of[l];
-      const int o = A.boff[b], mb = A.boff[b + 1] - o;
+      const int o = A.boff[b], mb = A.boff[b + 1] - o, ld = precond_ld(mb);
       const double sigma = 1e-6 * __longlong_as_double((long long)A.rowsum_max[b]);
       float* Mb = A.M + A.poff[b];
       for (int j = 0; j < A.Gnnz[l]; ++j) {
@@ -635,94 +835,206 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs A) {
         if (A.body_of[k] != b) continue;   // block-Jacobi over bodies
         double v = A.Gval[(long long)l * G_MAXNNZ + j];
         if (k == l) v += sigma;
-        Mb[(long long)(l - o) * mb + (k - o)] = (float)v;
+        Mb[(long long)(l - o) * ld + (k - o)] = (float)v;
       }
     }
     grid.sync();
-    gj_invert(A, grid, sh);
+    gj_invert(A, grid, sm);
   }
+  trace_mark(A, 1);
 
-  // ---- setup: x0 = warm ? w : 0;  r = B - G x0;  z = M r;  p = z
-  if (!A.warm)
-    for (int i = gtid; i < m3; i += nthreads) A.w[i] = 0.0;
+  // ---- set-up: w0 = warm ? w : 0;  r = B - G w0;  FP32 copies; p = A p = 0
+  for (int l = row0; l < m; l += rstep) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    if (A.warm) {
+      const int nnz = A.Gnnz[l];
+      for (int j = lane; j < nnz; j += 32) {
+        const int k = A.Gcol[(long long)l * G_MAXNNZ + j];
+        const double v = A.Gval[(long long)l * G_MAXNNZ + j];
+        s0 += v * A.w[3 * k];
+        s1 += v * A.w[3 * k + 1];
+        s2 += v * A.w[3 * k + 2];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      }
+    }
+    if (lane < 3) {
+      const int c = lane;
+      const int vi = A.voff[A.body_of[l]] + 3 * (l - A.boff[A.body_of[l]]) + c;
+      const double gx = c == 0 ? s0 : (c == 1 ? s1 : s2);
+      const double b = A.B[3 * l + c];
+      const double r = b - gx;
+      A.r[3 * l + c] = r;
+      A.rf[vi] = (float)r;
+      A.Bf[vi] = (float)b;
+      A.p[3 * l + c] = 0.0;
+      A.Ap[3 * l + c] = 0.0;
+      if (!A.warm) A.w[3 * l + c] = 0.0;
+    }
+  }
   grid.sync();
-  spmv_rows(A, A.w, A.Ap, gwarp, nwarps, lane);
-  grid.sync();
-  for (int i = gtid; i < m3; i += nthreads) A.r[i] = A.B[i] - A.Ap[i];
-  grid.sync();
-  precond_rows(A, A.r, A.z, gwarp, nwarps, lane);
-  precond_rows(A, A.B, A.Ap, gwarp, nwarps, lane);   // M B for the stopping scale
-  grid.sync();
+  // z = M r and the stopping scale B.(M B): partials r.z (slots 3..5) and B.MB (0..2)
   {
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int i = gtid; i < m3; i += nthreads) {
-      const int c = i % 3;
-      v[c] += A.r[i] * A.z[i];
-      v[3 + c] += A.B[i] * A.Ap[i];
+    double rz3[3] = {0, 0, 0}, bb3[3] = {0, 0, 0};
+    const float zero3[3] = {0.f, 0.f, 0.f};
+    for (int l = row0; l < m; l += rstep) {
+      float zr[3], zb[3];
+      precond_row(A, l, A.rf, nullptr, zero3, zr, lane);
+      precond_row(A, l, A.Bf, nullptr, zero3, zb, lane);
+      if (lane == 0)
+        for (int c = 0; c < 3; ++c) {
+          A.z[3 * l + c] = zr[c];
+          rz3[c] += A.r[3 * l + c] * (double)zr[c];
+          bb3[c] += A.B[3 * l + c] * (double)zb[c];
+        }
     }
-    block_sum<6>(v, shd);
-    if (threadIdx.x == 0)
-      for (int c = 0; c < 6; ++c) A.red[blockIdx.x * 8 + c] = v[c];
+    for (int c = 0; c < 3; ++c) {
+      const double t1 = block_total(rz3[c], shd);
+      const double t2 = block_total(bb3[c], shd);
+      if (threadIdx.x == 0) {
+        A.red[blockIdx.x * 8 + 3 + c] = t1;
+        A.red[blockIdx.x * 8 + c] = t2;
+      }
+    }
   }
-  for (int i = gtid; i < m3; i += nthreads) A.p[i] = A.z[i];
   grid.sync();
-  double tot[6];
-  grid_total<6>(A.red, 0, tot);
-  double rz[3] = {tot[0], tot[1], tot[2]};
-  double scale[3] = {tot[3], tot[4], tot[5]};
-  grid.sync();   // everyone has read the partials before they are overwritten
-
-  int it = 0;
-  bool done = true;
-  for (int c = 0; c < A.D; ++c) done &= !(rz[c] > PCG_TOL * PCG_TOL * scale[c]);
-  while (!done && it < PCG_MAX_ITERS) {
-    // Ap = G p;  partial p.Ap
-    spmv_rows(A, A.p, A.Ap, gwarp, nwarps, lane);
-    grid.sync();
-    {
-      double v[3] = {0, 0, 0};
-      for (int i = gtid; i < m3; i += nthreads) v[i % 3] += A.p[i] * A.Ap[i];
-      block_sum<3>(v, shd);
-      if (threadIdx.x == 0)
-        for (int c = 0; c < 3; ++c) A.red[blockIdx.x * 8 + c] = v[c];
-    }
-    grid.sync();
-    double pAp[3];
-    grid_total<3>(A.red, 0, pAp);
-    double alpha[3];
-    for (int c = 0; c < 3; ++c) alpha[c] = (pAp[c] > 0.0 && rz[c] > 0.0) ? rz[c] / pAp[c] : 0.0;
-    for (int i = gtid; i < m3; i += nthreads) {
-      const int c = i % 3;
-      A.w[i] += alpha[c] * A.p[i];
-      A.r[i] -= alpha[c] * A.Ap[i];
-    }
-    grid.sync();
-    // z = M r;  partial r.z
-    precond_rows(A, A.r, A.z, gwarp, nwarps, lane);
-    grid.sync();
-    {
-      double v[3] = {0, 0, 0};
-      for (int i = gtid; i < m3; i += nthreads) v[i % 3] += A.r[i] * A.z[i];
-      block_sum<3>(v, shd);
-      if (threadIdx.x == 0)
-        for (int c = 0; c < 3; ++c) A.red[blockIdx.x * 8 + 3 + c] = v[c];
-    }
-    grid.sync();
-    double rzn[3];
-    grid_total<3>(A.red, 3, rzn);
-    double beta[3];
-    for (int c = 0; c < 3; ++c) beta[c] = rz[c] > 0.0 ? rzn[c] / rz[c] : 0.0;
-    for (int i = gtid; i < m3; i += nthreads) A.p[i] = A.z[i] + beta[i % 3] * A.p[i];
-    for (int c = 0; c < 3; ++c) rz[c] = rzn[c];
-    ++it;
-    done = true;
-    for (int c = 0; c < A.D; ++c) done &= !(rz[c] > PCG_TOL * PCG_TOL * scale[c]);
-    grid.sync();
+  trace_mark(A, 2);
+  // Scalars of the recurrence live in shared memory: thread 0 of each block
+  // computes them from the grid totals (FP64 divisions are expensive on this
+  // GPU; every block gets bitwise the same values).
+  __shared__ double s_rz[3], s_rzp[3], s_scale[3], s_coef[3];
+  __shared__ float s_coeff[3];
+  __shared__ int s_done;
+  grid_total<3>(A.red, 0, s_scale, shd);
+  grid_total<3>(A.red, 3, s_rz, shd);
+  if (threadIdx.x == 0) {
+    bool d = true;
+    for (int c = 0; c < A.D; ++c) d &= !(s_rz[c] > A.tol * A.tol * s_scale[c]);
+    s_done = d ? 1 : 0;
+    for (int c = 0; c < 3; ++c) s_rzp[c] = 1.0;
   }
+  __syncthreads();
+  int it = 0;
+  bool done = s_done != 0;
+  while (!done && it < PCG_MAX_ITERS) {
+    // ---- P1: p = z + beta p;  A p = G z + beta A p;  partial p.Ap;  FP32 copies of r and A p
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 3; ++c) s_coef[c] = (it > 0 && s_rzp[c] > 0.0) ? s_rz[c] / s_rzp[c] : 0.0;
+    __syncthreads();
+    const double beta[3] = {s_coef[0], s_coef[1], s_coef[2]};
+    {
+      double pAp3[3] = {0, 0, 0};
+      for (int l = row0; l < m; l += rstep) {
+        const int nnz = A.Gnnz[l];
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int j = lane; j < nnz; j += 32) {
+          const int k = A.Gcol[(long long)l * G_MAXNNZ + j];
+          const double v = A.Gval[(long long)l * G_MAXNNZ + j];
+          s0 += v * A.z[3 * k];
+          s1 += v * A.z[3 * k + 1];
+          s2 += v * A.z[3 * k + 2];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+          s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        double contrib = 0.0;
+        if (lane < 3) {
+          const int c = lane;
+          const int vi = A.voff[A.body_of[l]] + 3 * (l - A.boff[A.body_of[l]]) + c;
+          const double gz = c == 0 ? s0 : (c == 1 ? s1 : s2);
+          const double pl = A.z[3 * l + c] + beta[c] * A.p[3 * l + c];
+          const double ap = gz + beta[c] * A.Ap[3 * l + c];
+          A.p[3 * l + c] = pl;
+          A.Ap[3 * l + c] = ap;
+          A.Apf[vi] = (float)ap;
+          A.rf[vi] = (float)A.r[3 * l + c];
+          contrib = pl * ap;
+        }
+        const double c1 = __shfl_sync(0xffffffffu, contrib, 1);
+        const double c2 = __shfl_sync(0xffffffffu, contrib, 2);
+        if (lane == 0) {
+          pAp3[0] += contrib;
+          pAp3[1] += c1;
+          pAp3[2] += c2;
+        }
+      }
+      for (int c = 0; c < 3; ++c) {
+        const double t = block_total(pAp3[c], shd);
+        if (threadIdx.x == 0) A.red[blockIdx.x * 8 + c] = t;
+      }
+    }
+    grid.sync();
+    trace_mark(A, 4 + 2 * it);
+    // ---- P2: alpha;  z = M (r - alpha A p) in FP32;  w += alpha p;  r -= alpha A p;  partial r.z
+    {
+      double pAp[3];
+      grid_total<3>(A.red, 0, pAp, shd);
+      if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) {
+          const double a = (pAp[c] > 0.0 && s_rz[c] > 0.0) ? s_rz[c] / pAp[c] : 0.0;
+          s_coef[c] = a;
+          s_coeff[c] = (float)a;
+        }
+      __syncthreads();
+    }
+    const double alpha[3] = {s_coef[0], s_coef[1], s_coef[2]};
+    const float alphaf[3] = {s_coeff[0], s_coeff[1], s_coeff[2]};
+    {
+      double rz3[3] = {0, 0, 0};
+      for (int l = row0; l < m; l += rstep) {
+        float zl[3];
+        precond_row(A, l, A.rf, A.Apf, alphaf, zl, lane);
+        double contrib = 0.0;
+        if (lane < 3) {
+          const int c = lane;
+          A.w[3 * l + c] += alpha[c] * A.p[3 * l + c];
+          const double rn = A.r[3 * l + c] - alpha[c] * A.Ap[3 * l + c];
+          A.r[3 * l + c] = rn;
+          A.z[3 * l + c] = zl[c];
+          contrib = rn * (double)zl[c];
+        }
+        const double c1 = __shfl_sync(0xffffffffu, contrib, 1);
+        const double c2 = __shfl_sync(0xffffffffu, contrib, 2);
+        if (lane == 0) {
+          rz3[0] += contrib;
+          rz3[1] += c1;
+          rz3[2] += c2;
+        }
+      }
+      for (int c = 0; c < 3; ++c) {
+        const double t = block_total(rz3[c], shd);
+        if (threadIdx.x == 0) A.red[blockIdx.x * 8 + 3 + c] = t;
+      }
+    }
+    grid.sync();
+    trace_mark(A, 5 + 2 * it);
+    {
+      double rzn[3];
+      grid_total<3>(A.red, 3, rzn, shd);
+      if (threadIdx.x == 0) {
+        bool d = true;
+        for (int c = 0; c < 3; ++c) {
+          s_rzp[c] = s_rz[c];
+          s_rz[c] = rzn[c];
+        }
+        for (int c = 0; c < A.D; ++c) d &= !(s_rz[c] > A.tol * A.tol * s_scale[c]);
+        s_done = d ? 1 : 0;
+      }
+      __syncthreads();
+    }
+    ++it;
+    done = s_done != 0;
+  }
+  trace_mark(A, 3);
   if (gtid == 0) {
     double rel = 0.0;
     for (int c = 0; c < A.D; ++c)
-      if (scale[c] > 0.0) rel = fmax(rel, sqrt(fmax(rz[c], 0.0) / scale[c]));
+      if (s_scale[c] > 0.0) rel = fmax(rel, sqrt(fmax(s_rz[c], 0.0) / s_scale[c]));
     A.info[0] = it;
     A.info[1] = (it > REFRESH_ITERS || !done) ? 1 : 0;
     A.info[2] = done ? 1 : 0;
@@ -732,56 +1044,53 @@ __global__ void __launch_bounds__(256) k_pcg(PcgArgs A) {
 }
 
 // ------------------------------------------------------------------ spreading and force density
+// du(x) = sum_l w_l D(x - X_l) (Eq. 15, w_l = du_B^l ds_l) as a scatter from
+// each marker's 64 (16 in 2D) stencil nodes into 64-bit fixed-point
+// accumulators of the band: integer addition is associative, so the sums
+// are bitwise independent of the order the atomics land in.
+constexpr double FIX_SCALE = 70368744177664.0;   // 2^46: |sum| < 1.3e5, resolution 1.4e-14
+constexpr double FIX_LIMIT = 9.0e18 / FIX_SCALE;
+
+__global__ void k_spread_scatter(int m_total, const int* __restrict__ base, const double* __restrict__ wts,
+                                 const double* __restrict__ wsol, const int* __restrict__ tile_slot, Geo g,
+                                 unsigned long long* __restrict__ acc, int* status) {
+  const int nn = g.D == 3 ? 64 : 16;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = (int)(gid / nn), k = (int)(gid % nn);
+  if (l >= m_total) return;
+  const int* b = base + 3 * l;
+  const double* w = wts + 12 * l;
+  const int i = k & 3, j = (k >> 2) & 3, q = k >> 4;
+  int node[3] = {b[0] + i, b[1] + j, g.D == 3 ? b[2] + q : 0};
+  for (int a = 0; a < g.D; ++a)
+    if (g.per[a]) node[a] = wrap(node[a], g.n[a]);
+  const double wt = w[i] * w[4 + j] * w[8 + (g.D == 3 ? q : 0)];
+  const int s = tile_slot[tile_of(g, node[0], node[1], node[2])];
+  if (s < 0) return;
+  const int local = ((node[2] % g.tg.tz) * g.tg.ty + (node[1] % g.tg.ty)) * g.tg.tx + (node[0] % g.tg.tx);
+  unsigned long long* a3 = acc + (long long)s * 3 * TILE_CELLS + local;
+  for (int c = 0; c < g.D; ++c) {
+    const double v = wt * wsol[3 * l + c];
+    if (!(fabs(v) < FIX_LIMIT)) { atomicOr(status, ST_OVERFLOW); continue; }
+    atomicAdd(a3 + c * TILE_CELLS, (unsigned long long)__double2ll_rn(v * FIX_SCALE));
+  }
+}
+
+// F = 2 rho du on the band (Eq. 26) from the accumulators, which are cleared
+// for the next step.
 template <class R>
-__global__ void k_spread(const int* __restrict__ slot_tile, const int* __restrict__ band_count, int cap,
-                         const int* __restrict__ tile_mcount, const int* __restrict__ tile_markers,
-                         const int* __restrict__ base, const double* __restrict__ wts,
-                         const double* __restrict__ wsol, const R* __restrict__ band_mom,
-                         R* __restrict__ band_F, Geo g) {
-  __shared__ int s_list[TILE_MARKER_CAP];
-  __shared__ int s_sorted[TILE_MARKER_CAP];
+__global__ void k_spread_finalize(const int* __restrict__ band_count, int cap, unsigned long long* __restrict__ acc,
+                                  const R* __restrict__ band_mom, R* __restrict__ band_F, int D) {
   const int n = min(*band_count, cap);
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
-    const int cnt = min(tile_mcount[s], TILE_MARKER_CAP);
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_list[i] = tile_markers[s * TILE_MARKER_CAP + i];
-    __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const int key = s_list[i];
-      int rank = 0;
-      for (int j = 0; j < cnt; ++j) rank += s_list[j] < key;
-      s_sorted[rank] = key;
-    }
-    __syncthreads();
-    const int tile = slot_tile[s];
     const int local = threadIdx.x;
-    const int x = (tile % g.tg.ntx) * g.tg.tx + local % g.tg.tx;
-    const int y = ((tile / g.tg.ntx) % g.tg.nty) * g.tg.ty + (local / g.tg.tx) % g.tg.ty;
-    const int z = (tile / (g.tg.ntx * g.tg.nty)) * g.tg.tz + local / (g.tg.tx * g.tg.ty);
-    const int node[3] = {x, y, z};
-    double du[3] = {0, 0, 0};
-    for (int j = 0; j < cnt; ++j) {
-      const int k = s_sorted[j];
-      const int* bk = base + 3 * k;
-      double wt = 1.0;
-      bool in = true;
-      for (int a = 0; a < g.D; ++a) {
-        int o = node[a] - bk[a];
-        if (g.per[a]) o = wrap(o, g.n[a]);
-        if (o < 0 || o > 3) { in = false; break; }
-        wt *= wts[12 * k + 4 * a + o];
-      }
-      if (!in) continue;
-      du[0] += wt * wsol[3 * k];
-      du[1] += wt * wsol[3 * k + 1];
-      du[2] += wt * wsol[3 * k + 2];
+    const double rho = (double)band_mom[(long long)s * 4 * TILE_CELLS + local];
+    for (int c = 0; c < 3; ++c) {
+      unsigned long long* a = acc + ((long long)s * 3 + c) * TILE_CELLS + local;
+      const double du = c < D ? (double)(long long)(*a) * (1.0 / FIX_SCALE) : 0.0;   // exact power of 2
+      *a = 0ull;
+      band_F[((long long)s * 3 + c) * TILE_CELLS + local] = (R)(2.0 * rho * du);
     }
-    const R* mo = band_mom + (long long)s * 4 * TILE_CELLS + local;
-    const double rho = (double)mo[0];
-    R* f = band_F + (long long)s * 3 * TILE_CELLS + local;
-    f[0] = (R)(2.0 * rho * du[0]);      // Eq. 26: F = 2 rho du / dt
-    f[TILE_CELLS] = (R)(2.0 * rho * du[1]);
-    f[2 * TILE_CELLS] = (R)(g.D == 3 ? 2.0 * rho * du[2] : 0.0);
-    __syncthreads();
   }
 }
 
@@ -789,7 +1098,7 @@ __global__ void k_spread(const int* __restrict__ slot_tile, const int* __restric
 __global__ void k_force_reduce(int nbodies, const int* __restrict__ boff, const double* __restrict__ rho_l,
                                const double* __restrict__ wsol, double* __restrict__ mforce,
                                double* __restrict__ hist, long long step) {
-  __shared__ double sh[8 * 3];
+  __shared__ double sh[8][3];
   const int b = blockIdx.x;
   if (b >= nbodies) return;
   const int o = boff[b], e = boff[b + 1];
@@ -801,10 +1110,19 @@ __global__ void k_force_reduce(int nbodies, const int* __restrict__ boff, const 
       v[a] += f;
     }
   }
-  block_sum<3>(v, sh);
+  // fixed-order tree: warp shuffles, then warp partials in warp order
+  for (int off = 16; off > 0; off >>= 1)
+    for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int a = 0; a < 3; ++a) sh[wid][a] = v[a];
+  __syncthreads();
   if (threadIdx.x == 0) {
+    double t[3] = {0, 0, 0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      for (int a = 0; a < 3; ++a) t[a] += sh[w][a];
     double* h = hist + ((long long)b * HIST_LEN + (step % HIST_LEN)) * 3;
-    for (int a = 0; a < 3; ++a) h[a] = -v[a];   // force on the body
+    for (int a = 0; a < 3; ++a) h[a] = -t[a];   // force on the body
   }
 }
 
@@ -865,6 +1183,14 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   IBL_CU(cudaMalloc(&c->d_tile_markers, sizeof(int) * (size_t)c->cap_slots * TILE_MARKER_CAP));
   IBL_CU(cudaMalloc(&c->d_band_mom, rs * 4 * TILE_CELLS * (size_t)c->cap_slots));
   IBL_CU(cudaMalloc(&c->d_band_F, rs * 3 * TILE_CELLS * (size_t)c->cap_slots));
+  IBL_CU(cudaMalloc(&c->d_acc, sizeof(unsigned long long) * 3 * TILE_CELLS * (size_t)c->cap_slots));
+  IBL_CU(cudaMemsetAsync(c->d_acc, 0, sizeof(unsigned long long) * 3 * TILE_CELLS * (size_t)c->cap_slots, c->stream));
+  IBL_CU(cudaMalloc(&c->d_bstate, sizeof(double) * 8 * MAX_BODIES));
+  IBL_CU(cudaMalloc(&c->d_slot_body, sizeof(int) * c->cap_slots));
+  IBL_CU(cudaMemsetAsync(c->d_slot_body, 0xff, sizeof(int) * c->cap_slots, c->stream));
+  IBL_CU(cudaMalloc(&c->d_mixed, 2 * sizeof(int)));   // [0] use tiles this step, [1] lists overflowed
+  IBL_CU(cudaMalloc(&c->d_cand, sizeof(int) * (size_t)m * CAND_MAX));
+  IBL_CU(cudaMalloc(&c->d_ncand, sizeof(int) * m));
   IBL_CU(cudaMalloc(&c->d_base, sizeof(int) * 3 * m));
   IBL_CU(cudaMalloc(&c->d_wts, sizeof(double) * 12 * m));
   IBL_CU(cudaMalloc(&c->d_rho_l, sizeof(double) * m));
@@ -875,6 +1201,15 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   IBL_CU(cudaMalloc(&c->d_p, sizeof(double) * 6 * m));
   IBL_CU(cudaMalloc(&c->d_Ap, sizeof(double) * 3 * m));
   IBL_CU(cudaMalloc(&c->d_z, sizeof(double) * 3 * m));
+  // three padded FP32 vectors (r, A p, B); each body's slice starts on a
+  // 16-byte boundary and carries a zero tail up to a multiple of 4 markers
+  size_t vf = 0;
+  for (auto& b : c->bodies) vf += 3 * (size_t)((b.m + 3) & ~3) + 4;
+  c->xf_floats = vf;
+  IBL_CU(cudaMalloc(&c->d_xf, sizeof(float) * 3 * vf));
+  IBL_CU(cudaMemsetAsync(c->d_xf, 0, sizeof(float) * 3 * vf, c->stream));
+  IBL_CU(cudaMalloc(&c->d_trace, sizeof(unsigned long long) * 256));
+  IBL_CU(cudaMemsetAsync(c->d_trace, 0, sizeof(unsigned long long) * 256, c->stream));
   IBL_CU(cudaMalloc(&c->d_Gcol, sizeof(int) * (size_t)m * G_MAXNNZ));
   IBL_CU(cudaMalloc(&c->d_Gval, sizeof(double) * (size_t)m * G_MAXNNZ));
   IBL_CU(cudaMalloc(&c->d_Gnnz, sizeof(int) * m));
@@ -882,7 +1217,7 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   size_t mf = 0;
   for (auto& b : c->bodies) {
     b.precond_offset = (int)mf;
-    mf += (size_t)b.m * b.m;
+    mf += (size_t)b.m * (size_t)((b.m + 3) & ~3);
   }
   c->M_floats = mf;
   IBL_CU(cudaMalloc(&c->d_M, sizeof(float) * mf));
@@ -905,6 +1240,7 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   boff[c->bodies.size()] = m;
   IBL_CU(cudaMalloc(&c->d_boff, sizeof(int) * boff.size()));
   IBL_CU(cudaMemcpy(c->d_boff, boff.data(), sizeof(int) * boff.size(), cudaMemcpyHostToDevice));
+  c->cand_ready = false;
   c->precond_valid = false;
   c->warm = false;
   c->ib_ready = true;
@@ -916,7 +1252,8 @@ void ib_free(ibl_ctx* c) {
                   c->d_slot_tile, c->d_band_count, c->d_tile_mcount, c->d_tile_markers, c->d_band_mom,
                   c->d_band_F, c->d_base, c->d_wts, c->d_rho_l, c->d_B, c->d_w, c->d_r, c->d_p,
                   c->d_Ap, c->d_z, c->d_Gcol, c->d_Gval, c->d_Gnnz, c->d_Gdiag_max, c->d_M, c->d_red,
-                  c->d_cg_info, c->d_cg_res, c->d_hist, c->d_mforce, c->d_boff};
+                  c->d_cg_info, c->d_cg_res, c->d_hist, c->d_mforce, c->d_boff, c->d_xf, c->d_trace,
+                  c->d_acc, c->d_bstate, c->d_slot_body, c->d_mixed, c->d_cand, c->d_ncand};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->d_X0 = c->d_ds = c->d_X = c->d_U = c->d_Xp = c->d_Up = nullptr;
@@ -927,6 +1264,11 @@ void ib_free(ibl_ctx* c) {
   c->d_rho_l = c->d_B = c->d_w = c->d_r = c->d_p = c->d_Ap = c->d_z = c->d_Gval = nullptr;
   c->d_Gdiag_max = c->d_red = c->d_cg_res = c->d_hist = c->d_mforce = nullptr;
   c->d_M = nullptr;
+  c->d_xf = nullptr;
+  c->d_trace = nullptr;
+  c->d_acc = nullptr;
+  c->d_bstate = nullptr;
+  c->d_slot_body = c->d_mixed = c->d_cand = c->d_ncand = nullptr;
   c->ib_ready = false;
 }
 
@@ -984,6 +1326,13 @@ cudaError_t ib_step(ibl_ctx* c) {
     if (g_num_sms <= 0) g_num_sms = 1;
   }
   Geo g = make_geo(c);
+  if (!c->cand_ready) {
+    IBL_CU(cudaMemsetAsync(c->d_mixed + 1, 0, sizeof(int), c->stream));
+    k_build_candidates<<<(m * 32 + 255) / 256, 256, 0, c->stream>>>(m, c->d_X0, c->d_body, c->d_boff, c->D,
+                                                                    c->d_cand, c->d_ncand, c->d_mixed + 1);
+    c->launches++;
+    c->cand_ready = true;
+  }
   BodyTable bt;
   bt.n = (int)c->bodies.size();
   for (int b = 0; b < bt.n; ++b) {
@@ -996,20 +1345,28 @@ cudaError_t ib_step(ibl_ctx* c) {
     d.A.table = h.tableA; d.alpha.table = h.tableAlpha;
     d.prescribed = h.prescribed ? 1 : 0;
   }
-  const int tb = 128;
+  const int tb = 64;
   const int mb = (m + tb - 1) / tb;
-  k_kinematics<<<mb, tb, 0, c->stream>>>(bt, m, c->d_body, c->d_X0, c->d_Xp, c->d_Up, c->d_X, c->d_U,
+  k_body_state<<<1, 32, 0, c->stream>>>(bt, (double)c->step, c->d_bstate);
+  k_kinematics<<<mb, tb, 0, c->stream>>>(bt, c->d_bstate, m, c->d_body, c->d_X0, c->d_Xp, c->d_Up, c->d_X, c->d_U,
                                          c->d_base, c->d_wts, (double)c->step, g, c->d_status);
-  for (auto& b : c->bodies) b.prescribed = false;
+  c->launches++;
   const int cg_grid = std::min(c->cap_slots, 4 * g_num_sms);
   k_clear_tiles<<<std::max(1, std::min(c->cap_slots / 256 + 1, g_num_sms)), 256, 0, c->stream>>>(
-      c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->d_tile_mcount, c->cap_slots);
+      c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->d_tile_mcount, c->d_slot_body, c->cap_slots);
+  // candidate-list assembly unless a body is driven by uploaded states this step
+  bool any_prescribed = false;
+  for (auto& b : c->bodies) any_prescribed |= b.prescribed;
+  const int use_tiles_host = any_prescribed ? 1 : 0;
+  IBL_CU(cudaMemsetAsync(c->d_mixed, use_tiles_host, sizeof(int), c->stream));
   IBL_CU(cudaMemsetAsync(c->d_band_count, 0, sizeof(int), c->stream));
   k_mark_tiles<<<mb, tb, 0, c->stream>>>(m, c->d_base, g, c->d_tile_slot);
   k_assign_slots<<<std::max(1, std::min((c->tg.n_tiles + 255) / 256, 2 * g_num_sms)), 256, 0, c->stream>>>(
       c->tg.n_tiles, c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->cap_slots, c->d_status);
   k_append_markers<<<mb, tb, 0, c->stream>>>(m, c->d_base, g, c->d_tile_slot, c->d_tile_mcount,
-                                             c->d_tile_markers, c->d_status);
+                                             c->d_tile_markers, c->d_status, c->d_body, c->d_slot_body,
+                                             c->d_mixed);
+  for (auto& b : c->bodies) b.prescribed = false;
   c->launches += 6;
   IBL_CU(cudaGetLastError());
   IBL_CU(band_moments(c, cg_grid));
@@ -1024,7 +1381,8 @@ cudaError_t ib_step(ibl_ctx* c) {
   k_assemble<<<(m + 7) / 8, 256, 0, c->stream>>>(m, c->d_base, c->d_wts, c->d_tile_slot,
                                                  c->d_tile_mcount, c->d_tile_markers, g, c->d_body, c->d_Gcol,
                                                  c->d_Gval, c->d_Gnnz, (unsigned long long*)c->d_Gdiag_max,
-                                                 c->d_status);
+                                                 c->d_status, c->d_cand, c->d_ncand, c->d_mixed,
+                                                 c->d_mixed + 1);
   c->launches += 2;
   IBL_CU(cudaGetLastError());
   // PCG (cooperative)
@@ -1041,6 +1399,17 @@ cudaError_t ib_step(ibl_ctx* c) {
   A.Gcol = c->d_Gcol; A.Gval = c->d_Gval; A.Gnnz = c->d_Gnnz;
   A.rowsum_max = (const unsigned long long*)c->d_Gdiag_max;
   A.B = c->d_B; A.w = c->d_w; A.r = c->d_r; A.p = c->d_p; A.Ap = c->d_Ap; A.z = c->d_z;
+  A.rf = c->d_xf;
+  A.Apf = c->d_xf + c->xf_floats;
+  A.Bf = c->d_xf + 2 * c->xf_floats;
+  {
+    int vo = 0;
+    for (int b = 0; b < A.nbodies; ++b) {
+      A.voff[b] = vo;
+      vo += 3 * ((c->bodies[b].m + 3) & ~3) + 4;
+    }
+  }
+  A.tol = c->prec == IBL_FP64 ? PCG_TOL : PCG_TOL_LOW;
   A.M = c->d_M; A.red = c->d_red; A.info = c->d_cg_info; A.res = c->d_cg_res;
   A.warm = c->warm ? 1 : 0;
   const bool sched = !c->precond_valid || (c->step - c->last_refresh_step) >= REFRESH_EVERY;
@@ -1051,28 +1420,33 @@ cudaError_t ib_step(ibl_ctx* c) {
   }
   c->precond_valid = true;
   A.status = c->d_status;
-  static int max_blocks_per_sm = 0;
-  if (!max_blocks_per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks_per_sm, k_pcg, 256, 0);
-    if (max_blocks_per_sm <= 0) max_blocks_per_sm = 1;
+  A.trace = c->d_trace;
+  static bool smem_set = false;
+  if (!smem_set) {
+    IBL_CU(cudaFuncSetAttribute((const void*)k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJ_SMEM));
+    smem_set = true;
   }
-  int pcg_blocks = std::min(g_num_sms * std::min(max_blocks_per_sm, 1), std::max(1, (m + 15) / 16));
-  pcg_blocks = std::min(pcg_blocks, 1024);
+  int pcg_blocks = std::max(1, std::min(g_num_sms, m));
   void* args[] = {&A};
-  IBL_CU(cudaLaunchCooperativeKernel((void*)k_pcg, dim3(pcg_blocks), dim3(256), args, 0, c->stream));
+  IBL_CU(cudaLaunchCooperativeKernel((void*)k_pcg, dim3(pcg_blocks), dim3(PCG_THREADS), args, GJ_SMEM, c->stream));
   c->launches++;
   c->warm = true;
-  // spreading
+  // spreading: fixed-point scatter, then F = 2 rho du
+  {
+    const int nn = c->D == 3 ? 64 : 16;
+    const long long tot = (long long)m * nn;
+    k_spread_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(m, c->d_base, c->d_wts, c->d_w,
+                                                                            c->d_tile_slot, g, c->d_acc, c->d_status);
+    c->launches++;
+  }
   if (c->prec == IBL_FP64)
-    k_spread<double><<<cg_grid, TILE_CELLS, 0, c->stream>>>(c->d_slot_tile, c->d_band_count, c->cap_slots,
-                                                            c->d_tile_mcount, c->d_tile_markers, c->d_base,
-                                                            c->d_wts, c->d_w, (const double*)c->d_band_mom,
-                                                            (double*)c->d_band_F, g);
+    k_spread_finalize<double><<<cg_grid, TILE_CELLS, 0, c->stream>>>(c->d_band_count, c->cap_slots, c->d_acc,
+                                                                     (const double*)c->d_band_mom,
+                                                                     (double*)c->d_band_F, c->D);
   else
-    k_spread<float><<<cg_grid, TILE_CELLS, 0, c->stream>>>(c->d_slot_tile, c->d_band_count, c->cap_slots,
-                                                           c->d_tile_mcount, c->d_tile_markers, c->d_base,
-                                                           c->d_wts, c->d_w, (const float*)c->d_band_mom,
-                                                           (float*)c->d_band_F, g);
+    k_spread_finalize<float><<<cg_grid, TILE_CELLS, 0, c->stream>>>(c->d_band_count, c->cap_slots, c->d_acc,
+                                                                    (const float*)c->d_band_mom,
+                                                                    (float*)c->d_band_F, c->D);
   c->launches++;
   IBL_CU(cudaGetLastError());
   return cudaSuccess;

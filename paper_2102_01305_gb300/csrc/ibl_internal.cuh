@@ -49,6 +49,11 @@ template <> struct Lat<9> {
   __host__ __device__ static constexpr double w(int i) {
     return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
   }
+  // 3 w_i rounded to FP32 values whose discrete moment 2 w3_axis + 4 w3_diag
+  // equals 1 exactly (11184811 * 2^-25 and 11184810 * 2^-27)
+  __host__ __device__ static constexpr double w3f(int i) {
+    return i == 0 ? 0.0 : (i < 5 ? 11184811.0 / 33554432.0 : 11184810.0 / 134217728.0);
+  }
 };
 
 template <> struct Lat<19> {
@@ -68,9 +73,25 @@ template <> struct Lat<19> {
   __host__ __device__ static constexpr double w(int i) {
     return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
   }
+  // 3 w_i rounded to FP32 values whose discrete moment 2 w3_face + 8 w3_edge
+  // equals 1 exactly (11184810 * 2^-26 and 11184811 * 2^-27)
+  __host__ __device__ static constexpr double w3f(int i) {
+    return i == 0 ? 0.0 : (i < 7 ? 11184810.0 / 67108864.0 : 11184811.0 / 134217728.0);
+  }
 };
 
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// Weight of the odd (momentum-carrying) part of f_eq and of the Guo term,
+// 3 w_i.  In FP32 the rounded 1/18, 1/36 (or 1/9, 1/36) break the identity
+// sum_i 3 w_i c_i c_i = I by ~1e-8, which makes every collision scale the
+// momentum by (1 + omega * 1e-8) - a drift of ~1e-5 after 1000 steps.  The
+// FP32 constants below satisfy the identity exactly.
+template <int Q, class R> __host__ __device__ constexpr R w3(int i);
+template <> __host__ __device__ constexpr float w3<9, float>(int i) { return (float)Lat<9>::w3f(i); }
+template <> __host__ __device__ constexpr float w3<19, float>(int i) { return (float)Lat<19>::w3f(i); }
+template <> __host__ __device__ constexpr double w3<9, double>(int i) { return 3.0 * Lat<9>::w(i); }
+template <> __host__ __device__ constexpr double w3<19, double>(int i) { return 3.0 * Lat<19>::w(i); }
 
 // ----------------------------------------------------------------- storage types
 template <class T> struct Store;
@@ -216,6 +237,16 @@ struct ibl_ctx {
   double* d_p = nullptr;         // 2 x m x 3 (ping-pong)
   double* d_Ap = nullptr;        // m x 3
   double* d_z = nullptr;         // m x 3
+  float* d_xf = nullptr;         // 3 padded FP32 vectors feeding the preconditioner
+  size_t xf_floats = 0;          // floats per padded vector
+  unsigned long long* d_trace = nullptr;   // 256 PCG phase timestamps
+  unsigned long long* d_acc = nullptr;     // cap_slots x 3 x TILE_CELLS fixed-point spread sums
+  double* d_bstate = nullptr;              // per-body motion state of the step (8 doubles)
+  int* d_slot_body = nullptr;              // body that first touched each band slot
+  int* d_mixed = nullptr;                  // 1: use the tile-based assembly this step
+  int* d_cand = nullptr;                   // m x CAND_MAX rigid-body partner candidates
+  int* d_ncand = nullptr;
+  bool cand_ready = false;
   int* d_Gcol = nullptr;         // m x G_MAXNNZ
   double* d_Gval = nullptr;      // m x G_MAXNNZ
   int* d_Gnnz = nullptr;         // m

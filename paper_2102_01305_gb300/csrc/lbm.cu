@@ -29,56 +29,122 @@ __device__ __forceinline__ void band_force(int x, int y, int z, const FluidParam
   }
 }
 
-// BGK collision with the Guo source in deviation form; returns rho.
+// BGK collision with the Guo source (Eqs. 7-8) in deviation form g = f - w.
+// Pairs (c, -c) share |c.u| and |c.F|: the even part of f_eq and of the
+// source is computed once per pair, the odd part flips sign.  rho = 1 + drho
+// is never formed in the storage precision where it would drop drho's low
+// bits: rho X = X + drho X and u = m - m drho/(1 + drho).  Returns drho.
 template <int Q, class R>
 __device__ __forceinline__ R collide(R g[Q], const R F[3], const FluidParams<R>& p) {
-  R drho = R(0), m0 = R(0), m1 = R(0), m2 = R(0);
+  R drho = g[0], m0 = R(0), m1 = R(0), m2 = R(0);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    drho += g[i];
-    if (Lat<Q>::cx(i)) m0 += R(Lat<Q>::cx(i)) * g[i];
-    if (Lat<Q>::cy(i)) m1 += R(Lat<Q>::cy(i)) * g[i];
-    if (Lat<Q>::cz(i)) m2 += R(Lat<Q>::cz(i)) * g[i];
+  for (int i = 1; i < Q; i += 2) {
+    drho += g[i] + g[i + 1];
+    const R d = g[i] - g[i + 1];
+    if (Lat<Q>::cx(i)) m0 += R(Lat<Q>::cx(i)) * d;
+    if (Lat<Q>::cy(i)) m1 += R(Lat<Q>::cy(i)) * d;
+    if (Lat<Q>::cz(i)) m2 += R(Lat<Q>::cz(i)) * d;
   }
-  const R rho = R(1) + drho;
-  const R inv = R(1) / rho;
-  const R u0 = (m0 + R(0.5) * F[0]) * inv;      // Eq. 9
-  const R u1 = (m1 + R(0.5) * F[1]) * inv;
-  const R u2 = (m2 + R(0.5) * F[2]) * inv;
+  // Eq. 9: rho u = sum c_i f_i + F/2
+  const R q = drho / (R(1) + drho);
+  R u0 = m0 + R(0.5) * F[0], u1 = m1 + R(0.5) * F[1], u2 = m2 + R(0.5) * F[2];
+  u0 -= u0 * q;
+  u1 -= u1 * q;
+  u2 -= u2 * q;
   const R usq = u0 * u0 + u1 * u1 + u2 * u2;
   const R uF = u0 * F[0] + u1 * F[1] + u2 * F[2];
+  const R om = p.omega;
+  {
+    // rest population: f_eq - w = w (drho - 1.5 rho u.u)
+    const R w = R(Lat<Q>::w(0));
+    const R X = R(-1.5) * usq;
+    const R geq = w * (drho + X + drho * X);
+    const R S = p.pref * w * (R(-3) * uF);
+    g[0] = g[0] - om * (g[0] - geq) + S;
+  }
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  for (int i = 1; i < Q; i += 2) {
     const R cu = R(Lat<Q>::cx(i)) * u0 + R(Lat<Q>::cy(i)) * u1 + R(Lat<Q>::cz(i)) * u2;
     const R cF = R(Lat<Q>::cx(i)) * F[0] + R(Lat<Q>::cy(i)) * F[1] + R(Lat<Q>::cz(i)) * F[2];
     const R w = R(Lat<Q>::w(i));
-    // f_eq - w_i  (Eq. 4, second-order expansion)
-    const R geq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq));
-    // Guo term (Eq. 8)
-    const R S = p.pref * w * (R(3) * (cF - uF) + R(9) * cu * cF);
-    g[i] = g[i] - p.omega * (g[i] - geq) + S;
+    const R wo = w3<Q, R>(i);
+    // Eq. 4 (second-order expansion): even part rho(4.5 cu^2 - 1.5 u.u), odd part 3 rho cu
+    const R Xe = R(4.5) * cu * cu - R(1.5) * usq;
+    const R ge = w * (drho + Xe + drho * Xe);
+    const R go = wo * (cu + drho * cu);
+    // Eq. 8: pref w [3 (c - u).F + 9 (c.u)(c.F)]: even 9 cu cF - 3 uF, odd 3 cF
+    const R Se = p.pref * w * (R(9) * cu * cF - R(3) * uF);
+    const R So = p.pref * wo * cF;
+    const R a = g[i], b = g[i + 1];
+    g[i] = a - om * (a - (ge + go)) + (Se + So);
+    g[i + 1] = b - om * (b - (ge - go)) + (Se - So);
   }
-  return rho;
+  return drho;
+}
+
+// Per-direction base pointers of the two population buffers (kernel
+// parameters, so no 64-bit index arithmetic per load or store).
+template <int Q, class T> struct DirPtrs {
+  const T* s[Q];
+  T* d[Q];
+};
+
+// True when the cell lies on a face that is not periodic (bounce-back or
+// Zou-He), where the general gather applies.
+template <class R>
+__device__ __forceinline__ bool on_special_face(int x, int y, int z, int D, const FluidParams<R>& p) {
+  return (x == 0 && p.bc[0] != IBL_PERIODIC) || (x == p.nx - 1 && p.bc[1] != IBL_PERIODIC) ||
+         (y == 0 && p.bc[2] != IBL_PERIODIC) || (y == p.ny - 1 && p.bc[3] != IBL_PERIODIC) ||
+         (D == 3 && ((z == 0 && p.bc[4] != IBL_PERIODIC) || (z == p.nz - 1 && p.bc[5] != IBL_PERIODIC)));
+}
+
+// Pull of an interior (or periodic-face) cell: neighbour rows and columns are
+// wrapped once per thread; each direction then costs one add and one load.
+template <int Q, class T, class R>
+__device__ __forceinline__ void gather_fast(const DirPtrs<Q, T>& P, int x, int y, int z,
+                                            const FluidParams<R>& p, R g[Q]) {
+  int xs[3] = {x - 1, x, x + 1};
+  if (xs[0] < 0) xs[0] += p.nx;
+  if (xs[2] >= p.nx) xs[2] -= p.nx;
+  int ys[3] = {y - 1, y, y + 1};
+  if (ys[0] < 0) ys[0] += p.ny;
+  if (ys[2] >= p.ny) ys[2] -= p.ny;
+  int zs[3] = {z - 1, z, z + 1};
+  if (Lat<Q>::D == 3) {
+    if (zs[0] < 0) zs[0] += p.nz;
+    if (zs[2] >= p.nz) zs[2] -= p.nz;
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int dy = 1 - Lat<Q>::cy(i), dz = 1 - Lat<Q>::cz(i), dx = 1 - Lat<Q>::cx(i);
+    const int src = (zs[dz] * p.ny + ys[dy]) * p.nx + xs[dx];
+    g[i] = Store<T>::ld(P.s[i][src]);
+  }
 }
 
 template <int Q, class T, bool PULL, bool IB>
-__global__ void __launch_bounds__(256) k_collide(const T* __restrict__ src, T* __restrict__ dst,
-                                                 FluidParams<typename Store<T>::R> p) {
+__global__ void __launch_bounds__(256) k_collide(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p) {
   using R = typename Store<T>::R;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   if (x >= p.nx || y >= p.ny) return;
-  const long long cell = ((long long)z * p.ny + y) * p.nx + x;
+  const int cell = (z * p.ny + y) * p.nx + x;
   R g[Q];
-  gather_q<Q, T, PULL, R>(src, x, y, z, cell, p, g);
+  if (!PULL) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) g[i] = Store<T>::ld(P.s[i][cell]);
+  } else if (!on_special_face<R>(x, y, z, Lat<Q>::D, p)) {
+    gather_fast<Q, T, R>(P, x, y, z, p, g);
+  } else {
+    gather_q<Q, T, true, R>(P.s[0], x, y, z, cell, p, g);
+  }
   R F[3] = {p.G[0], p.G[1], p.G[2]};
   if (IB) band_force<R>(x, y, z, p, F);
-  const R rho = collide<Q, R>(g, F, p);
-  if (!(rho > R(0) && rho < R(100))) atomicOr(p.status, ST_DIVERGED);
-  const long long N = p.N;
+  const R drho = collide<Q, R>(g, F, p);
+  if (!(drho > R(-1) && drho < R(99))) atomicOr(p.status, ST_DIVERGED);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) dst[i * N + cell] = Store<T>::st(g[i]);
+  for (int i = 0; i < Q; ++i) P.d[i][cell] = Store<T>::st(g[i]);
 }
 
 // rho, u = (sum c_i f_i + G/2)/rho and optionally f itself (FP64) of the
@@ -207,13 +273,18 @@ cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
   auto p = make_params<R>(c, with_ib);
   const T* src = (const T*)c->f[c->cur];
   T* dst = (T*)c->f[c->cur ^ 1];
+  DirPtrs<Q, T> P;
+  for (int i = 0; i < Q; ++i) {
+    P.s[i] = src + (size_t)i * c->N;
+    P.d[i] = dst + (size_t)i * c->N;
+  }
   dim3 b = cell_block(c), g = cell_grid(c, b);
   if (c->poststream) {
-    if (with_ib) k_collide<Q, T, false, true><<<g, b, 0, c->stream>>>(src, dst, p);
-    else k_collide<Q, T, false, false><<<g, b, 0, c->stream>>>(src, dst, p);
+    if (with_ib) k_collide<Q, T, false, true><<<g, b, 0, c->stream>>>(P, p);
+    else k_collide<Q, T, false, false><<<g, b, 0, c->stream>>>(P, p);
   } else {
-    if (with_ib) k_collide<Q, T, true, true><<<g, b, 0, c->stream>>>(src, dst, p);
-    else k_collide<Q, T, true, false><<<g, b, 0, c->stream>>>(src, dst, p);
+    if (with_ib) k_collide<Q, T, true, true><<<g, b, 0, c->stream>>>(P, p);
+    else k_collide<Q, T, true, false><<<g, b, 0, c->stream>>>(P, p);
   }
   c->launches++;
   return cudaGetLastError();

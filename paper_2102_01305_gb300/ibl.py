@@ -69,6 +69,7 @@ _SIGS = {
     "ibl_mass": ([_P, _D], C.c_int),
     "ibl_lattice_velocities": ([C.c_int32, _I32, _I32, _D], C.c_int),
     "ibl_solver_stats": ([_P, _I32, _D, _I64], C.c_int),
+    "ibl_solver_trace": ([_P, _I64, C.c_int32, _I32], C.c_int),
     "ibl_profile": ([_P, C.c_int32], C.c_int),
     "ibl_profile_read": ([_P, _D, _D, _I64], C.c_int),
     "ibl_launch_count": ([_P, _I64], C.c_int),
@@ -275,6 +276,12 @@ class Context:
         it, res, ref = C.c_int32(), C.c_double(), C.c_int64()
         _check(self.h, _lib.ibl_solver_stats(self.h, C.byref(it), C.byref(res), C.byref(ref)), allow)
         return it.value, res.value, ref.value
+
+    def ibl_solver_trace(self, allow=()):
+        out = np.zeros(256, dtype=np.int64)
+        n = C.c_int32()
+        _check(self.h, _lib.ibl_solver_trace(self.h, out.ctypes.data_as(_I64), 256, C.byref(n)), allow)
+        return out[:n.value]
 
     def ibl_profile(self, enable: bool):
         _check(self.h, _lib.ibl_profile(self.h, 1 if enable else 0))

@@ -14,11 +14,15 @@ pytestmark = pytest.mark.gpu
 
 
 def _coef_err(ctx, sim, body, steps):
+    """Errors of the C_L and C_T histories relative to the body's force scale
+    max(|C_L|, |C_T|) over the run (a symmetric body has C_L = 0 up to rounding,
+    so a C_L-relative error would compare rounding noise with rounding noise)."""
     hist = ctx.ibl_force_history(body, steps)
     ref = np.array(sim.history[body][-len(hist):])
     assert len(hist) == min(steps, len(sim.history[body]))
-    e_l = rel_err(hist[:, 0], ref[:, 0])
-    e_t = rel_err(hist[:, 1], ref[:, 1])
+    scale = max(np.abs(ref[:, 0]).max(), np.abs(ref[:, 1]).max())
+    e_l = np.abs(hist[:, 0] - ref[:, 0]).max() / scale
+    e_t = np.abs(hist[:, 1] - ref[:, 1]).max() / scale
     return e_l, e_t
 
 
@@ -109,11 +113,14 @@ def test_no_slip_and_force_balance_on_gpu(ibl):
     ctx.ibl_step(30)
     F = ctx.ibl_get_field(ibl.IBL_FIELD_FORCE)
     lag = np.zeros(3)
+    mag = 0.0
     for b in range(2):
         m = len(cfg["bodies"][b]["ds"])
         _, _, Fm = ctx.ibl_get_markers(b, m)
         lag += Fm.sum(0)
-    assert np.allclose(lag, F.reshape(3, -1).sum(1), rtol=1e-9, atol=1e-15)
+        mag += np.abs(Fm).sum()
+    # the sums cancel to ~1e-13 in y and z: compare against the summed magnitude
+    assert np.abs(lag - F.reshape(3, -1).sum(1)).max() < 1e-12 * mag
     del ib
 
 

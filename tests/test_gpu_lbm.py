@@ -21,13 +21,25 @@ def _tgv(n=(40, 36, 34), precision="fp32", tau=0.6, u0=0.05):
 
 
 def test_tgv3d_fp32_1000_steps(ibl):
-    cfg = _tgv()
+    """1000 steps at tau = 0.52: the vortex keeps ~3/4 of its amplitude, so the
+    field-relative bound measures the arithmetic, not the decay."""
+    cfg = _tgv(tau=0.52)
     ctx = ibl.from_workload(cfg)
     sim = oracle_from_workload(cfg)
     ctx.ibl_step(1000)
     sim.step(1000)
     eu, er = compare_fields(ctx, sim, ibl, TOL_FIELD_FP32, 1e-6)
     print(f"TGV FP32 1000 steps: u {eu:.2e} rho {er:.2e}")
+
+
+def test_tgv3d_fp32_roofline_config(ibl):
+    """The roofline-sweep parameters (u0 = 0.05, tau = 0.6) over 300 steps."""
+    cfg = _tgv()
+    ctx = ibl.from_workload(cfg)
+    sim = oracle_from_workload(cfg)
+    ctx.ibl_step(300)
+    sim.step(300)
+    compare_fields(ctx, sim, ibl, TOL_FIELD_FP32, 1e-6)
 
 
 def test_tgv3d_fp64_exact(ibl):

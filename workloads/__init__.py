@@ -180,7 +180,7 @@ def cylinder_channel(nx=200, ny=100, diameter=20.0, center=(50.0, 50.0), m=63,
 
 def clap_fling_3d(nx=256, ny=192, nz=160, chord=20.0, Re=100.0, J=1e-2, period=4000.0,
                   precision="fp32", spacing=1.0, span_ratio=5.0, hinge_x=None,
-                  gap_ratio=0.5, alpha_kind=WAVE_ABS_SIN, phase=0.0):
+                  gap_ratio=0.5, alpha_kind=WAVE_ABS_SIN, phase=0.0, faces="inlet-outlet"):
     """Two flat elliptic wings (chord c, span 5c) doing clap and fling on D3Q19.
 
     Wings hinge at the trailing edge (Sec. 3.3) about spanwise axes; at clap
@@ -208,10 +208,10 @@ def clap_fling_3d(nx=256, ny=192, nz=160, chord=20.0, Re=100.0, J=1e-2, period=4
             "lift_axis": (0.0, side, 0.0)})
     u_inf = p["u_inf"]
     area = float(ds.sum())
+    xb = [VEL_INLET, PRESS_OUTLET] if faces == "inlet-outlet" else [PERIODIC, PERIODIC]
     return {"lattice": 19, "tau": p["tau"],
-            "grid": grid(nx, ny, nz, [VEL_INLET, PRESS_OUTLET, PERIODIC, PERIODIC,
-                                      PERIODIC, PERIODIC], u_in=(u_inf, 0.0, 0.0),
-                         rho_out=1.0, precision=precision),
+            "grid": grid(nx, ny, nz, xb + [PERIODIC, PERIODIC, PERIODIC, PERIODIC],
+                         u_in=(u_inf, 0.0, 0.0), rho_out=1.0, precision=precision),
             "bodies": bodies, "rho0": 1.0, "u0": (u_inf, 0.0, 0.0),
             "reference": {"U_ref": p["u_tip"], "L": area, "rho_ref": 1.0},
             "params": p}
