@@ -254,14 +254,18 @@ def run_ours(args):
     if cfg["bodies"]:
         tr = ctx.ibl_solver_trace(allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
         if tr[0] and tr[3]:
-            per_it = [(tr[5 + 2 * k] - tr[3 + 2 * k if k else 2]) / 1e3 for k in range(iters) if tr[5 + 2 * k]]
+            it_n = min(iters, 40)
+            starts = [tr[2]] + [tr[13 + 6 * k] for k in range(it_n - 1)]
+            per_it = [(tr[13 + 6 * k] - starts[k]) / 1e3 for k in range(it_n)]
+            med = lambda v: statistics.median(v) if v else None
             trace = {"total_us": (tr[3] - tr[0]) / 1e3, "rebuild_us": (tr[1] - tr[0]) / 1e3,
-                     "setup_us": (tr[2] - tr[1]) / 1e3,
-                     "iteration_us_median": statistics.median(per_it) if per_it else None,
-                     "phase1_us_median": statistics.median([(tr[4 + 2 * k] - (tr[3 + 2 * k] if k else tr[2])) / 1e3
-                                                             for k in range(iters) if tr[4 + 2 * k]]) if iters else None}
-    cl = (ctx.ibl_forces(0, allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
-          if status == "ok" and cfg["bodies"] else None)
+                     "setup_us": (tr[2] - tr[1]) / 1e3, "iteration_us_median": med(per_it),
+                     "spmv_rows_us": med([(tr[8 + 6 * k] - starts[k]) / 1e3 for k in range(it_n)]),
+                     "spmv_reduce_us": med([(tr[9 + 6 * k] - tr[8 + 6 * k]) / 1e3 for k in range(it_n)]),
+                     "barrier1_us": med([(tr[10 + 6 * k] - tr[9 + 6 * k]) / 1e3 for k in range(it_n)]),
+                     "stage_us": med([(tr[11 + 6 * k] - tr[10 + 6 * k]) / 1e3 for k in range(it_n)]),
+                     "precond_rows_us": med([(tr[12 + 6 * k] - tr[11 + 6 * k]) / 1e3 for k in range(it_n)]),
+                     "reduce_barrier2_us": med([(tr[13 + 6 * k] - tr[12 + 6 * k]) / 1e3 for k in range(it_n)])}
     ctx.close()
 
     if WORLD > 1:

@@ -217,10 +217,22 @@ ibl_status ibl_lattice_velocities(int32_t lattice, int32_t* q, int32_t* c, doubl
 ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_residual,
                             int64_t* refreshes);
 
-/* Phase timestamps (GPU global timer, ns) of the last implicit solve:
- * [0] start, [1] after the optional preconditioner rebuild, [2] after set-up,
- * [3] end, [4 + 2k] / [5 + 2k] after the two grid barriers of iteration k.
- * Unused slots are 0.  Copies min(max, 256) values into ns. */
+/* Settings of the implicit IB solve (preconditioned conjugate gradients on
+ * the system of Eqs. 18-19): the dense FP32 approximate inverse used as
+ * preconditioner is rebuilt every refresh_every steps (default 128) and
+ * early when a solve needed more than 40 iterations; tol is the relative
+ * residual in the preconditioner's norm (0 = default: 1e-10 for FP64
+ * storage, 1e-8 otherwise); extrapolate != 0 starts each solve from
+ * 2 w_{n-1} - w_{n-2} instead of w_{n-1} (default on).  Changing these
+ * changes the iterates, not the system being solved. */
+ibl_status ibl_solver_config(ibl_ctx* ctx, int32_t refresh_every, double tol, int32_t extrapolate);
+
+/* Phase timestamps (GPU global timer, ns, taken by block 0) of the last
+ * implicit solve: [0] start, [1] after the optional preconditioner rebuild,
+ * [2] after set-up, [3] end; iteration k (k < 40) at 8 + 6k: SpMV rows done,
+ * block reduction done, grid barrier passed, preconditioner input staged,
+ * preconditioner rows done, grid barrier passed.  Unused slots are 0.
+ * Copies min(max, 256) values into ns. */
 ibl_status ibl_solver_trace(ibl_ctx* ctx, int64_t* ns, int32_t max, int32_t* n);
 
 /* Enable (1) or disable (0) CUDA-event timing, on the context's stream, of

@@ -176,6 +176,7 @@ ibl_status ibl_init_fluid(ibl_ctx* c, const double* rho, const double* u) {
   c->poststream = true;
   c->step = 0;
   c->warm = false;
+  c->warm_steps = 0;
   return IBL_OK;
 }
 
@@ -194,6 +195,7 @@ ibl_status ibl_set_populations(ibl_ctx* c, const double* f) {
   c->poststream = true;
   c->step = 0;
   c->warm = false;
+  c->warm_steps = 0;
   return IBL_OK;
 }
 
@@ -532,6 +534,15 @@ ibl_status ibl_solver_stats(ibl_ctx* c, int32_t* iterations, double* rel_residua
   if (rel_residual) *rel_residual = res;
   if (refreshes) *refreshes = c->refreshes;
   return s;
+}
+
+ibl_status ibl_solver_config(ibl_ctx* c, int32_t refresh_every, double tol, int32_t extrapolate) {
+  if (!c) return IBL_EINVAL;
+  if (refresh_every < 1 || !(tol >= 0.0) || tol >= 1.0) return fail(c, IBL_EINVAL, "refresh_every >= 1, 0 <= tol < 1");
+  c->refresh_every = refresh_every;
+  c->solver_tol = tol;
+  c->extrapolate = extrapolate != 0;
+  return IBL_OK;
 }
 
 ibl_status ibl_profile(ibl_ctx* c, int32_t enable) {

@@ -33,7 +33,7 @@ constexpr int GJ_NB = 64;          // Gauss-Jordan pivot block
 constexpr int PCG_MAX_ITERS = 200;
 constexpr double PCG_TOL = 1e-10;      // relative preconditioned residual (field A-norm), FP64 storage
 constexpr double PCG_TOL_LOW = 1e-8;   // FP32 / 16-bit storage: two decades under their rounding
-constexpr int REFRESH_EVERY = 64;  // steps between preconditioner rebuilds
+
 constexpr int REFRESH_ITERS = 40;  // rebuild early if a solve needed more
 
 struct BodyTable {
@@ -526,6 +526,8 @@ struct PcgArgs {
   int boff[MAX_BODIES + 1];     // marker offsets
   long long poff[MAX_BODIES];   // preconditioner offsets (floats, 16-byte aligned)
   int voff[MAX_BODIES];         // offset of each body's slice in the padded FP32 vectors
+  int vtotal;                   // floats of one padded FP32 vector (all bodies), multiple of 12
+  int smem_floats;              // dynamic shared memory available for staging, in floats
   const int* body_of;
   const int* Gcol;
   const double* Gval;
@@ -533,6 +535,7 @@ struct PcgArgs {
   const unsigned long long* rowsum_max;
   const double* B;
   double* w;
+  double* w_prev;   // solution of the step before (extrapolated warm start)
   double* r;
   double* p;        // 2 x m x 3 ping-pong search directions
   double* Ap;
@@ -559,6 +562,28 @@ __device__ __forceinline__ void trace_mark(const PcgArgs& A, int slot) {
   }
 }
 
+// Fixed-order block sum of three doubles per warp (lane 0 holds them); the
+// totals are returned to every thread.
+__device__ void block_total3(double v[3], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+    for (int c = 0; c < 3; ++c) sh[3 * wid + c] = v[c];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    for (int c = 0; c < 3; ++c) {
+      double t = threadIdx.x < PCG_WARPS ? sh[3 * threadIdx.x + c] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      v[c] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 3; ++c) sh[3 * PCG_WARPS + c] = v[c];
+  __syncthreads();
+  for (int c = 0; c < 3; ++c) v[c] = sh[3 * PCG_WARPS + c];
+}
+
 // Fixed-order block sum of one double per warp (lane 0 holds it); the total
 // is returned to every thread.
 __device__ double block_total(double v, double* sh) {
@@ -578,15 +603,27 @@ __device__ double block_total(double v, double* sh) {
 }
 
 // Sum of the per-block partials in a fixed order by warp 0; every block
-// computes bitwise the same totals, returned to all threads.
+// computes bitwise the same totals, returned to all threads.  Each lane
+// issues all of its loads before adding (one memory round trip).
+constexpr int MAX_PCG_BLOCKS = 256;
 template <int NV>
 __device__ void grid_total(const double* red, int slot, double out[NV], double* sh) {
   __syncthreads();
   if (threadIdx.x < 32) {
+    double buf[MAX_PCG_BLOCKS / 32][NV];
+#pragma unroll
+    for (int u = 0; u < MAX_PCG_BLOCKS / 32; ++u) {
+      const int b = threadIdx.x + 32 * u;
+#pragma unroll
+      for (int c = 0; c < NV; ++c) buf[u][c] = b < (int)gridDim.x ? __ldcg(red + b * 8 + slot + c) : 0.0;
+    }
     double v[NV];
-    for (int c = 0; c < NV; ++c) v[c] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
-      for (int c = 0; c < NV; ++c) v[c] += red[b * 8 + slot + c];
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      v[c] = 0.0;
+#pragma unroll
+      for (int u = 0; u < MAX_PCG_BLOCKS / 32; ++u) v[c] += buf[u][c];
+    }
     for (int o = 16; o > 0; o >>= 1)
       for (int c = 0; c < NV; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
     if (threadIdx.x == 0)
@@ -600,39 +637,82 @@ __device__ void grid_total(const double* red, int slot, double out[NV], double* 
 // start 16-byte aligned for 128-bit loads.
 __host__ __device__ __forceinline__ int precond_ld(int mb) { return (mb + 3) & ~3; }
 
-// One row of the preconditioner: sum_j M_lj x_j with x_j = a_j - s * b_j formed
-// in FP32 (b may be null); 128-bit loads of M and of the interleaved xyz
-// vectors, lane-parallel over the row; the result is returned in every lane.
-__device__ __forceinline__ void precond_row(const PcgArgs& A, int l, const float* __restrict__ a,
-                                            const float* __restrict__ b, const float s[3], float out[3],
-                                            int lane) {
+// x = a - s b (FP32, all bodies' padded slices) into shared memory, or null
+// when the vectors do not fit (then precond_row forms x from global memory).
+// Slices start at multiples of 12 floats, so entry i is component i % 3 and
+// the 128-bit group q holds components (4q, 4q+1, 4q+2, 4q+3) mod 3.
+__device__ float* stage_x(const PcgArgs& A, const float* __restrict__ a, const float* __restrict__ b,
+                          const float s[3], float* sm) {
+  if (A.vtotal > A.smem_floats) return nullptr;
+  __syncthreads();
+  const int nq = A.vtotal >> 2;
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  float4* o4 = reinterpret_cast<float4*>(sm);
+#pragma unroll 4
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    float4 v = __ldcg(a4 + q);
+    if (b) {
+      const float4 w = __ldcg(b4 + q);
+      const int c0 = (4 * q) % 3;
+      const float s0 = s[c0], s1 = s[(c0 + 1) % 3], s2 = s[(c0 + 2) % 3];
+      v.x = fmaf(-s0, w.x, v.x);
+      v.y = fmaf(-s1, w.y, v.y);
+      v.z = fmaf(-s2, w.z, v.z);
+      v.w = fmaf(-s0, w.w, v.w);
+    }
+    o4[q] = v;
+  }
+  __syncthreads();
+  return sm;
+}
+
+// One row of the preconditioner: sum_j M_lj x_j with x_j = a_j - s * b_j
+// (FP32).  x comes from shared memory (xs, already formed) or is formed here
+// from global memory; 128-bit loads of M and x, lane-parallel over the row;
+// the result is returned in every lane.
+__device__ __forceinline__ void precond_row(const PcgArgs& A, int l, const float* __restrict__ xs,
+                                            const float* __restrict__ a, const float* __restrict__ b,
+                                            const float s[3], float out[3], int lane) {
   const int bd = A.body_of[l];
   const int o = A.boff[bd], mb = A.boff[bd + 1] - o;
   const int ld = precond_ld(mb);
   const float* row = A.M + A.poff[bd] + (long long)(l - o) * ld;
-  // the vectors are padded per body so that 3*o is a multiple of 4 floats
-  const float* ab = a + A.voff[bd];
-  const float* bb = b ? b + A.voff[bd] : nullptr;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
   const int nq = ld >> 2;
-#pragma unroll 2
-  for (int q = lane; q < nq; q += 32) {
-    const float4 mv = reinterpret_cast<const float4*>(row)[q];
-    const float4* av = reinterpret_cast<const float4*>(ab + 12 * q);
-    float4 x0 = av[0], x1 = av[1], x2 = av[2];
-    if (bb) {
-      const float4* bv = reinterpret_cast<const float4*>(bb + 12 * q);
-      const float4 y0 = bv[0], y1 = bv[1], y2 = bv[2];
-      x0.x = fmaf(-s[0], y0.x, x0.x); x0.y = fmaf(-s[1], y0.y, x0.y); x0.z = fmaf(-s[2], y0.z, x0.z);
-      x0.w = fmaf(-s[0], y0.w, x0.w); x1.x = fmaf(-s[1], y1.x, x1.x); x1.y = fmaf(-s[2], y1.y, x1.y);
-      x1.z = fmaf(-s[0], y1.z, x1.z); x1.w = fmaf(-s[1], y1.w, x1.w); x2.x = fmaf(-s[2], y2.x, x2.x);
-      x2.y = fmaf(-s[0], y2.y, x2.y); x2.z = fmaf(-s[1], y2.z, x2.z); x2.w = fmaf(-s[2], y2.w, x2.w);
+  if (xs) {
+    const float* xb = xs + A.voff[bd];
+#pragma unroll 4
+    for (int q = lane; q < nq; q += 32) {
+      const float4 mv = __ldcg(reinterpret_cast<const float4*>(row) + q);
+      const float4* xv = reinterpret_cast<const float4*>(xb + 12 * q);
+      const float4 x0 = xv[0], x1 = xv[1], x2 = xv[2];
+      s0 = fmaf(mv.x, x0.x, s0); s1 = fmaf(mv.x, x0.y, s1); s2 = fmaf(mv.x, x0.z, s2);
+      s0 = fmaf(mv.y, x0.w, s0); s1 = fmaf(mv.y, x1.x, s1); s2 = fmaf(mv.y, x1.y, s2);
+      s0 = fmaf(mv.z, x1.z, s0); s1 = fmaf(mv.z, x1.w, s1); s2 = fmaf(mv.z, x2.x, s2);
+      s0 = fmaf(mv.w, x2.y, s0); s1 = fmaf(mv.w, x2.z, s1); s2 = fmaf(mv.w, x2.w, s2);
     }
-    // columns 4q .. 4q+3: (x0.x x0.y x0.z) (x0.w x1.x x1.y) (x1.z x1.w x2.x) (x2.y x2.z x2.w)
-    s0 = fmaf(mv.x, x0.x, s0); s1 = fmaf(mv.x, x0.y, s1); s2 = fmaf(mv.x, x0.z, s2);
-    s0 = fmaf(mv.y, x0.w, s0); s1 = fmaf(mv.y, x1.x, s1); s2 = fmaf(mv.y, x1.y, s2);
-    s0 = fmaf(mv.z, x1.z, s0); s1 = fmaf(mv.z, x1.w, s1); s2 = fmaf(mv.z, x2.x, s2);
-    s0 = fmaf(mv.w, x2.y, s0); s1 = fmaf(mv.w, x2.z, s1); s2 = fmaf(mv.w, x2.w, s2);
+  } else {
+    const float* ab = a + A.voff[bd];
+    const float* bb = b ? b + A.voff[bd] : nullptr;
+#pragma unroll 2
+    for (int q = lane; q < nq; q += 32) {
+      const float4 mv = __ldcg(reinterpret_cast<const float4*>(row) + q);
+      const float4* av = reinterpret_cast<const float4*>(ab + 12 * q);
+      float4 x0 = av[0], x1 = av[1], x2 = av[2];
+      if (bb) {
+        const float4* bv = reinterpret_cast<const float4*>(bb + 12 * q);
+        const float4 y0 = bv[0], y1 = bv[1], y2 = bv[2];
+        x0.x = fmaf(-s[0], y0.x, x0.x); x0.y = fmaf(-s[1], y0.y, x0.y); x0.z = fmaf(-s[2], y0.z, x0.z);
+        x0.w = fmaf(-s[0], y0.w, x0.w); x1.x = fmaf(-s[1], y1.x, x1.x); x1.y = fmaf(-s[2], y1.y, x1.y);
+        x1.z = fmaf(-s[0], y1.z, x1.z); x1.w = fmaf(-s[1], y1.w, x1.w); x2.x = fmaf(-s[2], y2.x, x2.x);
+        x2.y = fmaf(-s[0], y2.y, x2.y); x2.z = fmaf(-s[1], y2.z, x2.z); x2.w = fmaf(-s[2], y2.w, x2.w);
+      }
+      s0 = fmaf(mv.x, x0.x, s0); s1 = fmaf(mv.x, x0.y, s1); s2 = fmaf(mv.x, x0.z, s2);
+      s0 = fmaf(mv.y, x0.w, s0); s1 = fmaf(mv.y, x1.x, s1); s2 = fmaf(mv.y, x1.y, s2);
+      s0 = fmaf(mv.z, x1.z, s0); s1 = fmaf(mv.z, x1.w, s1); s2 = fmaf(mv.z, x2.x, s2);
+      s0 = fmaf(mv.w, x2.y, s0); s1 = fmaf(mv.w, x2.z, s1); s2 = fmaf(mv.w, x2.w, s2);
+    }
   }
   for (int off = 16; off > 0; off >>= 1) {
     s0 += __shfl_xor_sync(0xffffffffu, s0, off);
@@ -649,9 +729,12 @@ __device__ __forceinline__ void precond_row(const PcgArgs& A, int l, const float
 //   P <- P^-1;  row panel R <- P^-1 R;  rest S <- S - C R;  column panel C <- -C P^-1.
 // The three panel products run through one register-tiled shared-memory
 // routine (128 x 128 output tiles, 4 x 4 outputs per thread, K <= GJ_NB).
-constexpr int GT = 128;                 // output tile edge
+constexpr int GT = 128;                 // output tile edge (GT x GJ_NB = 2 x 4 x PCG_THREADS floats)
 constexpr int GS = GT + 4;              // padded shared-memory row
 constexpr size_t GJ_SMEM = sizeof(float) * 2 * GJ_NB * GS;
+// dynamic shared memory of the solve kernel: the rebuild's tiles or, during
+// the iterations, one staged FP32 vector of all bodies (up to 24k markers)
+constexpr size_t PCG_SMEM = 96 * 1024;
 
 // out[i0+r][j0+c] = (acc ? out : 0) + alpha * sum_q A[r][q] B[q][j0+c] over one
 // tile (r < nr, c < nc), skipping output rows in [sk0, sk1) and columns in
@@ -664,13 +747,41 @@ __device__ void tile_gemm(float* out, int ldo, const float* Ag, int lda, const f
   float* As = sm;               // [q][r], GJ_NB x GS
   float* Bs = sm + GJ_NB * GS;  // [q][c], GJ_NB x GS
   __syncthreads();
-  for (int e = threadIdx.x; e < GT * GJ_NB; e += blockDim.x) {
-    const int r = e / GJ_NB, q = e % GJ_NB;
-    As[q * GS + r] = (r < nr && q < K) ? Ag[(long long)r * lda + q] : 0.f;
+  // 128-bit staging, two groups per thread and operand, all loads in flight
+  // (rows, columns and K are multiples of 4 except at ragged edges, where the
+  // group falls back to masked scalar loads); lda, ldb and the tile origins
+  // are multiples of 4 floats, so full groups are 16-byte aligned.
+  float4 av[2], bv[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int f = threadIdx.x + u * PCG_THREADS;
+    const int r = f >> 4, q4 = (f & 15) << 2;
+    if (r < nr && q4 + 3 < K) {
+      av[u] = __ldcg(reinterpret_cast<const float4*>(Ag + (long long)r * lda + q4));
+    } else {
+      float t[4];
+      for (int i = 0; i < 4; ++i) t[i] = (r < nr && q4 + i < K) ? Ag[(long long)r * lda + q4 + i] : 0.f;
+      av[u] = make_float4(t[0], t[1], t[2], t[3]);
+    }
+    const int q = f >> 5, c4 = (f & 31) << 2;
+    if (q < K && c4 + 3 < nc) {
+      bv[u] = __ldcg(reinterpret_cast<const float4*>(Bg + (long long)q * ldb + j0 + c4));
+    } else {
+      float t[4];
+      for (int i = 0; i < 4; ++i) t[i] = (q < K && c4 + i < nc) ? Bg[(long long)q * ldb + j0 + c4 + i] : 0.f;
+      bv[u] = make_float4(t[0], t[1], t[2], t[3]);
+    }
   }
-  for (int e = threadIdx.x; e < GJ_NB * GT; e += blockDim.x) {
-    const int q = e / GT, c = e % GT;
-    Bs[q * GS + c] = (q < K && c < nc) ? Bg[(long long)q * ldb + j0 + c] : 0.f;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int f = threadIdx.x + u * PCG_THREADS;
+    const int r = f >> 4, q4 = (f & 15) << 2;
+    As[(q4 + 0) * GS + r] = av[u].x;
+    As[(q4 + 1) * GS + r] = av[u].y;
+    As[(q4 + 2) * GS + r] = av[u].z;
+    As[(q4 + 3) * GS + r] = av[u].w;
+    const int q = f >> 5, c4 = (f & 31) << 2;
+    *reinterpret_cast<float4*>(Bs + q * GS + c4) = bv[u];
   }
   __syncthreads();
   const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
@@ -806,13 +917,13 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) float sm[];
-  __shared__ double shd[64];
+  __shared__ double shd[3 * PCG_WARPS + 8];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nthreads = gridDim.x * blockDim.x;
   const int m = A.m_total;
-  const int row0 = blockIdx.x + gridDim.x * wib;       // this warp's first row
+  const int row0 = blockIdx.x + gridDim.x * wib;       // this warp's first row (groups of 4 in the SpMV)
   const int rstep = gridDim.x * PCG_WARPS;
 
   // ---- optional preconditioner rebuild: M_b <- (G_b + sigma_b I)^-1 in FP32
@@ -843,7 +954,18 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   }
   trace_mark(A, 1);
 
-  // ---- set-up: w0 = warm ? w : 0;  r = B - G w0;  FP32 copies; p = A p = 0
+  // ---- set-up: w0 = 0, the last solution, or 2 w_n-1 - w_n-2 once two exist
+  // (the solution varies smoothly in time); r = B - G w0; FP32 copies; p = A p = 0
+  if (A.warm >= 2) {
+    for (int i = gtid; i < 3 * m; i += nthreads) {
+      const double cur = A.w[i];
+      A.w[i] = 2.0 * cur - A.w_prev[i];
+      A.w_prev[i] = cur;
+    }
+    grid.sync();
+  } else if (A.warm == 1) {
+    for (int i = gtid; i < 3 * m; i += nthreads) A.w_prev[i] = A.w[i];
+  }
   for (int l = row0; l < m; l += rstep) {
     double s0 = 0, s1 = 0, s2 = 0;
     if (A.warm) {
@@ -880,25 +1002,30 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   {
     double rz3[3] = {0, 0, 0}, bb3[3] = {0, 0, 0};
     const float zero3[3] = {0.f, 0.f, 0.f};
+    const float* xs = stage_x(A, A.rf, nullptr, zero3, sm);
     for (int l = row0; l < m; l += rstep) {
-      float zr[3], zb[3];
-      precond_row(A, l, A.rf, nullptr, zero3, zr, lane);
-      precond_row(A, l, A.Bf, nullptr, zero3, zb, lane);
+      float zr[3];
+      precond_row(A, l, xs, A.rf, nullptr, zero3, zr, lane);
       if (lane == 0)
         for (int c = 0; c < 3; ++c) {
           A.z[3 * l + c] = zr[c];
           rz3[c] += A.r[3 * l + c] * (double)zr[c];
-          bb3[c] += A.B[3 * l + c] * (double)zb[c];
         }
     }
-    for (int c = 0; c < 3; ++c) {
-      const double t1 = block_total(rz3[c], shd);
-      const double t2 = block_total(bb3[c], shd);
-      if (threadIdx.x == 0) {
-        A.red[blockIdx.x * 8 + 3 + c] = t1;
-        A.red[blockIdx.x * 8 + c] = t2;
-      }
+    xs = stage_x(A, A.Bf, nullptr, zero3, sm);
+    for (int l = row0; l < m; l += rstep) {
+      float zb[3];
+      precond_row(A, l, xs, A.Bf, nullptr, zero3, zb, lane);
+      if (lane == 0)
+        for (int c = 0; c < 3; ++c) bb3[c] += A.B[3 * l + c] * (double)zb[c];
     }
+    block_total3(rz3, shd);
+    block_total3(bb3, shd);
+    if (threadIdx.x == 0)
+      for (int c = 0; c < 3; ++c) {
+        A.red[blockIdx.x * 8 + 3 + c] = rz3[c];
+        A.red[blockIdx.x * 8 + c] = bb3[c];
+      }
   }
   grid.sync();
   trace_mark(A, 2);
@@ -926,26 +1053,48 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     __syncthreads();
     const double beta[3] = {s_coef[0], s_coef[1], s_coef[2]};
     {
+      // 8 lanes per row, 4 rows per warp: a 3-level FP64 tree instead of 5
       double pAp3[3] = {0, 0, 0};
-      for (int l = row0; l < m; l += rstep) {
-        const int nnz = A.Gnnz[l];
+      // z of every marker in shared memory when it fits (one round trip, 128-bit)
+      const double* zs = A.z;
+      if (3 * m * (int)sizeof(double) <= A.smem_floats * (int)sizeof(float)) {
+        __syncthreads();
+        const float4* src = reinterpret_cast<const float4*>(A.z);
+        float4* dst = reinterpret_cast<float4*>(sm);
+        const int n4 = (3 * m) / 2;               // 2 doubles per 16 bytes (3m even: m padded below)
+#pragma unroll 4
+        for (int q = threadIdx.x; q < n4; q += blockDim.x) dst[q] = __ldcg(src + q);
+        if (threadIdx.x == 0 && (3 * m) % 2) reinterpret_cast<double*>(sm)[3 * m - 1] = __ldcg(A.z + 3 * m - 1);
+        __syncthreads();
+        zs = reinterpret_cast<const double*>(sm);
+      }
+      const int sub = lane >> 3, sl = lane & 7;
+      for (int l0 = row0 * 4; l0 < m; l0 += rstep * 4) {
+        const int l = l0 + sub;
         double s0 = 0, s1 = 0, s2 = 0;
-        for (int j = lane; j < nnz; j += 32) {
-          const int k = A.Gcol[(long long)l * G_MAXNNZ + j];
-          const double v = A.Gval[(long long)l * G_MAXNNZ + j];
-          s0 += v * A.z[3 * k];
-          s1 += v * A.z[3 * k + 1];
-          s2 += v * A.z[3 * k + 2];
+        if (l < m) {
+          const int nnz = A.Gnnz[l];
+          const int* gc = A.Gcol + (long long)l * G_MAXNNZ;
+          const double* gv = A.Gval + (long long)l * G_MAXNNZ;
+#pragma unroll 4
+          for (int j = sl; j < nnz; j += 8) {
+            const int k = gc[j];
+            const double v = gv[j];
+            s0 += v * zs[3 * k];
+            s1 += v * zs[3 * k + 1];
+            s2 += v * zs[3 * k + 2];
+          }
         }
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 4; o > 0; o >>= 1) {
           s0 += __shfl_xor_sync(0xffffffffu, s0, o);
           s1 += __shfl_xor_sync(0xffffffffu, s1, o);
           s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         }
         double contrib = 0.0;
-        if (lane < 3) {
-          const int c = lane;
-          const int vi = A.voff[A.body_of[l]] + 3 * (l - A.boff[A.body_of[l]]) + c;
+        if (l < m && sl < 3) {
+          const int c = sl;
+          const int bd = A.body_of[l];
+          const int vi = A.voff[bd] + 3 * (l - A.boff[bd]) + c;
           const double gz = c == 0 ? s0 : (c == 1 ? s1 : s2);
           const double pl = A.z[3 * l + c] + beta[c] * A.p[3 * l + c];
           const double ap = gz + beta[c] * A.Ap[3 * l + c];
@@ -955,21 +1104,21 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
           A.rf[vi] = (float)A.r[3 * l + c];
           contrib = pl * ap;
         }
-        const double c1 = __shfl_sync(0xffffffffu, contrib, 1);
-        const double c2 = __shfl_sync(0xffffffffu, contrib, 2);
-        if (lane == 0) {
-          pAp3[0] += contrib;
-          pAp3[1] += c1;
-          pAp3[2] += c2;
-        }
+        // lanes 8 sub + c hold component c of row l0 + sub: lane 0 gathers them in a fixed order
+        for (int r = 0; r < 4; ++r)
+          for (int c = 0; c < 3; ++c) {
+            const double v = __shfl_sync(0xffffffffu, contrib, 8 * r + c);
+            if (lane == 0) pAp3[c] += v;
+          }
       }
-      for (int c = 0; c < 3; ++c) {
-        const double t = block_total(pAp3[c], shd);
-        if (threadIdx.x == 0) A.red[blockIdx.x * 8 + c] = t;
-      }
+      trace_mark(A, 8 + 6 * it);
+      block_total3(pAp3, shd);
+      if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) A.red[blockIdx.x * 8 + c] = pAp3[c];
+      trace_mark(A, 9 + 6 * it);
     }
     grid.sync();
-    trace_mark(A, 4 + 2 * it);
+    trace_mark(A, 10 + 6 * it);
     // ---- P2: alpha;  z = M (r - alpha A p) in FP32;  w += alpha p;  r -= alpha A p;  partial r.z
     {
       double pAp[3];
@@ -986,9 +1135,11 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     const float alphaf[3] = {s_coeff[0], s_coeff[1], s_coeff[2]};
     {
       double rz3[3] = {0, 0, 0};
+      const float* xs = stage_x(A, A.rf, A.Apf, alphaf, sm);
+      trace_mark(A, 11 + 6 * it);
       for (int l = row0; l < m; l += rstep) {
         float zl[3];
-        precond_row(A, l, A.rf, A.Apf, alphaf, zl, lane);
+        precond_row(A, l, xs, A.rf, A.Apf, alphaf, zl, lane);
         double contrib = 0.0;
         if (lane < 3) {
           const int c = lane;
@@ -1006,13 +1157,13 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
           rz3[2] += c2;
         }
       }
-      for (int c = 0; c < 3; ++c) {
-        const double t = block_total(rz3[c], shd);
-        if (threadIdx.x == 0) A.red[blockIdx.x * 8 + 3 + c] = t;
-      }
+      trace_mark(A, 12 + 6 * it);
+      block_total3(rz3, shd);
+      if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) A.red[blockIdx.x * 8 + 3 + c] = rz3[c];
     }
     grid.sync();
-    trace_mark(A, 5 + 2 * it);
+    trace_mark(A, 13 + 6 * it);
     {
       double rzn[3];
       grid_total<3>(A.red, 3, rzn, shd);
@@ -1196,15 +1347,16 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   IBL_CU(cudaMalloc(&c->d_rho_l, sizeof(double) * m));
   IBL_CU(cudaMalloc(&c->d_B, sizeof(double) * 3 * m));
   IBL_CU(cudaMalloc(&c->d_w, sizeof(double) * 3 * m));
+  IBL_CU(cudaMalloc(&c->d_wprev, sizeof(double) * 3 * m));
   IBL_CU(cudaMemsetAsync(c->d_w, 0, sizeof(double) * 3 * m, c->stream));
   IBL_CU(cudaMalloc(&c->d_r, sizeof(double) * 3 * m));
   IBL_CU(cudaMalloc(&c->d_p, sizeof(double) * 6 * m));
   IBL_CU(cudaMalloc(&c->d_Ap, sizeof(double) * 3 * m));
   IBL_CU(cudaMalloc(&c->d_z, sizeof(double) * 3 * m));
-  // three padded FP32 vectors (r, A p, B); each body's slice starts on a
-  // 16-byte boundary and carries a zero tail up to a multiple of 4 markers
+  // three padded FP32 vectors (r, A p, B); each body's slice starts at a
+  // multiple of 12 floats and carries a zero tail up to a multiple of 4 markers
   size_t vf = 0;
-  for (auto& b : c->bodies) vf += 3 * (size_t)((b.m + 3) & ~3) + 4;
+  for (auto& b : c->bodies) vf += 3 * (size_t)((b.m + 3) & ~3) + 12;
   c->xf_floats = vf;
   IBL_CU(cudaMalloc(&c->d_xf, sizeof(float) * 3 * vf));
   IBL_CU(cudaMemsetAsync(c->d_xf, 0, sizeof(float) * 3 * vf, c->stream));
@@ -1243,6 +1395,7 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   c->cand_ready = false;
   c->precond_valid = false;
   c->warm = false;
+  c->warm_steps = 0;
   c->ib_ready = true;
   return cudaSuccess;
 }
@@ -1253,7 +1406,8 @@ void ib_free(ibl_ctx* c) {
                   c->d_band_F, c->d_base, c->d_wts, c->d_rho_l, c->d_B, c->d_w, c->d_r, c->d_p,
                   c->d_Ap, c->d_z, c->d_Gcol, c->d_Gval, c->d_Gnnz, c->d_Gdiag_max, c->d_M, c->d_red,
                   c->d_cg_info, c->d_cg_res, c->d_hist, c->d_mforce, c->d_boff, c->d_xf, c->d_trace,
-                  c->d_acc, c->d_bstate, c->d_slot_body, c->d_mixed, c->d_cand, c->d_ncand};
+                  c->d_acc, c->d_bstate, c->d_slot_body, c->d_mixed, c->d_cand, c->d_ncand,
+                  c->d_wprev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->d_X0 = c->d_ds = c->d_X = c->d_U = c->d_Xp = c->d_Up = nullptr;
@@ -1269,6 +1423,7 @@ void ib_free(ibl_ctx* c) {
   c->d_acc = nullptr;
   c->d_bstate = nullptr;
   c->d_slot_body = c->d_mixed = c->d_cand = c->d_ncand = nullptr;
+  c->d_wprev = nullptr;
   c->ib_ready = false;
 }
 
@@ -1406,13 +1561,16 @@ cudaError_t ib_step(ibl_ctx* c) {
     int vo = 0;
     for (int b = 0; b < A.nbodies; ++b) {
       A.voff[b] = vo;
-      vo += 3 * ((c->bodies[b].m + 3) & ~3) + 4;
+      vo += 3 * ((c->bodies[b].m + 3) & ~3) + 12;
     }
+    A.vtotal = vo;
   }
-  A.tol = c->prec == IBL_FP64 ? PCG_TOL : PCG_TOL_LOW;
+  A.smem_floats = (int)(PCG_SMEM / sizeof(float));
+  A.tol = c->solver_tol > 0 ? c->solver_tol : (c->prec == IBL_FP64 ? PCG_TOL : PCG_TOL_LOW);
   A.M = c->d_M; A.red = c->d_red; A.info = c->d_cg_info; A.res = c->d_cg_res;
-  A.warm = c->warm ? 1 : 0;
-  const bool sched = !c->precond_valid || (c->step - c->last_refresh_step) >= REFRESH_EVERY;
+  A.warm = c->warm_steps >= 2 && c->extrapolate ? 2 : (c->warm_steps >= 1 ? 1 : 0);
+  A.w_prev = c->d_wprev;
+  const bool sched = !c->precond_valid || (c->step - c->last_refresh_step) >= c->refresh_every;
   A.refresh = sched ? 1 : 0;
   if (sched) {
     c->last_refresh_step = c->step;
@@ -1423,14 +1581,15 @@ cudaError_t ib_step(ibl_ctx* c) {
   A.trace = c->d_trace;
   static bool smem_set = false;
   if (!smem_set) {
-    IBL_CU(cudaFuncSetAttribute((const void*)k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GJ_SMEM));
+    IBL_CU(cudaFuncSetAttribute((const void*)k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCG_SMEM));
     smem_set = true;
   }
-  int pcg_blocks = std::max(1, std::min(g_num_sms, m));
+  int pcg_blocks = std::max(1, std::min(std::min(g_num_sms, MAX_PCG_BLOCKS), m));
   void* args[] = {&A};
-  IBL_CU(cudaLaunchCooperativeKernel((void*)k_pcg, dim3(pcg_blocks), dim3(PCG_THREADS), args, GJ_SMEM, c->stream));
+  IBL_CU(cudaLaunchCooperativeKernel((void*)k_pcg, dim3(pcg_blocks), dim3(PCG_THREADS), args, PCG_SMEM, c->stream));
   c->launches++;
   c->warm = true;
+  c->warm_steps++;
   // spreading: fixed-point scatter, then F = 2 rho du
   {
     const int nn = c->D == 3 ? 64 : 16;

@@ -263,6 +263,11 @@ struct ibl_ctx {
   long long last_refresh_step = -1000000;
   bool precond_valid = false;
   bool warm = false;             // d_w holds the previous solution
+  long long warm_steps = 0;      // consecutive solves behind d_w (2+: extrapolate)
+  bool extrapolate = true;
+  int refresh_every = 128;       // steps between scheduled preconditioner rebuilds
+  double solver_tol = 0.0;       // 0: default for the storage precision
+  double* d_wprev = nullptr;     // m x 3 solution of the previous step
   // optional per-step event timing (ibl_profile)
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;   // 4 events per step: ib0, collide0, collide1, ib1

@@ -70,6 +70,7 @@ _SIGS = {
     "ibl_lattice_velocities": ([C.c_int32, _I32, _I32, _D], C.c_int),
     "ibl_solver_stats": ([_P, _I32, _D, _I64], C.c_int),
     "ibl_solver_trace": ([_P, _I64, C.c_int32, _I32], C.c_int),
+    "ibl_solver_config": ([_P, C.c_int32, C.c_double, C.c_int32], C.c_int),
     "ibl_profile": ([_P, C.c_int32], C.c_int),
     "ibl_profile_read": ([_P, _D, _D, _I64], C.c_int),
     "ibl_launch_count": ([_P, _I64], C.c_int),
@@ -276,6 +277,9 @@ class Context:
         it, res, ref = C.c_int32(), C.c_double(), C.c_int64()
         _check(self.h, _lib.ibl_solver_stats(self.h, C.byref(it), C.byref(res), C.byref(ref)), allow)
         return it.value, res.value, ref.value
+
+    def ibl_solver_config(self, refresh_every=128, tol=0.0, extrapolate=True):
+        _check(self.h, _lib.ibl_solver_config(self.h, int(refresh_every), float(tol), 1 if extrapolate else 0))
 
     def ibl_solver_trace(self, allow=()):
         out = np.zeros(256, dtype=np.int64)
