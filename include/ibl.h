@@ -205,6 +205,22 @@ ibl_status ibl_get_markers(ibl_ctx* ctx, int32_t body_id, double* X, double* U, 
  * in a fixed order. */
 ibl_status ibl_mass(ibl_ctx* ctx, double* mass);
 
+/* Same total as ibl_mass, for callers that must not allocate device memory
+ * after start-up: a solver embedded in a real-time control loop, code whose
+ * device memory is fully claimed by another allocator (a framework's caching
+ * allocator), or work recorded inside a CUDA stream capture, where cudaMalloc
+ * is not allowed.  ibl_mass allocates its partial sums per call; this call
+ * allocates nothing: its partials live in a static device array of 4096
+ * doubles (32 KB), which every GPU that loads the library holds until the
+ * process exits.  The paper has no counterpart of this call.
+ *   nparts  number of fixed chunks summed on the device, 1..4096 (IBL_EINVAL
+ *           beyond); with nparts = 1024 the result equals ibl_mass bitwise.
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make it before any stream capture.  All calls share
+ * the array: calls from different contexts or threads that overlap on the
+ * GPU race and must be serialised by the caller.  Synchronises the stream. */
+ibl_status ibl_mass_noalloc(ibl_ctx* ctx, int32_t nparts, double* mass);
+
 /* ------------------------------------------------------------------ introspection */
 
 /* Velocity set of a lattice: c is Q x 3 int32 (marker of direction order used by

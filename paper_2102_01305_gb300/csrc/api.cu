@@ -48,7 +48,10 @@ static ibl_status status_code(ibl_ctx* c) {
   return IBL_OK;
 }
 
-static ibl_status sync_and_collect(ibl_ctx* c) {
+namespace ibl {
+ibl_status sync_and_collect(ibl_ctx* c);
+}
+ibl_status ibl::sync_and_collect(ibl_ctx* c) {
   CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   int s = 0;
   CK(cudaMemcpy(&s, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");

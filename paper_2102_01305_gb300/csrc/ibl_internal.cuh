@@ -287,6 +287,7 @@ namespace ibl {
 // error helpers (api.cu)
 ibl_status fail(ibl_ctx* c, ibl_status s, const std::string& msg);
 ibl_status cuda_check(ibl_ctx* c, cudaError_t e, const char* what);
+ibl_status sync_and_collect(ibl_ctx* c);   // drain the stream, fold device status bits
 
 // fluid launches (lbm.cu)
 cudaError_t launch_init_eq(ibl_ctx* c, const double* d_rho, const double* d_u);

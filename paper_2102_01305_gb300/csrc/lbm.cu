@@ -9,6 +9,8 @@
 // Paper passages: Eq. 1 (BGK + streaming), Eq. 4 (equilibrium), Eqs. 7-8
 // (Guo forcing), Eq. 9 (rho u = sum c_i f_i + F/2), Sec. 2.1 bounce-back,
 // Sec. 3.1 Zou-He inlet / outlet.
+#include <mutex>
+
 #include "ibl_internal.cuh"
 #include "lbm_gather.cuh"
 
@@ -366,3 +368,56 @@ cudaError_t launch_init_eq(ibl_ctx* c, const double* d_rho, const double* d_u) {
 cudaError_t launch_set_pop(ibl_ctx* c, const double* d_f) { IBL_DISPATCH(setpop_q, d_f); }
 
 }  // namespace ibl
+
+// ----------------------------------------------------------------- allocation-free mass
+// ibl_mass allocates its partial sums on every call.  For callers that may
+// not allocate device memory, ibl_mass_noalloc keeps them in this file-scope
+// array instead (32 KB, held by every GPU that loads the library until exit).
+namespace {
+constexpr int NOALLOC_MAX_PARTS = 4096;
+__device__ __align__(256) double g_mass_partials[NOALLOC_MAX_PARTS];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+double* g_mass_partials_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+std::mutex g_noalloc_mutex;
+}  // namespace
+
+extern "C" ibl_status ibl_mass_noalloc(ibl_ctx* c, int32_t nparts, double* mass) {
+  using namespace ibl;
+  if (!c) return IBL_EINVAL;
+  if (!mass) return fail(c, IBL_EINVAL, "mass is NULL");
+  if (nparts < 1 || nparts > NOALLOC_MAX_PARTS)
+    return fail(c, IBL_EINVAL, "ibl_mass_noalloc: nparts must be in [1, 4096] (size of its static scratch)");
+  if (!c->initialised) return fail(c, IBL_ESTATE, "fluid not initialised");
+  if (c->device < 0 || c->device >= NOALLOC_MAX_DEVICES)
+    return fail(c, IBL_EINVAL, "ibl_mass_noalloc supports device ordinals below 64");
+  ibl_status s = sync_and_collect(c);
+  if (s != IBL_OK && s != IBL_ENOTCONV) return s;
+  // The array's name is a host-side stand-in: its device address is looked up
+  // once per device, with that device current, on the first call.
+  double* d_parts = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_mass_partials_addr[c->device]) {
+      int prev = 0;
+      cudaError_t e = cudaGetDevice(&prev);
+      if (e == cudaSuccess && prev != c->device) e = cudaSetDevice(c->device);
+      void* addr = nullptr;
+      if (e == cudaSuccess) e = cudaGetSymbolAddress(&addr, g_mass_partials);
+      if (prev != c->device) cudaSetDevice(prev);
+      if (e != cudaSuccess) return cuda_check(c, e, "cudaGetSymbolAddress(g_mass_partials)");
+      g_mass_partials_addr[c->device] = static_cast<double*>(addr);
+    }
+    d_parts = g_mass_partials_addr[c->device];
+  }
+  // every block writes its partial, so nothing needs clearing between calls
+  cudaError_t e = launch_mass(c, d_parts, nparts, nullptr);
+  double h[NOALLOC_MAX_PARTS];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h, d_parts, sizeof(double) * nparts, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "ibl_mass_noalloc");
+  double acc = 0.0;
+  for (int k = 0; k < nparts; ++k) acc += h[k];
+  *mass = acc;
+  return s;
+}

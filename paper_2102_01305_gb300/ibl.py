@@ -67,6 +67,7 @@ _SIGS = {
     "ibl_get_populations": ([_P, _D], C.c_int),
     "ibl_get_markers": ([_P, C.c_int32, _D, _D, _D], C.c_int),
     "ibl_mass": ([_P, _D], C.c_int),
+    "ibl_mass_noalloc": ([_P, C.c_int32, _D], C.c_int),
     "ibl_lattice_velocities": ([C.c_int32, _I32, _I32, _D], C.c_int),
     "ibl_solver_stats": ([_P, _I32, _D, _I64], C.c_int),
     "ibl_solver_trace": ([_P, _I64, C.c_int32, _I32], C.c_int),
@@ -271,6 +272,12 @@ class Context:
     def ibl_mass(self, allow=()):
         m = C.c_double()
         _check(self.h, _lib.ibl_mass(self.h, C.byref(m)), allow)
+        return m.value
+
+    def ibl_mass_noalloc(self, nparts=1024, allow=()):
+        """Total mass without any device allocation (static scratch, see ibl.h)."""
+        m = C.c_double()
+        _check(self.h, _lib.ibl_mass_noalloc(self.h, int(nparts), C.byref(m)), allow)
         return m.value
 
     def ibl_solver_stats(self, allow=()):
