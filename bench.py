@@ -38,8 +38,12 @@ if WORLD > 1 and "CUDA_VISIBLE_DEVICES" not in os.environ:
 METRIC = "IB-LBM D3Q19 GLUPS & % HBM roofline; sweep-serving solves/h, p50/p99 latency"
 UNIT = "GLUPS"
 FALLBACK_HBM_GBS = 6800.0
+# sources the collide-stream kernel is compiled from (lbm.cu up to its
+# allocation-free mass section); the recorded DRAM traffic is valid only
+# while their hash matches profiles/collide_traffic.txt
 COLLIDE_SOURCES = ["paper_2102_01305_gb300/csrc/lbm.cu", "paper_2102_01305_gb300/csrc/lbm_gather.cuh",
-                   "paper_2102_01305_gb300/csrc/ibl_internal.cuh"]
+                   "paper_2102_01305_gb300/csrc/lattice.cuh"]
+LBM_END_MARK = b"// ----------------------------------------------------------------- allocation-free mass"
 
 
 def parse():
@@ -176,6 +180,13 @@ def run_oracle_subprocess(scale: float, steps: int, warm: int = 0, timeout: floa
 
 def cpu_model() -> str:
     try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + f", {os.cpu_count()} cores"
+    except Exception:
+        pass
+    try:
         for line in open("/proc/cpuinfo"):
             if line.lower().startswith(("model name", "cpu part", "hardware")):
                 return line.split(":", 1)[1].strip()
@@ -186,7 +197,7 @@ def cpu_model() -> str:
 
 # ----------------------------------------------------------------------------- our arm
 def traffic_record(collide_hash: str):
-    path = os.path.join(ROOT, "profiles", "collide_traffic.json")
+    path = os.path.join(ROOT, "profiles", "collide_traffic.txt")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
@@ -198,7 +209,10 @@ def traffic_record(collide_hash: str):
 def source_hash() -> str:
     h = hashlib.sha256()
     for p in COLLIDE_SOURCES:
-        h.update(open(os.path.join(ROOT, p), "rb").read())
+        data = open(os.path.join(ROOT, p), "rb").read()
+        if p.endswith("lbm.cu") and LBM_END_MARK in data:
+            data = data[:data.index(LBM_END_MARK)]
+        h.update(data)
     return h.hexdigest()
 
 
@@ -266,6 +280,8 @@ def run_ours(args):
                      "stage_us": med([(tr[11 + 6 * k] - tr[10 + 6 * k]) / 1e3 for k in range(it_n)]),
                      "precond_rows_us": med([(tr[12 + 6 * k] - tr[11 + 6 * k]) / 1e3 for k in range(it_n)]),
                      "reduce_barrier2_us": med([(tr[13 + 6 * k] - tr[12 + 6 * k]) / 1e3 for k in range(it_n)])}
+    cl = (ctx.ibl_forces(0, allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
+          if status == "ok" and cfg["bodies"] else None)
     ctx.close()
 
     if WORLD > 1:
@@ -288,7 +304,8 @@ def run_ours(args):
     per_launch_s = collide_ms / max(nprof, 1) * 1e-3
     alg_bytes = bytes_per_cell * cells
     achieved = alg_bytes / per_launch_s / 1e9
-    rec = traffic_record(source_hash()) if args.precision == "fp32" else None
+    # the recorded traffic belongs to the wing workload's FP32 kernel (band lookup on)
+    rec = traffic_record(source_hash()) if (args.precision == "fp32" and args.workload == "wings") else None
     roofline = {"bound": "hbm", "kernel": "k_collide (collide + stream + faces, D3Q19)",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_src,
