@@ -57,6 +57,14 @@ def parse():
                     help="wings: the clap-and-fling wing pair (default); tgv: pure D3Q19 periodic "
                          "Taylor-Green vortex, u0=0.05, tau=0.6 (roofline sweep)")
     ap.add_argument("--size", type=int, default=256, help="cube edge of the tgv workload")
+    ap.add_argument("--serving", action="store_true",
+                    help="run the serving sweep (Poisson arrivals of clap-and-fling runs) instead")
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--mean-gap", type=float, default=2.0, help="mean Poisson inter-arrival gap, s")
+    ap.add_argument("--run-steps", type=int, default=10000)
+    ap.add_argument("--mix", default="mixed", choices=["mixed", "fp32", "fp16dev", "bf16dev"])
+    ap.add_argument("--serving-sample", type=int, default=12,
+                    help="requests of the short serving sample in the default line (0: none)")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-worker", default=None)   # internal: run the oracle sample
@@ -195,6 +203,19 @@ def cpu_model() -> str:
     return "unknown"
 
 
+# ----------------------------------------------------------------------------- replicas
+def aggregate_over_ranks(ms_local: float, cells: int, steps: int, world: int, dist=None, device="cpu"):
+    """Whole-job throughput of `world` independent replicas: every rank ran
+    `steps` steps of `cells` cells; the job time is the slowest rank's time."""
+    ms = ms_local
+    if world > 1 and dist is not None:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, cells * steps * world / (ms * 1e-3) / 1e9
+
+
 # ----------------------------------------------------------------------------- our arm
 def traffic_record(collide_hash: str):
     path = os.path.join(ROOT, "profiles", "collide_traffic.txt")
@@ -284,11 +305,7 @@ def run_ours(args):
           if status == "ok" and cfg["bodies"] else None)
     ctx.close()
 
-    if WORLD > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = cells * args.steps * WORLD / (ms * 1e-3) / 1e9
+    ms, value = aggregate_over_ranks(ms, cells, args.steps, WORLD, dist if WORLD > 1 else None, "cuda")
 
     # end to end: host buffers through the public API, copies inside the timed region
     e2e = None
@@ -327,6 +344,15 @@ def run_ours(args):
         except Exception as e:  # the baseline is reported, never required
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:300]}
 
+    serving = None
+    if RANK == 0 and WORLD == 1 and args.serving_sample > 0 and args.workload == "wings":
+        try:
+            serving = run_serving(args.serving_sample, 0.05, 1000, "mixed")
+            serving["note"] = ("short sample of the sweep (1000 steps per run, mean gap 0.05 s); "
+                               "`bench.py --serving` runs 64 requests x 10000 steps, mean gap 2 s")
+        except Exception as e:
+            serving = {"error": str(e)[:300]}
+
     if RANK == 0:
         line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": WORLD,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
@@ -336,7 +362,7 @@ def run_ours(args):
                 "data": "synthetic (seeded workload generator; no dataset)",
                 "config": describe(cfg, args.steps) | {"parallelism": f"replicas x{WORLD}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "status": status,
+                "clocks": clk, "status": status, "serving_sample": serving,
                 "solver": {"pcg_iterations_last_step": iters, "rel_residual_last_step": res,
                            "preconditioner_rebuilds": refreshes, "trace_last_step": trace},
                 "C_L_last_step_body0": cl[0] if cl else None}
@@ -373,6 +399,58 @@ def run_e2e(ibl, cfg, steps, cells):
     return {"value": round(cells * steps / dt / 1e9, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": steps,
             "path": "ibl_set_marker_state (host X, U of both wings) -> ibl_step(1) -> ibl_forces x2"}
+
+
+# ----------------------------------------------------------------------------- serving
+def sweep_requests(n: int, run_steps: int, mix: str, seed: int = 20210203):
+    """Requests of the parametric sweep: Re in {75,100,150}, f in {0.05,0.25}
+    Hz-equivalent (period 200c or 40c steps), J in {1e-3,1e-2,2}, grid drawn
+    uniformly from 96^3, 160x128x112, 256x192x160 with the chord scaled to the
+    grid; storage precision FP32 or FP16 deviations 50/50 ("mixed")."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    grids = [(96, 96, 96), (160, 128, 112), (256, 192, 160)]
+    out = []
+    for _ in range(n):
+        nx, ny, nz = grids[rng.integers(3)]
+        c = float(round(20.0 * nx / 256.0))
+        f = [0.05, 0.25][rng.integers(2)]
+        prec = mix if mix != "mixed" else ["fp32", "fp16dev"][rng.integers(2)]
+        out.append(dict(nx=nx, ny=ny, nz=nz, chord=c, Re=float([75, 100, 150][rng.integers(3)]),
+                        period=200.0 * c * 0.05 / f, J=float([1e-3, 1e-2, 2.0][rng.integers(3)]),
+                        precision=prec, steps=run_steps))
+    return out
+
+
+def run_serving(n: int, mean_gap: float, run_steps: int, mix: str, budget_frac: float = 0.8):
+    """Submit a Poisson stream of sweep requests, wait, report solves/h and latency."""
+    import numpy as np
+    import torch
+    from paper_2102_01305_gb300 import ibl
+    free, total = torch.cuda.mem_get_info()
+    srv = ibl.Server(hbm_budget_bytes=int(free * budget_frac), max_active=16, chunk_steps=50)
+    reqs = sweep_requests(n, run_steps, mix)
+    rng = np.random.default_rng(7)
+    gaps = rng.exponential(mean_gap, size=n)
+    t0 = time.perf_counter()
+    ids = []
+    for g, r in zip(gaps, reqs):
+        time.sleep(float(g))
+        ids.append(srv.ibl_server_submit(**r))
+    srv.ibl_server_wait_all(24 * 3600.0)
+    wall = time.perf_counter() - t0
+    res = [srv.ibl_server_poll(i) for i in ids]
+    srv.close()
+    ok = [r for r in res if r["status"] == ibl.IBL_OK]
+    lat = sorted(r["finish_s"] - r["submit_s"] for r in ok)
+    q = lambda p: float(np.percentile(lat, p)) if lat else None
+    cells = sum(rq["nx"] * rq["ny"] * rq["nz"] * rq["steps"] for rq, r in zip(reqs, res) if r["status"] == ibl.IBL_OK)
+    return {"solves_per_hour": len(ok) / wall * 3600.0, "requests": n, "completed": len(ok),
+            "failed": n - len(ok), "failure_statuses": sorted({ibl.STATUS_NAMES[r["status"]] for r in res
+                                                                if r["status"] != ibl.IBL_OK}),
+            "p50_latency_s": q(50), "p99_latency_s": q(99), "wall_s": wall, "mean_gap_s": mean_gap,
+            "steps_per_run": run_steps, "precision_mix": mix,
+            "aggregate_glups": cells / wall / 1e9}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -418,6 +496,14 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.serving:
+        r = run_serving(args.requests, args.mean_gap, args.run_steps, args.mix)
+        print(json.dumps({"metric": METRIC, "value": round(r["solves_per_hour"], 2), "unit": "solves/h",
+                          "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "data": "synthetic (seeded sweep of the paper's Re, f, J grid)",
+                          "config": {"workload": "serving sweep of clap-and-fling runs",
+                                     "parallelism": "continuous batching, one stream per run"},
+                          "serving": r}), flush=True)
     else:
         run_ours(args)
 

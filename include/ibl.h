@@ -272,6 +272,63 @@ ibl_status ibl_stream(const ibl_ctx* ctx, void** stream);
  * ctx == NULL, the last error of a failed ibl_create. */
 const char* ibl_last_error(const ibl_ctx* ctx);
 
+/* ------------------------------------------------------------------ serving */
+
+/* Serving form of the paper's parametric study (Sec. 3.3-3.7: clap-and-fling
+ * runs over Re, f and J): requests arrive while others run, are admitted by
+ * an HBM budget, and advance concurrently, each on its own stream, in
+ * chunks of steps.  A run follows exactly the kernel sequence it would
+ * follow alone, so its result does not depend on the mix. */
+typedef struct ibl_server ibl_server;
+
+typedef struct {
+  int64_t hbm_budget_bytes;  /* device memory the active runs may use together */
+  int32_t max_active;        /* runs advanced concurrently */
+  int32_t chunk_steps;       /* steps enqueued per run between scheduling passes */
+} ibl_server_config;
+
+/* One clap-and-fling run: D3Q19 box nx x ny x nz, two flat elliptic wings of
+ * chord `chord` (span 5 chord, unit-spaced markers) hinged at the trailing
+ * edge c/2 apart, opening angle (pi/3)|sin(2 pi t / period)| per wing;
+ * Re = U_tip c / nu with U_tip = 2 Phi c / period, Phi = 120 degrees (Eq. 24,
+ * Sec. 3.4), tau = 3 nu + 1/2 (Eq. 3); free stream J * U_tip along +x,
+ * imposed by Zou-He inlet/outlet faces (faces = 1) or as the initial flow of
+ * an x-periodic box (faces = 0). */
+typedef struct {
+  int32_t nx, ny, nz;
+  double chord;
+  double Re;
+  double period;        /* steps per flapping period, T = 1/f */
+  double J;
+  int32_t precision;    /* ibl_precision */
+  int32_t faces;
+  int64_t steps;        /* 1 .. 65536 */
+} ibl_run_request;
+
+typedef struct {
+  int32_t status;       /* ibl_status of the run */
+  int32_t done;         /* 1 once finished (or failed) */
+  int64_t steps_done;   /* steps enqueued so far */
+  double submit_s, start_s, finish_s;   /* server clock, seconds since creation */
+  double CL_max[2], CL_mean[2], CT_max[2], CT_mean[2];   /* per wing over the run */
+  double CL_last[2], CT_last[2];
+} ibl_run_result;
+
+/* Create a server on the current device (starts its scheduling thread). */
+ibl_status ibl_server_create(const ibl_server_config* cfg, ibl_server** out);
+/* Queue a run; *run_id identifies it.  IBL_EINVAL for a malformed request or
+ * wings that do not fit the box, IBL_ENOMEM if its footprint exceeds the
+ * whole budget.  Thread-safe. */
+ibl_status ibl_server_submit(ibl_server* s, const ibl_run_request* req, int64_t* run_id);
+/* Snapshot of a run's progress and, once done, its result.  Thread-safe. */
+ibl_status ibl_server_poll(ibl_server* s, int64_t run_id, ibl_run_result* out);
+/* Block until no run is queued or active; IBL_ETIMEOUT after timeout_s. */
+ibl_status ibl_server_wait_all(ibl_server* s, double timeout_s);
+ibl_status ibl_server_stats(ibl_server* s, int32_t* queued, int32_t* active, int32_t* finished,
+                            int64_t* hbm_in_use);
+/* Stop the scheduler and release every run. */
+ibl_status ibl_server_destroy(ibl_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1315,7 +1315,9 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   ib_free(c);
   const int m = c->m_total;
   if (m == 0) return cudaSuccess;
-  c->cap_slots = (int)std::min<long long>((long long)c->tg.n_tiles, 8LL * m + 64);
+  // band slots: a sheet of unit-spaced markers touches well under one tile per
+  // marker; overflow is reported as IBL_EINVAL rather than silently dropped
+  c->cap_slots = (int)std::min<long long>((long long)c->tg.n_tiles, (long long)m + 4096);
   const size_t rs = real_size(c);
   IBL_CU(cudaMalloc(&c->d_X0, sizeof(double) * 3 * m));
   IBL_CU(cudaMalloc(&c->d_ds, sizeof(double) * m));

@@ -1,0 +1,351 @@
+// Serving form: continuous batching of parameter-sweep runs on one GPU.
+//
+// A background thread owns every run's context.  Each pass it
+//   1. admits queued requests in arrival order while the active count and the
+//      HBM budget allow (a run's device footprint is estimated from its grid,
+//      lattice, precision and marker count before its context is created);
+//   2. enqueues the next chunk of steps of every active run whose previous
+//      chunk has finished (each run has its own CUDA stream, so the chunks of
+//      different runs overlap on the device);
+//   3. retires finished runs: reads their force histories, reduces them to
+//      the per-wing maxima and means of C_L and C_T (the quantities of the
+//      paper's parametric study, Sec. 3.4-3.7 and Fig. 11), destroys the
+//      context and returns its memory to the budget.
+// Every run advances through exactly the same kernel sequence as it would
+// alone, so its result does not depend on what else is running.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "ibl_internal.cuh"
+
+namespace {
+
+using clock_type = std::chrono::steady_clock;
+
+struct Run {
+  int64_t id = 0;
+  ibl_run_request req{};
+  ibl_run_result res{};
+  ibl_ctx* ctx = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool inflight = false;
+  size_t bytes = 0;
+  int m[2] = {0, 0};
+};
+
+}  // namespace
+
+struct ibl_server {
+  ibl_server_config cfg{};
+  int device = 0;
+  clock_type::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::shared_ptr<Run>> queue;
+  std::vector<std::shared_ptr<Run>> active;
+  std::map<int64_t, std::shared_ptr<Run>> all;
+  int64_t next_id = 1;
+  size_t in_use = 0;
+  int finished = 0;
+  std::atomic<bool> stop{false};
+  std::thread worker;
+  std::string err;
+};
+
+namespace {
+
+double now_s(const ibl_server* s) {
+  return std::chrono::duration<double>(clock_type::now() - s->t0).count();
+}
+
+// Flat elliptic planform (chord c, span 5c), unit-spaced cell-centred marker
+// mesh clipped to the ellipse; body frame x chordwise (leading edge at -c/2),
+// y normal, z spanwise.  Each marker carries its cell's area.
+void planform(double chord, std::vector<double>& X0, std::vector<double>& ds) {
+  const double a = 0.5 * chord, b = 2.5 * chord;
+  const int ni = (int)std::ceil(a) + 1, nk = (int)std::ceil(b) + 1;
+  X0.clear();
+  ds.clear();
+  for (int i = -ni; i < ni; ++i)
+    for (int k = -nk; k < nk; ++k) {
+      const double x = i + 0.5, z = k + 0.5;
+      if ((x / a) * (x / a) + (z / b) * (z / b) <= 1.0) {
+        X0.push_back(x);
+        X0.push_back(0.0);
+        X0.push_back(z);
+        ds.push_back(1.0);
+      }
+    }
+}
+
+size_t estimate_bytes(const ibl_run_request& r, int m_total, int m_body) {
+  const size_t N = (size_t)r.nx * r.ny * r.nz;
+  const size_t elem = r.precision == IBL_FP64 ? 8 : (r.precision == IBL_FP32 ? 4 : 2);
+  size_t b = 2 * 19 * N * elem;                                     // populations
+  const size_t tiles = (N + ibl::TILE_CELLS - 1) / ibl::TILE_CELLS;
+  const size_t slots = std::min<size_t>(tiles, (size_t)m_total + 4096);
+  const size_t rs = r.precision == IBL_FP64 ? 8 : 4;
+  b += tiles * 4 + slots * (7 * ibl::TILE_CELLS * rs + 3 * ibl::TILE_CELLS * 8 + ibl::TILE_MARKER_CAP * 4 + 16);
+  b += (size_t)m_total * (ibl::G_MAXNNZ * 12 + 320 * 4 + 64 * 8 + 12 * 8);
+  b += 2 * (size_t)m_body * ((m_body + 3) & ~3) * 4;                // dense preconditioners
+  b += 2 * (size_t)ibl::HIST_LEN * 3 * 8;                            // force histories
+  return b + (64u << 20);                                           // slack
+}
+
+// Build the context of a clap-and-fling wing pair (Sec. 3.3): trailing-edge
+// hinges c/2 apart about the mid-plane, opening angle (pi/3)|sin(2 pi t/T)|
+// per wing, Re = U_tip c / nu with U_tip = 2 Phi f c, Phi = 120 degrees
+// (Eq. 24), tau = 3 nu + 1/2 (Eq. 3), free stream U_inf = J U_tip.
+ibl_status build_run(Run& run) {
+  const ibl_run_request& r = run.req;
+  const double pi = 3.14159265358979323846;
+  const double f = 1.0 / r.period;
+  const double u_tip = 2.0 * (2.0 * pi / 3.0) * f * r.chord;
+  const double nu = u_tip * r.chord / r.Re;
+  const double tau = 3.0 * nu + 0.5;
+  const double u_inf = r.J * u_tip;
+  ibl_grid g{};
+  g.nx = r.nx; g.ny = r.ny; g.nz = r.nz;
+  const int xface0 = r.faces ? IBL_VEL_INLET : IBL_PERIODIC;
+  const int xface1 = r.faces ? IBL_PRESS_OUTLET : IBL_PERIODIC;
+  const int bc[6] = {xface0, xface1, IBL_PERIODIC, IBL_PERIODIC, IBL_PERIODIC, IBL_PERIODIC};
+  for (int i = 0; i < 6; ++i) g.bc[i] = bc[i];
+  g.u_in[0] = u_inf;
+  g.rho_out = 1.0;
+  g.precision = r.precision;
+  ibl_status st = ibl_create(&g, tau, IBL_D3Q19, &run.ctx);
+  if (st != IBL_OK) return st;
+  std::vector<double> X0, ds;
+  planform(r.chord, X0, ds);
+  const int m = (int)ds.size();
+  const double hx = std::round(r.nx / 3.0), ymid = 0.5 * r.ny, zc = 0.5 * r.nz, gap = 0.5 * r.chord;
+  const double hinge[3] = {0.5 * r.chord, 0.0, 0.0};
+  for (int w = 0; w < 2; ++w) {
+    const double side = w == 0 ? -1.0 : 1.0;
+    const double axis[3] = {0.0, 0.0, w == 0 ? 1.0 : -1.0};
+    const double origin[3] = {hx - 0.5 * r.chord, ymid + side * 0.5 * gap, zc};
+    int32_t bid = -1;
+    st = ibl_set_markers(run.ctx, m, X0.data(), ds.data(), hinge, axis, origin, &bid);
+    if (st != IBL_OK) return st;
+    ibl_wave A{IBL_WAVE_CONST, 0.0, 0.0, nullptr, 0};
+    ibl_wave al{IBL_WAVE_ABS_SIN, pi / 3.0, 0.0, nullptr, 0};
+    st = ibl_set_kinematics(run.ctx, bid, &A, &al, 0.0, 0.0, f, r.J);
+    if (st != IBL_OK) return st;
+    const double lift[3] = {0.0, side, 0.0};
+    st = ibl_set_lift_axis(run.ctx, bid, lift);
+    if (st != IBL_OK) return st;
+    run.m[w] = m;
+  }
+  st = ibl_set_reference(run.ctx, u_tip, (double)m, 1.0);
+  if (st != IBL_OK) return st;
+  std::vector<double> u(3 * (size_t)g.nx * g.ny * g.nz, 0.0);
+  std::fill(u.begin(), u.begin() + (size_t)g.nx * g.ny * g.nz, u_inf);
+  st = ibl_init_fluid(run.ctx, nullptr, u.data());
+  if (st != IBL_OK) return st;
+  return cudaEventCreateWithFlags(&run.ev, cudaEventDisableTiming) == cudaSuccess ? IBL_OK : IBL_ECUDA;
+}
+
+void retire(ibl_server* s, Run& run, ibl_status st) {
+  ibl_run_result& res = run.res;
+  res.status = st;
+  if (st == IBL_OK || st == IBL_ENOTCONV) {
+    std::vector<double> h(3 * (size_t)std::max<int64_t>(run.req.steps, 1));
+    for (int w = 0; w < 2; ++w) {
+      int64_t n = 0;
+      const ibl_status hs = ibl_force_history(run.ctx, w, run.req.steps, h.data(), &n);
+      if (hs != IBL_OK && hs != IBL_ENOTCONV) {
+        res.status = hs;
+        break;
+      }
+      double clmax = -1e300, ctmax = -1e300, clsum = 0, ctsum = 0;
+      for (int64_t k = 0; k < n; ++k) {
+        clmax = std::max(clmax, h[3 * k]);
+        ctmax = std::max(ctmax, h[3 * k + 1]);
+        clsum += h[3 * k];
+        ctsum += h[3 * k + 1];
+      }
+      res.CL_max[w] = n ? clmax : 0;
+      res.CT_max[w] = n ? ctmax : 0;
+      res.CL_mean[w] = n ? clsum / n : 0;
+      res.CT_mean[w] = n ? ctsum / n : 0;
+      res.CL_last[w] = n ? h[3 * (n - 1)] : 0;
+      res.CT_last[w] = n ? h[3 * (n - 1) + 1] : 0;
+    }
+  }
+  if (run.ev) cudaEventDestroy(run.ev);
+  run.ev = nullptr;
+  ibl_destroy(run.ctx);
+  run.ctx = nullptr;
+  res.finish_s = now_s(s);
+  res.done = 1;
+  s->in_use -= run.bytes;
+  s->finished++;
+}
+
+void worker_loop(ibl_server* s) {
+  cudaSetDevice(s->device);
+  while (!s->stop.load()) {
+    bool busy = false;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      // 1. admission by arrival order, active count and HBM budget
+      while (!s->queue.empty() && (int)s->active.size() < s->cfg.max_active) {
+        auto run = s->queue.front();
+        if (s->in_use + run->bytes > s->cfg.hbm_budget_bytes && !s->active.empty()) break;
+        s->queue.pop_front();
+        s->in_use += run->bytes;
+        const ibl_status st = build_run(*run);
+        run->res.start_s = now_s(s);
+        if (st != IBL_OK) {
+          if (run->ctx) {
+            retire(s, *run, st);
+          } else {
+            run->res.status = st;
+            run->res.done = 1;
+            run->res.finish_s = now_s(s);
+            s->in_use -= run->bytes;
+            s->finished++;
+          }
+          continue;
+        }
+        s->active.push_back(run);
+        busy = true;
+      }
+      // 2. next chunk of every run whose previous chunk finished; 3. retire
+      for (size_t i = 0; i < s->active.size();) {
+        Run& r = *s->active[i];
+        if (r.inflight) {
+          const cudaError_t q = cudaEventQuery(r.ev);
+          if (q == cudaErrorNotReady) {
+            ++i;
+            continue;
+          }
+          r.inflight = false;
+        }
+        if (r.res.steps_done >= r.req.steps) {
+          retire(s, r, ibl_sync(r.ctx));
+          s->active.erase(s->active.begin() + i);
+          s->cv.notify_all();
+          busy = true;
+          continue;
+        }
+        const int64_t n = std::min<int64_t>(s->cfg.chunk_steps, r.req.steps - r.res.steps_done);
+        const ibl_status st = ibl_step(r.ctx, n);
+        if (st != IBL_OK) {
+          retire(s, r, st);
+          s->active.erase(s->active.begin() + i);
+          s->cv.notify_all();
+          continue;
+        }
+        void* stream = nullptr;
+        ibl_stream(r.ctx, &stream);
+        cudaEventRecord(r.ev, (cudaStream_t)stream);
+        r.inflight = true;
+        r.res.steps_done += n;
+        busy = true;
+        ++i;
+      }
+    }
+    if (!busy) std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+ibl_status ibl_server_create(const ibl_server_config* cfg, ibl_server** out) {
+  if (!out || !cfg) return IBL_EINVAL;
+  *out = nullptr;
+  if (cfg->max_active < 1 || cfg->chunk_steps < 1 || cfg->hbm_budget_bytes == 0) return IBL_EINVAL;
+  ibl_server* s = new ibl_server();
+  s->cfg = *cfg;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    return IBL_ECUDA;
+  }
+  s->t0 = clock_type::now();
+  s->worker = std::thread(worker_loop, s);
+  *out = s;
+  return IBL_OK;
+}
+
+ibl_status ibl_server_submit(ibl_server* s, const ibl_run_request* req, int64_t* run_id) {
+  if (!s || !req) return IBL_EINVAL;
+  if (req->nx < 16 || req->ny < 16 || req->nz < 16 || !(req->chord >= 4.0) || !(req->Re > 0) ||
+      !(req->period > 0) || !(req->J >= 0) || req->steps < 1 || req->steps > ibl::HIST_LEN ||
+      req->precision < IBL_FP64 || req->precision > IBL_BF16DEV)
+    return IBL_EINVAL;
+  // the wings must fit: chord and span within the box with stencil margins
+  if (req->chord * 5.0 + 8 > req->nz || std::round(req->nx / 3.0) - req->chord < 4 ||
+      0.5 * req->ny - 0.25 * req->chord - req->chord < 4)
+    return IBL_EINVAL;
+  auto run = std::make_shared<Run>();
+  run->req = *req;
+  std::vector<double> X0, ds;
+  planform(req->chord, X0, ds);
+  const int m = (int)ds.size();
+  run->bytes = estimate_bytes(*req, 2 * m, m);
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (run->bytes > s->cfg.hbm_budget_bytes) return IBL_ENOMEM;
+  run->id = s->next_id++;
+  run->res.submit_s = now_s(s);
+  run->res.status = IBL_OK;
+  s->queue.push_back(run);
+  s->all[run->id] = run;
+  if (run_id) *run_id = run->id;
+  return IBL_OK;
+}
+
+ibl_status ibl_server_poll(ibl_server* s, int64_t run_id, ibl_run_result* out) {
+  if (!s || !out) return IBL_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->all.find(run_id);
+  if (it == s->all.end()) return IBL_EINVAL;
+  *out = it->second->res;
+  return IBL_OK;
+}
+
+ibl_status ibl_server_wait_all(ibl_server* s, double timeout_s) {
+  if (!s) return IBL_EINVAL;
+  std::unique_lock<std::mutex> lock(s->mu);
+  const auto deadline = clock_type::now() + std::chrono::duration<double>(timeout_s);
+  while (!(s->queue.empty() && s->active.empty())) {
+    if (s->cv.wait_until(lock, deadline) == std::cv_status::timeout &&
+        !(s->queue.empty() && s->active.empty()))
+      return IBL_ETIMEOUT;
+  }
+  return IBL_OK;
+}
+
+ibl_status ibl_server_stats(ibl_server* s, int32_t* queued, int32_t* active, int32_t* finished,
+                            int64_t* hbm_in_use) {
+  if (!s) return IBL_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (queued) *queued = (int32_t)s->queue.size();
+  if (active) *active = (int32_t)s->active.size();
+  if (finished) *finished = s->finished;
+  if (hbm_in_use) *hbm_in_use = (int64_t)s->in_use;
+  return IBL_OK;
+}
+
+ibl_status ibl_server_destroy(ibl_server* s) {
+  if (!s) return IBL_OK;
+  s->stop.store(true);
+  if (s->worker.joinable()) s->worker.join();
+  for (auto& r : s->active)
+    if (r->ctx) ibl_destroy(r->ctx);
+  delete s;
+  return IBL_OK;
+}
+
+}  // extern "C"

@@ -43,6 +43,23 @@ class ibl_wave(C.Structure):
                 ("table", C.POINTER(C.c_double)), ("n_table", C.c_int64)]
 
 
+class ibl_server_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_active", C.c_int32), ("chunk_steps", C.c_int32)]
+
+
+class ibl_run_request(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("chord", C.c_double),
+                ("Re", C.c_double), ("period", C.c_double), ("J", C.c_double), ("precision", C.c_int32),
+                ("faces", C.c_int32), ("steps", C.c_int64)]
+
+
+class ibl_run_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("done", C.c_int32), ("steps_done", C.c_int64),
+                ("submit_s", C.c_double), ("start_s", C.c_double), ("finish_s", C.c_double),
+                ("CL_max", C.c_double * 2), ("CL_mean", C.c_double * 2), ("CT_max", C.c_double * 2),
+                ("CT_mean", C.c_double * 2), ("CL_last", C.c_double * 2), ("CT_last", C.c_double * 2)]
+
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _I32 = C.POINTER(C.c_int32)
@@ -77,6 +94,12 @@ _SIGS = {
     "ibl_launch_count": ([_P, _I64], C.c_int),
     "ibl_stream": ([_P, C.POINTER(_P)], C.c_int),
     "ibl_last_error": ([_P], C.c_char_p),
+    "ibl_server_create": ([C.POINTER(ibl_server_config), C.POINTER(_P)], C.c_int),
+    "ibl_server_submit": ([_P, C.POINTER(ibl_run_request), _I64], C.c_int),
+    "ibl_server_poll": ([_P, C.c_int64, C.POINTER(ibl_run_result)], C.c_int),
+    "ibl_server_wait_all": ([_P, C.c_double], C.c_int),
+    "ibl_server_stats": ([_P, _I32, _I32, _I32, _I64], C.c_int),
+    "ibl_server_destroy": ([_P], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -331,3 +354,56 @@ def from_workload(cfg: dict, init: bool = True) -> Context:
         else:
             ctx.ibl_init_fluid(None, np.asarray(cfg.get("u0", (0.0, 0.0, 0.0)))[:ctx.d])
     return ctx
+
+
+class Server:
+    """Continuous-batching server of clap-and-fling runs (ibl_server_* calls)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 8, chunk_steps: int = 50):
+        cfg = ibl_server_config(int(hbm_budget_bytes), int(max_active), int(chunk_steps))
+        h = _P()
+        st = _lib.ibl_server_create(C.byref(cfg), C.byref(h))
+        if st != IBL_OK:
+            raise IblError(st, "ibl_server_create failed")
+        self.h = h
+
+    def ibl_server_submit(self, nx, ny, nz, chord, Re, period, J, precision="fp32", steps=1000, faces=0):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        req = ibl_run_request(int(nx), int(ny), int(nz), float(chord), float(Re), float(period), float(J),
+                              prec, int(faces), int(steps))
+        rid = C.c_int64()
+        st = _lib.ibl_server_submit(self.h, C.byref(req), C.byref(rid))
+        if st != IBL_OK:
+            raise IblError(st, "ibl_server_submit rejected the request")
+        return rid.value
+
+    def ibl_server_poll(self, run_id):
+        r = ibl_run_result()
+        st = _lib.ibl_server_poll(self.h, int(run_id), C.byref(r))
+        if st != IBL_OK:
+            raise IblError(st, "unknown run id")
+        return {"status": r.status, "done": bool(r.done), "steps_done": r.steps_done,
+                "submit_s": r.submit_s, "start_s": r.start_s, "finish_s": r.finish_s,
+                "CL_max": list(r.CL_max), "CL_mean": list(r.CL_mean), "CT_max": list(r.CT_max),
+                "CT_mean": list(r.CT_mean), "CL_last": list(r.CL_last), "CT_last": list(r.CT_last)}
+
+    def ibl_server_wait_all(self, timeout_s=3600.0):
+        st = _lib.ibl_server_wait_all(self.h, float(timeout_s))
+        if st != IBL_OK:
+            raise IblError(st, "ibl_server_wait_all timed out")
+
+    def ibl_server_stats(self):
+        q, a, f, b = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
+        _lib.ibl_server_stats(self.h, C.byref(q), C.byref(a), C.byref(f), C.byref(b))
+        return {"queued": q.value, "active": a.value, "finished": f.value, "hbm_in_use": b.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ibl_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,76 @@
+"""Serving form: continuous batching of clap-and-fling runs (GPU).
+
+A run's result must not depend on what else is running: the same request
+alone and inside a mix of concurrent, later-arriving runs gives bitwise the
+same force statistics.  The server's runs also match a direct run of the
+same wing pair through the plain C ABI."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REQ = dict(nx=64, ny=48, nz=48, chord=6.0, Re=20.0, period=600.0, J=1e-2, precision="fp32", steps=150)
+OTHERS = [dict(nx=72, ny=48, nz=48, chord=6.0, Re=10.0, period=400.0, J=0.1, precision="fp16dev", steps=120),
+          dict(nx=64, ny=56, nz=48, chord=7.0, Re=30.0, period=800.0, J=1e-3, precision="fp32", steps=200),
+          dict(nx=48, ny=48, nz=40, chord=6.0, Re=15.0, period=500.0, J=2e-2, precision="bf16dev", steps=100)]
+
+
+def _keys(r):
+    return (tuple(r["CL_max"]), tuple(r["CL_mean"]), tuple(r["CT_max"]), tuple(r["CT_mean"]),
+            tuple(r["CL_last"]), tuple(r["CT_last"]))
+
+
+def test_result_is_the_same_alone_and_in_the_mix(ibl):
+    alone = ibl.Server(hbm_budget_bytes=8 << 30, max_active=4, chunk_steps=25)
+    rid = alone.ibl_server_submit(**REQ)
+    alone.ibl_server_wait_all(600)
+    ra = alone.ibl_server_poll(rid)
+    alone.close()
+    assert ra["done"] and ra["status"] == ibl.IBL_OK
+
+    mix = ibl.Server(hbm_budget_bytes=8 << 30, max_active=3, chunk_steps=25)
+    ids = [mix.ibl_server_submit(**OTHERS[0])]
+    time.sleep(0.05)
+    rid = mix.ibl_server_submit(**REQ)                  # arrives while another run is active
+    for o in OTHERS[1:]:
+        time.sleep(0.02)
+        ids.append(mix.ibl_server_submit(**o))         # arrive later, queue behind max_active
+    mix.ibl_server_wait_all(600)
+    rm = mix.ibl_server_poll(rid)
+    others = [mix.ibl_server_poll(i) for i in ids]
+    stats = mix.ibl_server_stats()
+    mix.close()
+    assert rm["done"] and rm["status"] == ibl.IBL_OK
+    assert _keys(ra) == _keys(rm)
+    assert all(o["done"] for o in others) and stats["finished"] == 4 and stats["hbm_in_use"] == 0
+
+
+def test_server_run_matches_a_direct_run(ibl):
+    srv = ibl.Server(hbm_budget_bytes=8 << 30, max_active=2, chunk_steps=40)
+    rid = srv.ibl_server_submit(**REQ)
+    srv.ibl_server_wait_all(600)
+    r = srv.ibl_server_poll(rid)
+    srv.close()
+    cfg = W.clap_fling_3d(nx=REQ["nx"], ny=REQ["ny"], nz=REQ["nz"], chord=REQ["chord"], Re=REQ["Re"],
+                          J=REQ["J"], period=REQ["period"], faces="periodic")
+    ctx = ibl.from_workload(cfg)
+    ctx.ibl_step(REQ["steps"])
+    for w in range(2):
+        h = ctx.ibl_force_history(w, REQ["steps"])
+        assert np.isclose(h[:, 0].max(), r["CL_max"][w], rtol=1e-12, atol=0)
+        assert np.isclose(h[:, 1].mean(), r["CT_mean"][w], rtol=1e-10, atol=1e-14)
+
+
+def test_budget_and_validation(ibl):
+    srv = ibl.Server(hbm_budget_bytes=1 << 20, max_active=2, chunk_steps=10)
+    with pytest.raises(ibl.IblError) as e:
+        srv.ibl_server_submit(**REQ)              # larger than the whole budget
+    assert e.value.status == ibl.IBL_ENOMEM
+    with pytest.raises(ibl.IblError) as e:
+        srv.ibl_server_submit(**dict(REQ, nz=20))  # the span does not fit
+    assert e.value.status == ibl.IBL_EINVAL
+    srv.close()
