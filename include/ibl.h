@@ -238,7 +238,7 @@ ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_resid
  * preconditioner is rebuilt every refresh_every steps (default 128) and
  * early when a solve needed more than 40 iterations; tol is the relative
  * residual in the preconditioner's norm (0 = default: 1e-10 for FP64
- * storage, 1e-8 otherwise); extrapolate != 0 starts each solve from
+ * storage, 1e-7 for FP32, 1e-6 for FP16/BF16); extrapolate != 0 starts each solve from
  * 2 w_{n-1} - w_{n-2} instead of w_{n-1} (default on).  Changing these
  * changes the iterates, not the system being solved. */
 ibl_status ibl_solver_config(ibl_ctx* ctx, int32_t refresh_every, double tol, int32_t extrapolate);

@@ -8,18 +8,18 @@
 //   k_mark/assign/append
 //                    grid tiles touched by a stencil get a band slot and a
 //                    list of the markers that touch them;
-//   k_band_moments   rho and u* = (sum c_i f_i + G/2)/rho on band tiles (Eq. 11);
-//   k_interpolate    rho_l and u*_l (Eq. 17); B = U_B - u*_l (Eq. 19);
+//   k_interpolate    rho_l and u*_l (Eq. 17) from the populations of the stencil
+//                    nodes (moments of Eq. 11); B = U_B - u*_l (Eq. 19);
 //   k_assemble       sparse G_lk = sum_x D(x-X_l) D(x-X_k) (Eq. 18 without
 //                    ds_k: the solve is run on w = ds * du_B, G w = B);
 //   k_pcg            preconditioned conjugate gradients for the three velocity
 //                    components at once, FP64 vectors and SpMV, an FP32 dense
 //                    per-body approximate inverse as preconditioner, rebuilt
 //                    in-kernel (blocked Gauss-Jordan) every few steps;
-//   k_spread         du(x) = sum_l w_l D(x - X_l) (Eq. 15) as a per-tile gather
-//                    over the tile's markers in marker-index order (no float
-//                    atomics), F = 2 rho du (Eq. 26) into the band force;
-//   k_force_reduce   F_w = -sum_l 2 rho_l w_l per body in FP64, fixed order.
+//   k_spread_scatter du(x) = sum_l w_l D(x - X_l) (Eq. 15) into 64-bit
+//                    fixed-point band accumulators (order-independent sums);
+//                    the collide kernel forms F = 2 rho du (Eq. 26) from them;
+//   (end of k_pcg)   F_w = -sum_l 2 rho_l w_l per body in FP64, fixed order.
 #include <cooperative_groups.h>
 
 #include "ibl_internal.cuh"
@@ -31,8 +31,11 @@ namespace ibl {
 constexpr int MAX_BODIES = 16;
 constexpr int GJ_NB = 64;          // Gauss-Jordan pivot block
 constexpr int PCG_MAX_ITERS = 200;
-constexpr double PCG_TOL = 1e-10;      // relative preconditioned residual (field A-norm), FP64 storage
-constexpr double PCG_TOL_LOW = 1e-8;   // FP32 / 16-bit storage: two decades under their rounding
+// relative preconditioned residual (the spread field's A-norm error) per
+// storage precision: about two decades under what the storage resolves
+constexpr double PCG_TOL = 1e-10;       // FP64
+constexpr double PCG_TOL_FP32 = 1e-7;   // FP32 deviations
+constexpr double PCG_TOL_HALF = 1e-6;   // FP16 / BF16 deviations
 
 constexpr int REFRESH_ITERS = 40;  // rebuild early if a solve needed more
 
@@ -81,16 +84,12 @@ __device__ void wave_eval(const Wave& w, double t, double f, double phi, double&
 }
 
 // ------------------------------------------------------------------ kinematics + stencil
-// One thread per body: wave values and rates (Eqs. 20-23) and the rotation's
-// cosine and sine at time t, shared by all of the body's markers.
-__global__ void k_body_state(BodyTable bt, double t, double* __restrict__ bstate) {
-  const int b = threadIdx.x;
-  if (b >= bt.n) return;
-  const BodyDev& B = bt.b[b];
+// Wave values and rates (Eqs. 20-23) and the rotation's cosine and sine at
+// time t for body b, shared by all of the body's markers.
+__device__ void body_state(const BodyDev& B, double t, double st[8]) {
   double A, Ad, al, ald;
   wave_eval(B.A, t, B.f, B.phi, A, Ad);
   wave_eval(B.alpha, t, B.f, B.phi, al, ald);
-  double* st = bstate + 8 * b;
   st[0] = A;
   st[1] = Ad;
   st[2] = ald;
@@ -101,12 +100,14 @@ __global__ void k_body_state(BodyTable bt, double t, double* __restrict__ bstate
   st[7] = al;
 }
 
-__global__ void k_kinematics(BodyTable bt, const double* __restrict__ bstate, int m_total,
-                             const int* __restrict__ body_of,
+__global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ body_of,
                              const double* __restrict__ X0, const double* __restrict__ Xp,
                              const double* __restrict__ Up, double* __restrict__ X,
                              double* __restrict__ U, int* __restrict__ base,
                              double* __restrict__ wts, double t, Geo geo, int* status) {
+  __shared__ double sst[MAX_BODIES][8];
+  if (threadIdx.x < bt.n) body_state(bt.b[threadIdx.x], t, sst[threadIdx.x]);
+  __syncthreads();
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= m_total) return;
   const BodyDev& B = bt.b[body_of[l]];
@@ -114,8 +115,8 @@ __global__ void k_kinematics(BodyTable bt, const double* __restrict__ bstate, in
   if (B.prescribed) {
     for (int a = 0; a < 3; ++a) { x[a] = Xp[3 * l + a]; u[a] = Up[3 * l + a]; }
   } else {
-    // per-body motion state of this step (k_body_state): A, A', alpha', cos, sin, e_s
-    const double* st = bstate + 8 * body_of[l];
+    // per-body motion state of this step: A, A', alpha', cos, sin, e_s
+    const double* st = sst[body_of[l]];
     const double A = st[0], Ad = st[1], ald = st[2], c = st[3], s = st[4];
     const double es[3] = {st[5], st[6], 0.0};
     const double* e = B.axis;
@@ -254,59 +255,16 @@ __global__ void k_append_markers(int m_total, const int* __restrict__ base, Geo 
 
 namespace ibl {
 
+// rho_l and u*_l (Eq. 17) gathered straight from the populations of each
+// stencil node (the same pull, face rules and moment arithmetic as the
+// collision), FP64 accumulation; B = U_B - u*_l (Eq. 19).  One warp per
+// marker, 64 (3D) or 16 (2D) nodes over its lanes.
 template <int Q, class T, bool PULL>
-__global__ void k_band_moments(const T* __restrict__ src, FluidParams<typename Store<T>::R> p,
-                               const int* __restrict__ slot_tile, const int* __restrict__ band_count,
-                               int cap, typename Store<T>::R* __restrict__ band_mom) {
-  using R = typename Store<T>::R;
-  const int n = min(*band_count, cap);
-  const TileGeom& tg = p.tg;
-  for (int s = blockIdx.x; s < n; s += gridDim.x) {
-    const int tile = slot_tile[s];
-    const int tx0 = (tile % tg.ntx) * tg.tx;
-    const int ty0 = ((tile / tg.ntx) % tg.nty) * tg.ty;
-    const int tz0 = (tile / (tg.ntx * tg.nty)) * tg.tz;
-    const int local = threadIdx.x;
-    const int lx = local % tg.tx, ly = (local / tg.tx) % tg.ty, lz = local / (tg.tx * tg.ty);
-    const int x = tx0 + lx, y = ty0 + ly, z = tz0 + lz;
-    R rho = R(1), u0 = R(0), u1 = R(0), u2 = R(0);
-    if (x < p.nx && y < p.ny && z < p.nz) {
-      const long long cell = ((long long)z * p.ny + y) * p.nx + x;
-      R g[Q];
-      gather_q<Q, T, PULL, R>(src, x, y, z, cell, p, g);
-      R drho = R(0), m0 = R(0), m1 = R(0), m2 = R(0);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        drho += g[i];
-        if (Lat<Q>::cx(i)) m0 += R(Lat<Q>::cx(i)) * g[i];
-        if (Lat<Q>::cy(i)) m1 += R(Lat<Q>::cy(i)) * g[i];
-        if (Lat<Q>::cz(i)) m2 += R(Lat<Q>::cz(i)) * g[i];
-      }
-      rho = R(1) + drho;
-      // Eq. 11 with the uniform body force; u = m - m drho/(1 + drho) keeps
-      // drho's low bits (as the collision does)
-      const R q = drho / rho;
-      u0 = m0 + R(0.5) * p.G[0];
-      u1 = m1 + R(0.5) * p.G[1];
-      u2 = m2 + R(0.5) * p.G[2];
-      u0 -= u0 * q;
-      u1 -= u1 * q;
-      u2 -= u2 * q;
-    }
-    R* o = band_mom + (long long)s * 4 * TILE_CELLS + local;
-    o[0] = rho;
-    o[TILE_CELLS] = u0;
-    o[2 * TILE_CELLS] = u1;
-    o[3 * TILE_CELLS] = u2;
-  }
-}
-
-// ------------------------------------------------------------------ interpolation
-template <class R>
 __global__ void k_interpolate(int m_total, const int* __restrict__ base, const double* __restrict__ wts,
-                              const R* __restrict__ band_mom, const int* __restrict__ tile_slot, Geo g,
+                              const T* __restrict__ src, FluidParams<typename Store<T>::R> p, Geo g,
                               const double* __restrict__ U, double* __restrict__ rho_l,
                               double* __restrict__ B) {
+  using R = typename Store<T>::R;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= m_total) return;
@@ -321,15 +279,28 @@ __global__ void k_interpolate(int m_total, const int* __restrict__ base, const d
     for (int a = 0; a < g.D; ++a)
       if (g.per[a]) node[a] = wrap(node[a], g.n[a]);
     const double wt = w[i] * w[4 + j] * w[8 + (g.D == 3 ? q : 0)];
-    const int tile = tile_of(g, node[0], node[1], node[2]);
-    const int s = tile_slot[tile];
-    if (s < 0) continue;   // cannot happen: every stencil tile has a slot
-    const int local = ((node[2] % g.tg.tz) * g.tg.ty + (node[1] % g.tg.ty)) * g.tg.tx + (node[0] % g.tg.tx);
-    const R* mo = band_mom + (long long)s * 4 * TILE_CELLS + local;
-    acc[0] += wt * (double)mo[0];
-    acc[1] += wt * (double)mo[TILE_CELLS];
-    acc[2] += wt * (double)mo[2 * TILE_CELLS];
-    acc[3] += wt * (double)mo[3 * TILE_CELLS];
+    const long long cell = ((long long)node[2] * p.ny + node[1]) * p.nx + node[0];
+    R gg[Q];
+    gather_q<Q, T, PULL, R>(src, node[0], node[1], node[2], cell, p, gg);
+    R drho = gg[0], m0 = R(0), m1 = R(0), m2 = R(0);
+#pragma unroll
+    for (int e = 1; e < Q; e += 2) {
+      drho += gg[e] + gg[e + 1];
+      const R d = gg[e] - gg[e + 1];
+      if (Lat<Q>::cx(e)) m0 += R(Lat<Q>::cx(e)) * d;
+      if (Lat<Q>::cy(e)) m1 += R(Lat<Q>::cy(e)) * d;
+      if (Lat<Q>::cz(e)) m2 += R(Lat<Q>::cz(e)) * d;
+    }
+    // Eq. 11 with the uniform body force: u* = (m + G/2) / rho, as m - m drho / rho
+    const R qd = drho / (R(1) + drho);
+    R u0 = m0 + R(0.5) * p.G[0], u1 = m1 + R(0.5) * p.G[1], u2 = m2 + R(0.5) * p.G[2];
+    u0 -= u0 * qd;
+    u1 -= u1 * qd;
+    u2 -= u2 * qd;
+    acc[0] += wt * (1.0 + (double)drho);
+    acc[1] += wt * (double)u0;
+    acc[2] += wt * (double)u1;
+    acc[3] += wt * (double)u2;
   }
   for (int o = 16; o > 0; o >>= 1)
     for (int c = 0; c < 4; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
@@ -552,6 +523,11 @@ struct PcgArgs {
   int refresh;      // host-scheduled rebuild
   int* status;
   unsigned long long* trace;   // optional phase timestamps (ns), see ibl_solver_trace
+  // body-force reduction after the solve (Sec. 3.7)
+  const double* rho_l;
+  double* mforce;
+  double* hist;
+  long long step;
 };
 
 __device__ __forceinline__ void trace_mark(const PcgArgs& A, int slot) {
@@ -1182,6 +1158,24 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     done = s_done != 0;
   }
   trace_mark(A, 3);
+  // ---- body forces F_w = -sum_l 2 rho_l w_l (Eq. 26 x ds, Sec. 3.7): block b reduces
+  // body b in a fixed order (lane-strided FP64 sums, fixed shuffle tree, warp order)
+  for (int b = blockIdx.x; b < A.nbodies; b += gridDim.x) {
+    double v[3] = {0, 0, 0};
+    for (int l = A.boff[b] + threadIdx.x; l < A.boff[b + 1]; l += blockDim.x)
+      for (int c = 0; c < 3; ++c) {
+        const double f = 2.0 * A.rho_l[l] * A.w[3 * l + c];   // force on the fluid
+        A.mforce[3 * l + c] = f;
+        v[c] += f;
+      }
+    for (int o = 16; o > 0; o >>= 1)
+      for (int c = 0; c < 3; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+    block_total3(v, shd);
+    if (threadIdx.x == 0) {
+      double* h = A.hist + ((long long)b * HIST_LEN + (A.step % HIST_LEN)) * 3;
+      for (int c = 0; c < 3; ++c) h[c] = -v[c];   // force on the body
+    }
+  }
   if (gtid == 0) {
     double rel = 0.0;
     for (int c = 0; c < A.D; ++c)
@@ -1199,8 +1193,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
 // each marker's 64 (16 in 2D) stencil nodes into 64-bit fixed-point
 // accumulators of the band: integer addition is associative, so the sums
 // are bitwise independent of the order the atomics land in.
-constexpr double FIX_SCALE = 70368744177664.0;   // 2^46: |sum| < 1.3e5, resolution 1.4e-14
-constexpr double FIX_LIMIT = 9.0e18 / FIX_SCALE;
+constexpr double FIX_LIMIT = 9.0e18 / FIX_SCALE;   // |sum| < 1.3e5 at 2^46, resolution 1.4e-14
 
 __global__ void k_spread_scatter(int m_total, const int* __restrict__ base, const double* __restrict__ wts,
                                  const double* __restrict__ wsol, const int* __restrict__ tile_slot, Geo g,
@@ -1227,56 +1220,7 @@ __global__ void k_spread_scatter(int m_total, const int* __restrict__ base, cons
   }
 }
 
-// F = 2 rho du on the band (Eq. 26) from the accumulators, which are cleared
-// for the next step.
-template <class R>
-__global__ void k_spread_finalize(const int* __restrict__ band_count, int cap, unsigned long long* __restrict__ acc,
-                                  const R* __restrict__ band_mom, R* __restrict__ band_F, int D) {
-  const int n = min(*band_count, cap);
-  for (int s = blockIdx.x; s < n; s += gridDim.x) {
-    const int local = threadIdx.x;
-    const double rho = (double)band_mom[(long long)s * 4 * TILE_CELLS + local];
-    for (int c = 0; c < 3; ++c) {
-      unsigned long long* a = acc + ((long long)s * 3 + c) * TILE_CELLS + local;
-      const double du = c < D ? (double)(long long)(*a) * (1.0 / FIX_SCALE) : 0.0;   // exact power of 2
-      *a = 0ull;
-      band_F[((long long)s * 3 + c) * TILE_CELLS + local] = (R)(2.0 * rho * du);
-    }
-  }
-}
-
 // ------------------------------------------------------------------ forces
-__global__ void k_force_reduce(int nbodies, const int* __restrict__ boff, const double* __restrict__ rho_l,
-                               const double* __restrict__ wsol, double* __restrict__ mforce,
-                               double* __restrict__ hist, long long step) {
-  __shared__ double sh[8][3];
-  const int b = blockIdx.x;
-  if (b >= nbodies) return;
-  const int o = boff[b], e = boff[b + 1];
-  double v[3] = {0, 0, 0};
-  for (int l = o + threadIdx.x; l < e; l += blockDim.x) {
-    for (int a = 0; a < 3; ++a) {
-      const double f = 2.0 * rho_l[l] * wsol[3 * l + a];   // force on the fluid (Eq. 26 x ds)
-      mforce[3 * l + a] = f;
-      v[a] += f;
-    }
-  }
-  // fixed-order tree: warp shuffles, then warp partials in warp order
-  for (int off = 16; off > 0; off >>= 1)
-    for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0)
-    for (int a = 0; a < 3; ++a) sh[wid][a] = v[a];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t[3] = {0, 0, 0};
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-      for (int a = 0; a < 3; ++a) t[a] += sh[w][a];
-    double* h = hist + ((long long)b * HIST_LEN + (step % HIST_LEN)) * 3;
-    for (int a = 0; a < 3; ++a) h[a] = -t[a];   // force on the body
-  }
-}
-
 // Eulerian IB force density of the last step for every cell (band cells, zero elsewhere).
 template <class R>
 __global__ void k_force_field(long long N, int nx, int ny, TileGeom tg, const int* __restrict__ tile_slot,
@@ -1334,11 +1278,9 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   IBL_CU(cudaMalloc(&c->d_tile_mcount, sizeof(int) * c->cap_slots));
   IBL_CU(cudaMemsetAsync(c->d_tile_mcount, 0, sizeof(int) * c->cap_slots, c->stream));
   IBL_CU(cudaMalloc(&c->d_tile_markers, sizeof(int) * (size_t)c->cap_slots * TILE_MARKER_CAP));
-  IBL_CU(cudaMalloc(&c->d_band_mom, rs * 4 * TILE_CELLS * (size_t)c->cap_slots));
   IBL_CU(cudaMalloc(&c->d_band_F, rs * 3 * TILE_CELLS * (size_t)c->cap_slots));
   IBL_CU(cudaMalloc(&c->d_acc, sizeof(unsigned long long) * 3 * TILE_CELLS * (size_t)c->cap_slots));
   IBL_CU(cudaMemsetAsync(c->d_acc, 0, sizeof(unsigned long long) * 3 * TILE_CELLS * (size_t)c->cap_slots, c->stream));
-  IBL_CU(cudaMalloc(&c->d_bstate, sizeof(double) * 8 * MAX_BODIES));
   IBL_CU(cudaMalloc(&c->d_slot_body, sizeof(int) * c->cap_slots));
   IBL_CU(cudaMemsetAsync(c->d_slot_body, 0xff, sizeof(int) * c->cap_slots, c->stream));
   IBL_CU(cudaMalloc(&c->d_mixed, 2 * sizeof(int)));   // [0] use tiles this step, [1] lists overflowed
@@ -1404,18 +1346,18 @@ cudaError_t ib_alloc(ibl_ctx* c) {
 
 void ib_free(ibl_ctx* c) {
   void* ptrs[] = {c->d_X0, c->d_ds, c->d_body, c->d_X, c->d_U, c->d_Xp, c->d_Up, c->d_tile_slot,
-                  c->d_slot_tile, c->d_band_count, c->d_tile_mcount, c->d_tile_markers, c->d_band_mom,
+                  c->d_slot_tile, c->d_band_count, c->d_tile_mcount, c->d_tile_markers,
                   c->d_band_F, c->d_base, c->d_wts, c->d_rho_l, c->d_B, c->d_w, c->d_r, c->d_p,
                   c->d_Ap, c->d_z, c->d_Gcol, c->d_Gval, c->d_Gnnz, c->d_Gdiag_max, c->d_M, c->d_red,
                   c->d_cg_info, c->d_cg_res, c->d_hist, c->d_mforce, c->d_boff, c->d_xf, c->d_trace,
-                  c->d_acc, c->d_bstate, c->d_slot_body, c->d_mixed, c->d_cand, c->d_ncand,
+                  c->d_acc, c->d_slot_body, c->d_mixed, c->d_cand, c->d_ncand,
                   c->d_wprev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->d_X0 = c->d_ds = c->d_X = c->d_U = c->d_Xp = c->d_Up = nullptr;
   c->d_body = c->d_tile_slot = c->d_slot_tile = c->d_band_count = c->d_tile_mcount = nullptr;
   c->d_tile_markers = c->d_base = c->d_Gcol = c->d_Gnnz = c->d_cg_info = c->d_boff = nullptr;
-  c->d_band_mom = c->d_band_F = nullptr;
+  c->d_band_F = nullptr;
   c->d_wts = nullptr;
   c->d_rho_l = c->d_B = c->d_w = c->d_r = c->d_p = c->d_Ap = c->d_z = c->d_Gval = nullptr;
   c->d_Gdiag_max = c->d_red = c->d_cg_res = c->d_hist = c->d_mforce = nullptr;
@@ -1423,14 +1365,13 @@ void ib_free(ibl_ctx* c) {
   c->d_xf = nullptr;
   c->d_trace = nullptr;
   c->d_acc = nullptr;
-  c->d_bstate = nullptr;
   c->d_slot_body = c->d_mixed = c->d_cand = c->d_ncand = nullptr;
   c->d_wprev = nullptr;
   c->ib_ready = false;
 }
 
 template <int Q, class T>
-static cudaError_t band_moments_q(ibl_ctx* c, int grid) {
+static cudaError_t interpolate_q(ibl_ctx* c, const Geo& g) {
   using R = typename Store<T>::R;
   FluidParams<R> p;
   p.nx = c->nx; p.ny = c->ny; p.nz = c->nz; p.N = c->N;
@@ -1441,33 +1382,34 @@ static cudaError_t band_moments_q(ibl_ctx* c, int grid) {
   p.pref = (R)(1.0 - 0.5 / c->tau);
   p.tg = c->tg;
   p.tile_slot = nullptr;
+  p.band_acc = nullptr;
   p.band_F = nullptr;
   p.status = c->d_status;
   const T* src = (const T*)c->f[c->cur];
+  const int m = c->m_total;
+  const int wb = (m * 32 + 255) / 256;
   if (c->poststream)
-    k_band_moments<Q, T, false><<<grid, TILE_CELLS, 0, c->stream>>>(src, p, c->d_slot_tile, c->d_band_count,
-                                                                  c->cap_slots, (R*)c->d_band_mom);
+    k_interpolate<Q, T, false><<<wb, 256, 0, c->stream>>>(m, c->d_base, c->d_wts, src, p, g, c->d_U, c->d_rho_l, c->d_B);
   else
-    k_band_moments<Q, T, true><<<grid, TILE_CELLS, 0, c->stream>>>(src, p, c->d_slot_tile, c->d_band_count,
-                                                                 c->cap_slots, (R*)c->d_band_mom);
+    k_interpolate<Q, T, true><<<wb, 256, 0, c->stream>>>(m, c->d_base, c->d_wts, src, p, g, c->d_U, c->d_rho_l, c->d_B);
   c->launches++;
   return cudaGetLastError();
 }
 
-static cudaError_t band_moments(ibl_ctx* c, int grid) {
+static cudaError_t interpolate(ibl_ctx* c, const Geo& g) {
   if (c->Q == 9) {
     switch (c->prec) {
-      case IBL_FP64: return band_moments_q<9, double>(c, grid);
-      case IBL_FP32: return band_moments_q<9, float>(c, grid);
-      case IBL_FP16DEV: return band_moments_q<9, __half>(c, grid);
-      default: return band_moments_q<9, __nv_bfloat16>(c, grid);
+      case IBL_FP64: return interpolate_q<9, double>(c, g);
+      case IBL_FP32: return interpolate_q<9, float>(c, g);
+      case IBL_FP16DEV: return interpolate_q<9, __half>(c, g);
+      default: return interpolate_q<9, __nv_bfloat16>(c, g);
     }
   }
   switch (c->prec) {
-    case IBL_FP64: return band_moments_q<19, double>(c, grid);
-    case IBL_FP32: return band_moments_q<19, float>(c, grid);
-    case IBL_FP16DEV: return band_moments_q<19, __half>(c, grid);
-    default: return band_moments_q<19, __nv_bfloat16>(c, grid);
+    case IBL_FP64: return interpolate_q<19, double>(c, g);
+    case IBL_FP32: return interpolate_q<19, float>(c, g);
+    case IBL_FP16DEV: return interpolate_q<19, __half>(c, g);
+    default: return interpolate_q<19, __nv_bfloat16>(c, g);
   }
 }
 
@@ -1504,10 +1446,8 @@ cudaError_t ib_step(ibl_ctx* c) {
   }
   const int tb = 64;
   const int mb = (m + tb - 1) / tb;
-  k_body_state<<<1, 32, 0, c->stream>>>(bt, (double)c->step, c->d_bstate);
-  k_kinematics<<<mb, tb, 0, c->stream>>>(bt, c->d_bstate, m, c->d_body, c->d_X0, c->d_Xp, c->d_Up, c->d_X, c->d_U,
+  k_kinematics<<<mb, tb, 0, c->stream>>>(bt, m, c->d_body, c->d_X0, c->d_Xp, c->d_Up, c->d_X, c->d_U,
                                          c->d_base, c->d_wts, (double)c->step, g, c->d_status);
-  c->launches++;
   const int cg_grid = std::min(c->cap_slots, 4 * g_num_sms);
   k_clear_tiles<<<std::max(1, std::min(c->cap_slots / 256 + 1, g_num_sms)), 256, 0, c->stream>>>(
       c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->d_tile_mcount, c->d_slot_body, c->cap_slots);
@@ -1526,14 +1466,7 @@ cudaError_t ib_step(ibl_ctx* c) {
   for (auto& b : c->bodies) b.prescribed = false;
   c->launches += 6;
   IBL_CU(cudaGetLastError());
-  IBL_CU(band_moments(c, cg_grid));
-  const int wb = (m * 32 + 255) / 256;
-  if (c->prec == IBL_FP64)
-    k_interpolate<double><<<wb, 256, 0, c->stream>>>(m, c->d_base, c->d_wts, (const double*)c->d_band_mom,
-                                                     c->d_tile_slot, g, c->d_U, c->d_rho_l, c->d_B);
-  else
-    k_interpolate<float><<<wb, 256, 0, c->stream>>>(m, c->d_base, c->d_wts, (const float*)c->d_band_mom,
-                                                    c->d_tile_slot, g, c->d_U, c->d_rho_l, c->d_B);
+  IBL_CU(interpolate(c, g));
   IBL_CU(cudaMemsetAsync(c->d_Gdiag_max, 0, sizeof(double) * MAX_BODIES, c->stream));
   k_assemble<<<(m + 7) / 8, 256, 0, c->stream>>>(m, c->d_base, c->d_wts, c->d_tile_slot,
                                                  c->d_tile_mcount, c->d_tile_markers, g, c->d_body, c->d_Gcol,
@@ -1568,7 +1501,8 @@ cudaError_t ib_step(ibl_ctx* c) {
     A.vtotal = vo;
   }
   A.smem_floats = (int)(PCG_SMEM / sizeof(float));
-  A.tol = c->solver_tol > 0 ? c->solver_tol : (c->prec == IBL_FP64 ? PCG_TOL : PCG_TOL_LOW);
+  A.tol = c->solver_tol > 0 ? c->solver_tol
+                             : (c->prec == IBL_FP64 ? PCG_TOL : (c->prec == IBL_FP32 ? PCG_TOL_FP32 : PCG_TOL_HALF));
   A.M = c->d_M; A.red = c->d_red; A.info = c->d_cg_info; A.res = c->d_cg_res;
   A.warm = c->warm_steps >= 2 && c->extrapolate ? 2 : (c->warm_steps >= 1 ? 1 : 0);
   A.w_prev = c->d_wprev;
@@ -1581,6 +1515,10 @@ cudaError_t ib_step(ibl_ctx* c) {
   c->precond_valid = true;
   A.status = c->d_status;
   A.trace = c->d_trace;
+  A.rho_l = c->d_rho_l;
+  A.mforce = c->d_mforce;
+  A.hist = c->d_hist;
+  A.step = c->step;
   static bool smem_set = false;
   if (!smem_set) {
     IBL_CU(cudaFuncSetAttribute((const void*)k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCG_SMEM));
@@ -1600,25 +1538,14 @@ cudaError_t ib_step(ibl_ctx* c) {
                                                                             c->d_tile_slot, g, c->d_acc, c->d_status);
     c->launches++;
   }
-  if (c->prec == IBL_FP64)
-    k_spread_finalize<double><<<cg_grid, TILE_CELLS, 0, c->stream>>>(c->d_band_count, c->cap_slots, c->d_acc,
-                                                                     (const double*)c->d_band_mom,
-                                                                     (double*)c->d_band_F, c->D);
-  else
-    k_spread_finalize<float><<<cg_grid, TILE_CELLS, 0, c->stream>>>(c->d_band_count, c->cap_slots, c->d_acc,
-                                                                    (const float*)c->d_band_mom,
-                                                                    (float*)c->d_band_F, c->D);
   c->launches++;
   IBL_CU(cudaGetLastError());
   return cudaSuccess;
 }
 
 cudaError_t ib_after_collide(ibl_ctx* c) {
-  if (c->m_total == 0) return cudaSuccess;
-  const int nb = (int)c->bodies.size();
-  k_force_reduce<<<nb, 256, 0, c->stream>>>(nb, c->d_boff, c->d_rho_l, c->d_w, c->d_mforce, c->d_hist, c->step);
-  c->launches++;
-  return cudaGetLastError();
+  (void)c;   // the body forces are reduced at the end of the solve
+  return cudaSuccess;
 }
 
 cudaError_t launch_force_field(ibl_ctx* c, double* d_out) {

@@ -105,7 +105,6 @@ struct ibl_ctx {
   int* d_band_count = nullptr;   // 1 int: used slots
   int* d_tile_mcount = nullptr;  // cap_slots
   int* d_tile_markers = nullptr; // cap_slots x TILE_MARKER_CAP
-  void* d_band_mom = nullptr;    // cap_slots x 4 x TILE_CELLS (real)
   void* d_band_F = nullptr;      // cap_slots x 3 x TILE_CELLS (real)
   int* d_base = nullptr;         // m x 3 stencil base nodes (unwrapped)
   double* d_wts = nullptr;       // m x 3 x 4 delta weights per axis (FP64)
@@ -120,7 +119,6 @@ struct ibl_ctx {
   size_t xf_floats = 0;          // floats per padded vector
   unsigned long long* d_trace = nullptr;   // 256 PCG phase timestamps
   unsigned long long* d_acc = nullptr;     // cap_slots x 3 x TILE_CELLS fixed-point spread sums
-  double* d_bstate = nullptr;              // per-body motion state of the step (8 doubles)
   int* d_slot_body = nullptr;              // body that first touched each band slot
   int* d_mixed = nullptr;                  // 1: use the tile-based assembly this step
   int* d_cand = nullptr;                   // m x CAND_MAX rigid-body partner candidates

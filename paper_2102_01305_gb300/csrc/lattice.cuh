@@ -108,6 +108,7 @@ constexpr int TILE_CELLS = 256;
 constexpr int TILE_MARKER_CAP = 512;   // markers whose stencil touches one tile
 constexpr int G_MAXNNZ = 192;          // nonzeros per row of the IB system
 constexpr int HIST_LEN = 65536;        // force history ring per body
+constexpr double FIX_SCALE = 70368744177664.0;   // 2^46: fixed-point scale of the spread sums
 
 // status bits raised on the device
 constexpr int ST_DIVERGED = 1;
@@ -133,7 +134,8 @@ template <class R> struct FluidParams {
   R pref;      // 1 - 1/(2 tau), Guo prefactor (Eq. 8)
   TileGeom tg;
   const int* tile_slot;   // n_tiles, -1 where no band slot; nullptr without markers
-  const R* band_F;        // [slot][3][TILE_CELLS] IB force density (Eq. 26)
+  unsigned long long* band_acc;   // [slot][3][TILE_CELLS] fixed-point sum_l w_l D (Eq. 15), cleared on read
+  R* band_F;              // [slot][3][TILE_CELLS] IB force density 2 rho du written back (Eq. 26)
   int* status;
 };
 

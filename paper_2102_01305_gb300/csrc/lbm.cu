@@ -16,19 +16,22 @@
 
 namespace ibl {
 
-// IB force density of a cell from the band buffers (Eq. 26), zero elsewhere.
+// Velocity correction du of a cell from the band's fixed-point spreading sums
+// (Eq. 15), zero elsewhere; the sums are cleared for the next step.
 template <class R>
-__device__ __forceinline__ void band_force(int x, int y, int z, const FluidParams<R>& p, R F[3]) {
+__device__ __forceinline__ int band_du(int x, int y, int z, const FluidParams<R>& p, R du[3]) {
   const TileGeom& t = p.tg;
   const int tile = ((z / t.tz) * t.nty + (y / t.ty)) * t.ntx + (x / t.tx);
   const int slot = p.tile_slot[tile];
-  if (slot >= 0) {
-    const int local = ((z % t.tz) * t.ty + (y % t.ty)) * t.tx + (x % t.tx);
-    const R* b = p.band_F + (long long)slot * 3 * TILE_CELLS + local;
-    F[0] += b[0];
-    F[1] += b[TILE_CELLS];
-    F[2] += b[2 * TILE_CELLS];
+  if (slot < 0) return -1;
+  const int local = ((z % t.tz) * t.ty + (y % t.ty)) * t.tx + (x % t.tx);
+  unsigned long long* a = p.band_acc + (long long)slot * 3 * TILE_CELLS + local;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    du[c] = (R)((double)(long long)a[c * TILE_CELLS] * (1.0 / FIX_SCALE));
+    a[c * TILE_CELLS] = 0ull;
   }
+  return slot * 3 * TILE_CELLS + local;
 }
 
 // BGK collision with the Guo source (Eqs. 7-8) in deviation form g = f - w.
@@ -36,8 +39,10 @@ __device__ __forceinline__ void band_force(int x, int y, int z, const FluidParam
 // source is computed once per pair, the odd part flips sign.  rho = 1 + drho
 // is never formed in the storage precision where it would drop drho's low
 // bits: rho X = X + drho X and u = m - m drho/(1 + drho).  Returns drho.
+// F is the uniform body force G plus the IB force density 2 rho du (Eq. 26),
+// formed here from this cell's own density; F is returned in F.
 template <int Q, class R>
-__device__ __forceinline__ R collide(R g[Q], const R F[3], const FluidParams<R>& p) {
+__device__ __forceinline__ R collide(R g[Q], R F[3], const R du[3], const FluidParams<R>& p) {
   R drho = g[0], m0 = R(0), m1 = R(0), m2 = R(0);
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
@@ -47,6 +52,9 @@ __device__ __forceinline__ R collide(R g[Q], const R F[3], const FluidParams<R>&
     if (Lat<Q>::cy(i)) m1 += R(Lat<Q>::cy(i)) * d;
     if (Lat<Q>::cz(i)) m2 += R(Lat<Q>::cz(i)) * d;
   }
+  // 2 rho du = 2 du + 2 drho du (rho = 1 + drho is not formed in low precision)
+#pragma unroll
+  for (int c = 0; c < 3; ++c) F[c] = p.G[c] + (R(2) * du[c] + R(2) * drho * du[c]);
   // Eq. 9: rho u = sum c_i f_i + F/2
   const R q = drho / (R(1) + drho);
   R u0 = m0 + R(0.5) * F[0], u1 = m1 + R(0.5) * F[1], u2 = m2 + R(0.5) * F[2];
@@ -141,12 +149,20 @@ __global__ void __launch_bounds__(256) k_collide(DirPtrs<Q, T> P, FluidParams<ty
   } else {
     gather_q<Q, T, true, R>(P.s[0], x, y, z, cell, p, g);
   }
-  R F[3] = {p.G[0], p.G[1], p.G[2]};
-  if (IB) band_force<R>(x, y, z, p, F);
-  const R drho = collide<Q, R>(g, F, p);
+  R F[3];
+  R du[3] = {R(0), R(0), R(0)};
+  int band = -1;
+  if (IB) band = band_du<R>(x, y, z, p, du);
+  const R drho = collide<Q, R>(g, F, du, p);
   if (!(drho > R(-1) && drho < R(99))) atomicOr(p.status, ST_DIVERGED);
 #pragma unroll
   for (int i = 0; i < Q; ++i) P.d[i][cell] = Store<T>::st(g[i]);
+  if (IB && band >= 0) {
+    // the IB force density of this step, for ibl_get_field(IBL_FIELD_FORCE)
+    p.band_F[band] = F[0] - p.G[0];
+    p.band_F[band + TILE_CELLS] = F[1] - p.G[1];
+    p.band_F[band + 2 * TILE_CELLS] = F[2] - p.G[2];
+  }
 }
 
 // rho, u = (sum c_i f_i + G/2)/rho and optionally f itself (FP64) of the
@@ -256,7 +272,8 @@ FluidParams<R> make_params(ibl_ctx* c, bool with_ib) {
   p.pref = (R)(1.0 - 0.5 / c->tau);
   p.tg = c->tg;
   p.tile_slot = with_ib ? c->d_tile_slot : nullptr;
-  p.band_F = with_ib ? (const R*)c->d_band_F : nullptr;
+  p.band_acc = with_ib ? c->d_acc : nullptr;
+  p.band_F = with_ib ? (R*)c->d_band_F : nullptr;
   p.status = c->d_status;
   return p;
 }
