@@ -66,6 +66,12 @@ def parse():
     ap.add_argument("--serving-sample", type=int, default=12,
                     help="requests of the short serving sample in the default line (0: none)")
     ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--overlap", type=int, default=-1, choices=[-1, 0, 1],
+                    help="collide scheduling: -1 automatic, 0 one kernel after the IB chain, 1 split")
+    ap.add_argument("--solver-blocks", type=int, default=0, help="blocks of the implicit solve (0: default)")
+    ap.add_argument("--ib-sweep", action="store_true",
+                    help="IB-stage throughput: interpolate + spread of random point clouds (no solve)")
+    ap.add_argument("--ib-markers", default="1000,10000,100000,1000000")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-worker", default=None)   # internal: run the oracle sample
     return ap.parse_args()
@@ -204,6 +210,29 @@ def cpu_model() -> str:
 
 
 # ----------------------------------------------------------------------------- replicas
+PCG_PHASES = ["stage_z", "spmv_rows", "block_reduce", "barrier1", "alpha", "stage_x", "precond_rows",
+              "reduce_barrier2"]
+
+
+def pcg_trace_summary(tr, iters):
+    """Median phase durations (us) of one solve from its timestamps: slots 0-3
+    are start / after rebuild / after set-up / end; iteration k (k < 27) has 9
+    marks from slot 8 + 9k: scalars ready, then the end of each phase."""
+    if not (tr[0] and tr[3]):
+        return None
+    n = min(iters, 27)
+    base = [8 + 9 * k for k in range(n)]
+    med = lambda v: round(statistics.median(v), 3) if v else None
+    out = {"total_us": (tr[3] - tr[0]) / 1e3, "rebuild_us": (tr[1] - tr[0]) / 1e3,
+           "setup_us": (tr[2] - tr[1]) / 1e3}
+    prev_end = [tr[2]] + [tr[b + 8] for b in base[:-1]]
+    out["scalars_us"] = med([(tr[b] - e) / 1e3 for b, e in zip(base, prev_end)])
+    for j, name in enumerate(PCG_PHASES):
+        out[name + "_us"] = med([(tr[b + j + 1] - tr[b + j]) / 1e3 for b in base])
+    out["iteration_us_median"] = med([(tr[b + 8] - e) / 1e3 for b, e in zip(base, prev_end)])
+    return out
+
+
 def aggregate_over_ranks(ms_local: float, cells: int, steps: int, world: int, dist=None, device="cpu"):
     """Whole-job throughput of `world` independent replicas: every rank ran
     `steps` steps of `cells` cells; the job time is the slowest rank's time."""
@@ -255,6 +284,8 @@ def run_ours(args):
     bytes_per_cell = 2 * q * elem
 
     ctx = ibl.from_workload(cfg)
+    ctx.ibl_set_overlap(args.overlap)
+    ctx.ibl_solver_blocks(args.solver_blocks)
     ctx.ibl_step(args.warmup)
     ctx.ibl_sync(allow=(ibl.IBL_ENOTCONV,))
     stream = torch.cuda.ExternalStream(ctx.ibl_stream())
@@ -288,19 +319,7 @@ def run_ours(args):
     trace = None
     if cfg["bodies"]:
         tr = ctx.ibl_solver_trace(allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
-        if tr[0] and tr[3]:
-            it_n = min(iters, 40)
-            starts = [tr[2]] + [tr[13 + 6 * k] for k in range(it_n - 1)]
-            per_it = [(tr[13 + 6 * k] - starts[k]) / 1e3 for k in range(it_n)]
-            med = lambda v: statistics.median(v) if v else None
-            trace = {"total_us": (tr[3] - tr[0]) / 1e3, "rebuild_us": (tr[1] - tr[0]) / 1e3,
-                     "setup_us": (tr[2] - tr[1]) / 1e3, "iteration_us_median": med(per_it),
-                     "spmv_rows_us": med([(tr[8 + 6 * k] - starts[k]) / 1e3 for k in range(it_n)]),
-                     "spmv_reduce_us": med([(tr[9 + 6 * k] - tr[8 + 6 * k]) / 1e3 for k in range(it_n)]),
-                     "barrier1_us": med([(tr[10 + 6 * k] - tr[9 + 6 * k]) / 1e3 for k in range(it_n)]),
-                     "stage_us": med([(tr[11 + 6 * k] - tr[10 + 6 * k]) / 1e3 for k in range(it_n)]),
-                     "precond_rows_us": med([(tr[12 + 6 * k] - tr[11 + 6 * k]) / 1e3 for k in range(it_n)]),
-                     "reduce_barrier2_us": med([(tr[13 + 6 * k] - tr[12 + 6 * k]) / 1e3 for k in range(it_n)])}
+        trace = pcg_trace_summary(tr, iters)
     cl = (ctx.ibl_forces(0, allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
           if status == "ok" and cfg["bodies"] else None)
     ctx.close()
@@ -360,7 +379,10 @@ def run_ours(args):
                 "dtype": {"fp32": "f32", "fp16dev": "f16 storage / f32 compute",
                           "bf16dev": "bf16 storage / f32 compute", "fp64": "f64"}[args.precision],
                 "data": "synthetic (seeded workload generator; no dataset)",
-                "config": describe(cfg, args.steps) | {"parallelism": f"replicas x{WORLD}"},
+                "config": describe(cfg, args.steps) | {"parallelism": f"replicas x{WORLD}",
+                                                       "collide_schedule": {-1: "automatic", 0: "single kernel",
+                                                                            1: "split"}[args.overlap],
+                                                       "solver_blocks": args.solver_blocks or "half the SMs"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "status": status, "serving_sample": serving,
                 "solver": {"pcg_iterations_last_step": iters, "rel_residual_last_step": res,
@@ -453,6 +475,77 @@ def run_serving(n: int, mean_gap: float, run_steps: int, mix: str, budget_frac: 
             "aggregate_glups": cells / wall / 1e9}
 
 
+def run_ib_sweep(args):
+    """Markers/s of the IB stage without the solve: per step one interpolation
+    of rho, u* (Eq. 17) and one spreading (Eq. 15) of m random points on a
+    size^3 periodic D3Q19 state (a Taylor-Green field after one step), for
+    each m of --ib-markers.  Times are CUDA events around each ABI call on
+    the context's stream, so they include the call's launch latency and, for
+    the spreading, zeroing and converting the dense 3 x N FP64 output."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2102_01305_gb300 import ibl
+    torch.cuda.set_device(0)
+    n = args.size
+    N = n ** 3
+    cfg = {"lattice": 19, "tau": 0.6, "grid": W.grid(n, n, n, [W.PERIODIC] * 6, precision=args.precision),
+           "bodies": [], "u_field": W.tgv3d_velocity(n, n, n, 0.05)}
+    ctx = ibl.from_workload(cfg)
+    del cfg["u_field"]
+    ctx.ibl_step(1)
+    ctx.ibl_sync()
+    stream = torch.cuda.ExternalStream(ctx.ibl_stream())
+    dev = dict(dtype=torch.float64, device="cuda")
+    out = torch.empty((3, n, n, n), **dev)
+    elem = {"fp32": 4, "fp16dev": 2, "bf16dev": 2, "fp64": 8}[args.precision]
+    rows = []
+    clocks = ClockSampler()
+    clocks.start()
+    for m in [int(v) for v in args.ib_markers.split(",")]:
+        X, V = W.random_markers(m, n, 2.0, n - 2.0, 0.05)
+        Xd, Vd, dsd = (torch.as_tensor(a, **dev) for a in (X, V, np.ones(m)))
+        U = torch.empty((m, 3), **dev)
+        rho = torch.empty(m, **dev)
+        ti, ts = [], []
+        for k in range(max(args.warmup, 3) + args.steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            ctx.ibl_interpolate_points(Xd, U, rho)
+            ev[1].record(stream)
+            ctx.ibl_spread_points(Xd, Vd, dsd, out)
+            ev[2].record(stream)
+            ev[2].synchronize()
+            if k >= max(args.warmup, 3):
+                ti.append(ev[0].elapsed_time(ev[1]))
+                ts.append(ev[1].elapsed_time(ev[2]))
+        t_i, t_s = statistics.median(ti), statistics.median(ts)
+        union = N * (1.0 - math.exp(-64.0 * m / N))   # cells covered by at least one stencil
+        # algorithmic bytes: the interpolation reads 19 populations on the
+        # covered cells and 36 B of point data; the spreading writes 24 B
+        # (3 x FP64) on the covered cells and reads 64 B of point data
+        b_i = union * 19 * elem + m * 24 + m * 32
+        b_s = union * 24 + m * 64
+        rows.append({"markers": m, "interpolate_ms": round(t_i, 4), "spread_ms": round(t_s, 4),
+                     "markers_per_s": m / ((t_i + t_s) * 1e-3),
+                     "covered_cells_frac": round(union / N, 4),
+                     "interpolate_GBs": round(b_i / (t_i * 1e-3) / 1e9, 1),
+                     "spread_GBs": round(b_s / (t_s * 1e-3) / 1e9, 1)})
+        del Xd, Vd, dsd, U, rho
+    clk = clocks.stop()
+    ctx.close()
+    best = max(rows, key=lambda r: r["markers_per_s"])
+    print(json.dumps({"metric": "IB-stage markers/s (interpolate + spread, no solve)",
+                      "value": round(best["markers_per_s"], 1), "unit": "markers/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": max(args.warmup, 3), "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+                      "data": "synthetic (uniform random points in [2, n-2)^3, velocities in [-0.05, 0.05]^3)",
+                      "config": {"workload": f"IB sweep on a {n}^3 periodic D3Q19 grid",
+                                 "l2": "no flush: the populations (2 x 19 x N) exceed L2",
+                                 "timing": "CUDA events around each ABI call (median)"},
+                      "sweep": rows, "clocks": clk}), flush=True)
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
     if WORLD > 1:
@@ -496,6 +589,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.ib_sweep:
+        run_ib_sweep(args)
     elif args.serving:
         r = run_serving(args.requests, args.mean_gap, args.run_steps, args.mix)
         print(json.dumps({"metric": METRIC, "value": round(r["solves_per_hour"], 2), "unit": "solves/h",

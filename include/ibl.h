@@ -221,6 +221,24 @@ ibl_status ibl_mass(ibl_ctx* ctx, double* mass);
  * GPU race and must be serialised by the caller.  Synchronises the stream. */
 ibl_status ibl_mass_noalloc(ibl_ctx* ctx, int32_t nparts, double* mass);
 
+/* ------------------------------------------------------------------ point operators */
+
+/* The two transfers of the IB step on an arbitrary cloud of m points, without
+ * the implicit solve (for throughput sweeps and for callers that run their
+ * own marker update).  All arrays are DEVICE pointers (e.g. tensor storage).
+ * ibl_interpolate_points: U (m x d, point-major) and, if non-NULL, rho (m) =
+ *   sum_x u*(x) D(x - X_l), sum_x rho(x) D(x - X_l) of the current
+ *   populations (Eq. 17 with the velocity of Eq. 11 including G/2).
+ * ibl_spread_points: out (d x N, component-major, overwritten) =
+ *   sum_l V_l ds_l D(x - X_l) (Eq. 15).  The sums are accumulated in 64-bit
+ *   fixed point (2^-46) inside `out` itself, so they do not depend on the
+ *   order of the atomic additions; |V ds| must stay below 1.3e5.
+ * X is m x 3 (point-major; z ignored in 2D).  Both synchronise the stream.
+ * IBL_EINVAL if a stencil leaves a non-periodic axis. */
+ibl_status ibl_interpolate_points(ibl_ctx* ctx, int32_t m, const double* d_X, double* d_U, double* d_rho);
+ibl_status ibl_spread_points(ibl_ctx* ctx, int32_t m, const double* d_X, const double* d_V,
+                             const double* d_ds, double* d_out);
+
 /* ------------------------------------------------------------------ introspection */
 
 /* Velocity set of a lattice: c is Q x 3 int32 (marker of direction order used by
@@ -243,22 +261,39 @@ ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_resid
  * changes the iterates, not the system being solved. */
 ibl_status ibl_solver_config(ibl_ctx* ctx, int32_t refresh_every, double tol, int32_t extrapolate);
 
+/* Thread blocks (one per SM, 1024 threads) of the cooperative implicit
+ * solve; 0 (default) = half the SMs, larger values are capped at the SM
+ * count.  The block count fixes the solve's reduction order: runs with the
+ * same count are bitwise reproducible. */
+ibl_status ibl_solver_blocks(ibl_ctx* ctx, int32_t blocks);
+
+/* How a step with markers schedules its collision: 0 = one kernel over all
+ * cells after the IB chain; 1 = split: the cells outside the IB band collide
+ * on a second stream while the IB chain (interpolation, solve, spreading)
+ * runs, and the band tiles collide after the spreading; -1 (default) =
+ * split on grids of at least 2^20 cells.  Both give bitwise the same
+ * populations and forces (every cell runs the same arithmetic). */
+ibl_status ibl_set_overlap(ibl_ctx* ctx, int32_t mode);
+
 /* Phase timestamps (GPU global timer, ns, taken by block 0) of the last
  * implicit solve: [0] start, [1] after the optional preconditioner rebuild,
- * [2] after set-up, [3] end; iteration k (k < 40) at 8 + 6k: SpMV rows done,
- * block reduction done, grid barrier passed, preconditioner input staged,
- * preconditioner rows done, grid barrier passed.  Unused slots are 0.
- * Copies min(max, 256) values into ns. */
+ * [2] after set-up, [3] end; iteration k (k < 27) at 8 + 9k: recurrence
+ * scalars ready, search direction input staged, SpMV rows done, block
+ * reduction done, grid barrier passed, step length ready, preconditioner
+ * input staged, preconditioner rows done, grid barrier passed.  Unused
+ * slots are 0.  Copies min(max, 256) values into ns. */
 ibl_status ibl_solver_trace(ibl_ctx* ctx, int64_t* ns, int32_t max, int32_t* n);
 
-/* Enable (1) or disable (0) CUDA-event timing, on the context's stream, of
- * the collide-stream kernel and of the IB chain (kinematics .. spreading and
- * the force reduction) of every step enqueued while enabled.  Enabling
- * resets the totals.  Adds events only; the launch sequence is unchanged. */
+/* Enable (1) or disable (0) CUDA-event timing of the collide-stream
+ * kernel(s) and of the IB chain (kinematics .. spreading and the force
+ * reduction) of every step enqueued while enabled.  In a split step (see
+ * ibl_set_overlap) the bulk collide is timed on its own stream, concurrently
+ * with the IB chain.  Enabling resets the totals.  Adds events only; the
+ * launch sequence is unchanged. */
 ibl_status ibl_profile(ibl_ctx* ctx, int32_t enable);
 
 /* Totals since the last ibl_profile(ctx, 1): milliseconds in the
- * collide-stream kernel, milliseconds in the IB chain, steps timed.
+ * collide-stream kernel(s), milliseconds in the IB chain, steps timed.
  * Synchronises the stream. */
 ibl_status ibl_profile_read(ibl_ctx* ctx, double* collide_ms, double* ib_ms, int64_t* steps);
 

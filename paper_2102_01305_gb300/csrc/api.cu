@@ -126,8 +126,8 @@ ibl_status ibl_create(const ibl_grid* grid, double tau, int32_t lattice, ibl_ctx
   const size_t bytes = (size_t)c->Q * (size_t)c->N * c->elem;
   if (e == cudaSuccess) e = cudaMalloc(&c->f[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->f[1], bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 2 * sizeof(int));
   if (e != cudaSuccess) {
     ibl_status s = cuda_check(nullptr, e, "ibl_create");
     ibl_destroy(c);
@@ -140,6 +140,12 @@ ibl_status ibl_create(const ibl_grid* grid, double tau, int32_t lattice, ibl_ctx
 ibl_status ibl_destroy(ibl_ctx* c) {
   if (!c) return IBL_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->stream_bulk) {
+    cudaStreamSynchronize(c->stream_bulk);
+    cudaStreamDestroy(c->stream_bulk);
+  }
+  if (c->ev_tiles) cudaEventDestroy(c->ev_tiles);
+  if (c->ev_bulk) cudaEventDestroy(c->ev_bulk);
   ib_free(c);
   for (auto& b : c->bodies) {
     if (b.tableA) cudaFree(b.tableA);
@@ -210,8 +216,8 @@ ibl_status ibl_set_markers(ibl_ctx* c, int32_t m, const double* X0, const double
     return fail(c, IBL_EINVAL, "ibl_set_markers: m > 0 and non-NULL arrays required");
   if ((int)c->bodies.size() >= 16) return fail(c, IBL_EINVAL, "at most 16 bodies");
   for (int a = 0; a < c->D; ++a)
-    if (c->bc[2 * a] == IBL_PERIODIC && (a == 0 ? c->nx : (a == 1 ? c->ny : c->nz)) < 8)
-      return fail(c, IBL_EINVAL, "periodic axes carrying markers need at least 8 nodes");
+    if ((a == 0 ? c->nx : (a == 1 ? c->ny : c->nz)) < 8)
+      return fail(c, IBL_EINVAL, "axes carrying markers need at least 8 nodes");
   const double en = std::sqrt(axis[0] * axis[0] + axis[1] * axis[1] + axis[2] * axis[2]);
   if (!(en > 0)) return fail(c, IBL_EINVAL, "rotation axis is zero");
   for (int l = 0; l < m; ++l)
@@ -282,6 +288,15 @@ ibl_status ibl_set_kinematics(ibl_ctx* c, int32_t body_id, const ibl_wave* A, co
   return IBL_OK;
 }
 
+// Second stream and the two events of the split step, created on first use.
+static ibl_status ensure_split(ibl_ctx* c) {
+  if (c->stream_bulk) return IBL_OK;
+  CK(cudaStreamCreateWithFlags(&c->stream_bulk, cudaStreamNonBlocking), "bulk stream");
+  CK(cudaEventCreateWithFlags(&c->ev_tiles, cudaEventDisableTiming), "event");
+  CK(cudaEventCreateWithFlags(&c->ev_bulk, cudaEventDisableTiming), "event");
+  return IBL_OK;
+}
+
 static ibl_status ensure_ib(ibl_ctx* c) {
   if (c->ib_ready || c->m_total == 0) return IBL_OK;
   CK(cudaStreamSynchronize(c->stream), "sync");
@@ -349,29 +364,65 @@ ibl_status ibl_step(ibl_ctx* c, int64_t n) {
   ibl_status s = ensure_ib(c);
   if (s != IBL_OK) return s;
   const bool with_ib = c->m_total > 0;
+  // split step: the cells outside the IB band collide on a second stream
+  // while the IB chain runs; the band tiles collide after the spreading
+  const bool split = with_ib && (c->overlap == 1 || (c->overlap < 0 && c->N >= (1LL << 20)));
+  if (split) {
+    s = ensure_split(c);
+    if (s != IBL_OK) return s;
+  }
   for (int64_t k = 0; k < n; ++k) {
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     if (c->profiling) {
-      const size_t need = 4 * (size_t)(c->prof_steps + 1);
+      const size_t need = 6 * (size_t)(c->prof_steps + 1);
       while (c->prof_ev.size() < need) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e), "profile event");
         c->prof_ev.push_back(e);
       }
-      for (int j = 0; j < 4; ++j) ev[j] = c->prof_ev[4 * c->prof_steps + j];
+      for (int j = 0; j < 6; ++j) ev[j] = c->prof_ev[6 * c->prof_steps + j];
+      c->prof_split.push_back(split ? 1 : 0);
       c->prof_steps++;
     }
     if (ev[0]) CK(cudaEventRecord(ev[0], c->stream), "event");
-    if (with_ib) CK(ib_step(c), "IB step");
-    if (ev[1]) CK(cudaEventRecord(ev[1], c->stream), "event");
-    CK(launch_collide(c, with_ib), "collide");
-    if (ev[2]) CK(cudaEventRecord(ev[2], c->stream), "event");
-    if (with_ib) CK(ib_after_collide(c), "force reduce");
+    if (split) {
+      CK(ib_step_front(c), "IB step");
+      CK(cudaEventRecord(c->ev_tiles, c->stream), "event");
+      CK(cudaStreamWaitEvent(c->stream_bulk, c->ev_tiles, 0), "stream wait");
+      if (ev[4]) CK(cudaEventRecord(ev[4], c->stream_bulk), "event");
+      CK(launch_collide_bulk(c, std::max(1, num_sms() - pcg_block_count(c))), "bulk collide");
+      if (ev[5]) CK(cudaEventRecord(ev[5], c->stream_bulk), "event");
+      CK(cudaEventRecord(c->ev_bulk, c->stream_bulk), "event");
+      CK(ib_step_back(c), "IB step");
+      if (ev[1]) CK(cudaEventRecord(ev[1], c->stream), "event");
+      CK(launch_collide_band(c, std::max(1, std::min(c->cap_slots, 4 * num_sms()))), "band collide");
+      if (ev[2]) CK(cudaEventRecord(ev[2], c->stream), "event");
+      CK(cudaStreamWaitEvent(c->stream, c->ev_bulk, 0), "stream wait");
+    } else {
+      if (with_ib) CK(ib_step(c), "IB step");
+      if (ev[1]) CK(cudaEventRecord(ev[1], c->stream), "event");
+      CK(launch_collide(c, with_ib), "collide");
+      if (ev[2]) CK(cudaEventRecord(ev[2], c->stream), "event");
+    }
     if (ev[3]) CK(cudaEventRecord(ev[3], c->stream), "event");
     c->cur ^= 1;
     c->poststream = false;
     c->step++;
   }
+  return IBL_OK;
+}
+
+ibl_status ibl_solver_blocks(ibl_ctx* c, int32_t blocks) {
+  if (!c) return IBL_EINVAL;
+  if (blocks < 0 || blocks > 256) return fail(c, IBL_EINVAL, "solver blocks must be in [0, 256]");
+  c->pcg_blocks = blocks;
+  return IBL_OK;
+}
+
+ibl_status ibl_set_overlap(ibl_ctx* c, int32_t mode) {
+  if (!c) return IBL_EINVAL;
+  if (mode < -1 || mode > 1) return fail(c, IBL_EINVAL, "overlap mode must be -1, 0 or 1");
+  c->overlap = mode;
   return IBL_OK;
 }
 
@@ -553,6 +604,7 @@ ibl_status ibl_profile(ibl_ctx* c, int32_t enable) {
   CK(cudaStreamSynchronize(c->stream), "sync");
   c->profiling = enable != 0;
   c->prof_steps = 0;
+  c->prof_split.clear();
   return IBL_OK;
 }
 
@@ -562,12 +614,19 @@ ibl_status ibl_profile_read(ibl_ctx* c, double* collide_ms, double* ib_ms, int64
   double tc = 0, ti = 0;
   for (long long k = 0; k < c->prof_steps; ++k) {
     float a = 0, b = 0, d = 0;
-    cudaEvent_t* e = &c->prof_ev[4 * k];
+    cudaEvent_t* e = &c->prof_ev[6 * k];
     CK(cudaEventElapsedTime(&a, e[0], e[1]), "elapsed");
     CK(cudaEventElapsedTime(&b, e[1], e[2]), "elapsed");
     CK(cudaEventElapsedTime(&d, e[2], e[3]), "elapsed");
-    tc += b;
-    ti += a + d;
+    if (c->prof_split[k]) {
+      float bulk = 0;
+      CK(cudaEventElapsedTime(&bulk, e[4], e[5]), "elapsed");
+      tc += b + bulk;
+      ti += a;
+    } else {
+      tc += b;
+      ti += a + d;
+    }
   }
   if (collide_ms) *collide_ms = tc;
   if (ib_ms) *ib_ms = ti;

@@ -22,7 +22,7 @@
 //   (end of k_pcg)   F_w = -sum_l 2 rho_l w_l per body in FP64, fixed order.
 #include <cooperative_groups.h>
 
-#include "ibl_internal.cuh"
+#include "ib_stencil.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -146,19 +146,11 @@ __global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ 
       wts[12 * l + 4 * a + 3] = 0.0;
       continue;
     }
-    const double fl = floor(x[a]);
-    const int b0 = (int)fl - 1;
-    if (!geo.per[a] && (b0 < 0 || b0 + 3 >= geo.n[a])) atomicOr(status, ST_OVERFLOW);
-    // Eq. 14 at the four nodes b0..b0+3, |r| = 1+s, s, 1-s, 2-s with s = x - floor(x):
-    // cos(pi|r|/2) = -sin, cos, sin, -cos of (pi s / 2).  The stored base is
-    // reduced into [0, n) on periodic axes so that later offsets wrap once at most.
-    double sn, cs;
-    sincospi(0.5 * (x[a] - fl), &sn, &cs);
-    wts[12 * l + 4 * a + 0] = 0.25 * (1.0 - sn);
-    wts[12 * l + 4 * a + 1] = 0.25 * (1.0 + cs);
-    wts[12 * l + 4 * a + 2] = 0.25 * (1.0 + sn);
-    wts[12 * l + 4 * a + 3] = 0.25 * (1.0 - cs);
-    base[3 * l + a] = geo.per[a] ? ((b0 % geo.n[a]) + geo.n[a]) % geo.n[a] : b0;
+    int b0;
+    double w[4];
+    if (!stencil_axis(x[a], geo.n[a], geo.per[a] != 0, b0, w)) atomicOr(status, ST_OVERFLOW);
+    for (int k = 0; k < 4; ++k) wts[12 * l + 4 * a + k] = w[k];
+    base[3 * l + a] = b0;
   }
 }
 
@@ -246,15 +238,6 @@ __global__ void k_append_markers(int m_total, const int* __restrict__ base, Geo 
   }
 }
 
-}  // namespace ibl
-
-// The gather/Zou-He code of the fluid kernels is reused for the band moments
-// so that rho and u* on the band are bitwise the values the collision
-// recomputes.
-#include "lbm_gather.cuh"
-
-namespace ibl {
-
 // rho_l and u*_l (Eq. 17) gathered straight from the populations of each
 // stencil node (the same pull, face rules and moment arithmetic as the
 // collision), FP64 accumulation; B = U_B - u*_l (Eq. 19).  One warp per
@@ -264,7 +247,6 @@ __global__ void k_interpolate(int m_total, const int* __restrict__ base, const d
                               const T* __restrict__ src, FluidParams<typename Store<T>::R> p, Geo g,
                               const double* __restrict__ U, double* __restrict__ rho_l,
                               double* __restrict__ B) {
-  using R = typename Store<T>::R;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= m_total) return;
@@ -280,27 +262,12 @@ __global__ void k_interpolate(int m_total, const int* __restrict__ base, const d
       if (g.per[a]) node[a] = wrap(node[a], g.n[a]);
     const double wt = w[i] * w[4 + j] * w[8 + (g.D == 3 ? q : 0)];
     const long long cell = ((long long)node[2] * p.ny + node[1]) * p.nx + node[0];
-    R gg[Q];
-    gather_q<Q, T, PULL, R>(src, node[0], node[1], node[2], cell, p, gg);
-    R drho = gg[0], m0 = R(0), m1 = R(0), m2 = R(0);
-#pragma unroll
-    for (int e = 1; e < Q; e += 2) {
-      drho += gg[e] + gg[e + 1];
-      const R d = gg[e] - gg[e + 1];
-      if (Lat<Q>::cx(e)) m0 += R(Lat<Q>::cx(e)) * d;
-      if (Lat<Q>::cy(e)) m1 += R(Lat<Q>::cy(e)) * d;
-      if (Lat<Q>::cz(e)) m2 += R(Lat<Q>::cz(e)) * d;
-    }
-    // Eq. 11 with the uniform body force: u* = (m + G/2) / rho, as m - m drho / rho
-    const R qd = drho / (R(1) + drho);
-    R u0 = m0 + R(0.5) * p.G[0], u1 = m1 + R(0.5) * p.G[1], u2 = m2 + R(0.5) * p.G[2];
-    u0 -= u0 * qd;
-    u1 -= u1 * qd;
-    u2 -= u2 * qd;
-    acc[0] += wt * (1.0 + (double)drho);
-    acc[1] += wt * (double)u0;
-    acc[2] += wt * (double)u1;
-    acc[3] += wt * (double)u2;
+    double rho, u[3];
+    node_rho_u<Q, T, PULL>(src, node[0], node[1], node[2], cell, p, rho, u);
+    acc[0] += wt * rho;
+    acc[1] += wt * u[0];
+    acc[2] += wt * u[1];
+    acc[3] += wt * u[2];
   }
   for (int o = 16; o > 0; o >>= 1)
     for (int c = 0; c < 4; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
@@ -488,6 +455,7 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
 // ------------------------------------------------------------------ PCG with in-kernel preconditioner rebuild
 constexpr int PCG_THREADS = 1024;
 constexpr int TRACE_SLOTS = 256;
+constexpr int TRACE_PER_IT = 9;   // phase marks per traced iteration, from slot 8
 constexpr int PCG_WARPS = PCG_THREADS / 32;
 
 struct PcgArgs {
@@ -499,6 +467,7 @@ struct PcgArgs {
   int voff[MAX_BODIES];         // offset of each body's slice in the padded FP32 vectors
   int vtotal;                   // floats of one padded FP32 vector (all bodies), multiple of 12
   int smem_floats;              // dynamic shared memory available for staging, in floats
+  int row_slot;                 // floats per resident preconditioner row (0: rows read from L2)
   const int* body_of;
   const int* Gcol;
   const double* Gval;
@@ -609,6 +578,32 @@ __device__ void grid_total(const double* red, int slot, double out[NV], double* 
   for (int c = 0; c < NV; ++c) out[c] = sh[c];
 }
 
+// The same fixed-order grid totals, for warp 0 only and without a block
+// barrier: every lane of warp 0 ends with the NV totals (pairwise tree over
+// each lane's partials, then a butterfly across lanes).
+template <int NV>
+__device__ __forceinline__ void warp0_total(const double* red, int slot, double v[NV]) {
+  constexpr int U = MAX_PCG_BLOCKS / 32;
+  double buf[U][NV];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int b = threadIdx.x + 32 * u;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) buf[u][c] = b < (int)gridDim.x ? __ldcg(red + b * 8 + slot + c) : 0.0;
+  }
+#pragma unroll
+  for (int w = U / 2; w >= 1; w >>= 1)
+#pragma unroll
+    for (int u = 0; u < w; ++u)
+#pragma unroll
+      for (int c = 0; c < NV; ++c) buf[u][c] += buf[u + w][c];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) v[c] = buf[0][c];
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < NV; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+}
+
 // Row stride of a body's dense preconditioner: padded to 4 floats so rows
 // start 16-byte aligned for 128-bit loads.
 __host__ __device__ __forceinline__ int precond_ld(int mb) { return (mb + 3) & ~3; }
@@ -649,14 +644,29 @@ __device__ float* stage_x(const PcgArgs& A, const float* __restrict__ a, const f
 // the result is returned in every lane.
 __device__ __forceinline__ void precond_row(const PcgArgs& A, int l, const float* __restrict__ xs,
                                             const float* __restrict__ a, const float* __restrict__ b,
-                                            const float s[3], float out[3], int lane) {
+                                            const float s[3], float out[3], int lane,
+                                            const float* __restrict__ mres) {
   const int bd = A.body_of[l];
   const int o = A.boff[bd], mb = A.boff[bd + 1] - o;
   const int ld = precond_ld(mb);
   const float* row = A.M + A.poff[bd] + (long long)(l - o) * ld;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
   const int nq = ld >> 2;
-  if (xs) {
+  if (xs && mres) {
+    // the row is resident in shared memory for the whole solve
+    const float* xb = xs + A.voff[bd];
+    const float* rs = mres + (long long)((l - (int)blockIdx.x) / (int)gridDim.x) * A.row_slot;
+#pragma unroll 4
+    for (int q = lane; q < nq; q += 32) {
+      const float4 mv = reinterpret_cast<const float4*>(rs)[q];
+      const float4* xv = reinterpret_cast<const float4*>(xb + 12 * q);
+      const float4 x0 = xv[0], x1 = xv[1], x2 = xv[2];
+      s0 = fmaf(mv.x, x0.x, s0); s1 = fmaf(mv.x, x0.y, s1); s2 = fmaf(mv.x, x0.z, s2);
+      s0 = fmaf(mv.y, x0.w, s0); s1 = fmaf(mv.y, x1.x, s1); s2 = fmaf(mv.y, x1.y, s2);
+      s0 = fmaf(mv.z, x1.z, s0); s1 = fmaf(mv.z, x1.w, s1); s2 = fmaf(mv.z, x2.x, s2);
+      s0 = fmaf(mv.w, x2.y, s0); s1 = fmaf(mv.w, x2.z, s1); s2 = fmaf(mv.w, x2.w, s2);
+    }
+  } else if (xs) {
     const float* xb = xs + A.voff[bd];
 #pragma unroll 4
     for (int q = lane; q < nq; q += 32) {
@@ -711,6 +721,9 @@ constexpr size_t GJ_SMEM = sizeof(float) * 2 * GJ_NB * GS;
 // dynamic shared memory of the solve kernel: the rebuild's tiles or, during
 // the iterations, one staged FP32 vector of all bodies (up to 24k markers)
 constexpr size_t PCG_SMEM = 96 * 1024;
+// upper bound of the dynamic shared memory (227 KB per block, less the
+// kernel's static shared memory)
+constexpr size_t PCG_SMEM_MAX = 226 * 1024;
 
 // out[i0+r][j0+c] = (acc ? out : 0) + alpha * sum_q A[r][q] B[q][j0+c] over one
 // tile (r < nr, c < nc), skipping output rows in [sk0, sk1) and columns in
@@ -928,6 +941,20 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     grid.sync();
     gj_invert(A, grid, sm);
   }
+  // this block's preconditioner rows (l = blockIdx.x + gridDim.x j) stay in
+  // shared memory for the whole solve when they fit; warp j % 32 owns row j
+  float* mres = nullptr;
+  if (A.row_slot > 0) {
+    mres = sm + A.smem_floats;
+    for (int j = wib, l = blockIdx.x + gridDim.x * wib; l < m; j += PCG_WARPS, l += rstep) {
+      const int bd = A.body_of[l];
+      const int o = A.boff[bd], ld = precond_ld(A.boff[bd + 1] - o);
+      const float4* src = reinterpret_cast<const float4*>(A.M + A.poff[bd] + (long long)(l - o) * ld);
+      float4* dst = reinterpret_cast<float4*>(mres + (long long)j * A.row_slot);
+#pragma unroll 4
+      for (int q = lane; q < (ld >> 2); q += 32) dst[q] = __ldcg(src + q);
+    }
+  }
   trace_mark(A, 1);
 
   // ---- set-up: w0 = 0, the last solution, or 2 w_n-1 - w_n-2 once two exist
@@ -981,7 +1008,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     const float* xs = stage_x(A, A.rf, nullptr, zero3, sm);
     for (int l = row0; l < m; l += rstep) {
       float zr[3];
-      precond_row(A, l, xs, A.rf, nullptr, zero3, zr, lane);
+      precond_row(A, l, xs, A.rf, nullptr, zero3, zr, lane, mres);
       if (lane == 0)
         for (int c = 0; c < 3; ++c) {
           A.z[3 * l + c] = zr[c];
@@ -991,7 +1018,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     xs = stage_x(A, A.Bf, nullptr, zero3, sm);
     for (int l = row0; l < m; l += rstep) {
       float zb[3];
-      precond_row(A, l, xs, A.Bf, nullptr, zero3, zb, lane);
+      precond_row(A, l, xs, A.Bf, nullptr, zero3, zb, lane, mres);
       if (lane == 0)
         for (int c = 0; c < 3; ++c) bb3[c] += A.B[3 * l + c] * (double)zb[c];
     }
@@ -1008,8 +1035,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   // Scalars of the recurrence live in shared memory: thread 0 of each block
   // computes them from the grid totals (FP64 divisions are expensive on this
   // GPU; every block gets bitwise the same values).
-  __shared__ double s_rz[3], s_rzp[3], s_scale[3], s_coef[3];
-  __shared__ float s_coeff[3];
+  __shared__ double s_rz[3], s_scale[3], s_beta[3], s_alpha[3];
+  __shared__ float s_alphaf[3];
   __shared__ int s_done;
   grid_total<3>(A.red, 0, s_scale, shd);
   grid_total<3>(A.red, 3, s_rz, shd);
@@ -1017,17 +1044,17 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     bool d = true;
     for (int c = 0; c < A.D; ++c) d &= !(s_rz[c] > A.tol * A.tol * s_scale[c]);
     s_done = d ? 1 : 0;
-    for (int c = 0; c < 3; ++c) s_rzp[c] = 1.0;
+    for (int c = 0; c < 3; ++c) s_beta[c] = 0.0;
   }
   __syncthreads();
   int it = 0;
   bool done = s_done != 0;
   while (!done && it < PCG_MAX_ITERS) {
     // ---- P1: p = z + beta p;  A p = G z + beta A p;  partial p.Ap;  FP32 copies of r and A p
-    if (threadIdx.x == 0)
-      for (int c = 0; c < 3; ++c) s_coef[c] = (it > 0 && s_rzp[c] > 0.0) ? s_rz[c] / s_rzp[c] : 0.0;
-    __syncthreads();
-    const double beta[3] = {s_coef[0], s_coef[1], s_coef[2]};
+    // beta was formed with the convergence test at the end of the previous iteration
+    const double beta[3] = {s_beta[0], s_beta[1], s_beta[2]};
+    const int ts = 8 + TRACE_PER_IT * it;
+    trace_mark(A, ts);
     {
       // 8 lanes per row, 4 rows per warp: a 3-level FP64 tree instead of 5
       double pAp3[3] = {0, 0, 0};
@@ -1044,6 +1071,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
         __syncthreads();
         zs = reinterpret_cast<const double*>(sm);
       }
+      trace_mark(A, ts + 1);
       const int sub = lane >> 3, sl = lane & 7;
       for (int l0 = row0 * 4; l0 < m; l0 += rstep * 4) {
         const int l = l0 + sub;
@@ -1087,35 +1115,39 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
             if (lane == 0) pAp3[c] += v;
           }
       }
-      trace_mark(A, 8 + 6 * it);
+      trace_mark(A, ts + 2);
       block_total3(pAp3, shd);
       if (threadIdx.x == 0)
         for (int c = 0; c < 3; ++c) A.red[blockIdx.x * 8 + c] = pAp3[c];
-      trace_mark(A, 9 + 6 * it);
+      trace_mark(A, ts + 3);
     }
     grid.sync();
-    trace_mark(A, 10 + 6 * it);
+    trace_mark(A, ts + 4);
     // ---- P2: alpha;  z = M (r - alpha A p) in FP32;  w += alpha p;  r -= alpha A p;  partial r.z
     {
-      double pAp[3];
-      grid_total<3>(A.red, 0, pAp, shd);
-      if (threadIdx.x == 0)
-        for (int c = 0; c < 3; ++c) {
+      // warp 0: totals p.Ap, then lanes 0-2 form alpha of their component
+      if (threadIdx.x < 32) {
+        double pAp[3];
+        warp0_total<3>(A.red, 0, pAp);
+        if (lane < 3) {
+          const int c = lane;
           const double a = (pAp[c] > 0.0 && s_rz[c] > 0.0) ? s_rz[c] / pAp[c] : 0.0;
-          s_coef[c] = a;
-          s_coeff[c] = (float)a;
+          s_alpha[c] = a;
+          s_alphaf[c] = (float)a;
         }
+      }
       __syncthreads();
     }
-    const double alpha[3] = {s_coef[0], s_coef[1], s_coef[2]};
-    const float alphaf[3] = {s_coeff[0], s_coeff[1], s_coeff[2]};
+    trace_mark(A, ts + 5);
+    const double alpha[3] = {s_alpha[0], s_alpha[1], s_alpha[2]};
+    const float alphaf[3] = {s_alphaf[0], s_alphaf[1], s_alphaf[2]};
     {
       double rz3[3] = {0, 0, 0};
       const float* xs = stage_x(A, A.rf, A.Apf, alphaf, sm);
-      trace_mark(A, 11 + 6 * it);
+      trace_mark(A, ts + 6);
       for (int l = row0; l < m; l += rstep) {
         float zl[3];
-        precond_row(A, l, xs, A.rf, A.Apf, alphaf, zl, lane);
+        precond_row(A, l, xs, A.rf, A.Apf, alphaf, zl, lane, mres);
         double contrib = 0.0;
         if (lane < 3) {
           const int c = lane;
@@ -1133,24 +1165,30 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
           rz3[2] += c2;
         }
       }
-      trace_mark(A, 12 + 6 * it);
+      trace_mark(A, ts + 7);
       block_total3(rz3, shd);
       if (threadIdx.x == 0)
         for (int c = 0; c < 3; ++c) A.red[blockIdx.x * 8 + 3 + c] = rz3[c];
     }
     grid.sync();
-    trace_mark(A, 13 + 6 * it);
+    trace_mark(A, ts + 8);
     {
-      double rzn[3];
-      grid_total<3>(A.red, 3, rzn, shd);
-      if (threadIdx.x == 0) {
-        bool d = true;
-        for (int c = 0; c < 3; ++c) {
-          s_rzp[c] = s_rz[c];
-          s_rz[c] = rzn[c];
+      // warp 0: totals r.z; lanes 0-2 form beta for the next iteration; lane 0 tests convergence
+      if (threadIdx.x < 32) {
+        double rzn[3];
+        warp0_total<3>(A.red, 3, rzn);
+        if (lane < 3) {
+          const int c = lane;
+          const double prev = s_rz[c];
+          s_beta[c] = prev > 0.0 ? rzn[c] / prev : 0.0;
         }
-        for (int c = 0; c < A.D; ++c) d &= !(s_rz[c] > A.tol * A.tol * s_scale[c]);
-        s_done = d ? 1 : 0;
+        __syncwarp();
+        if (lane == 0) {
+          bool d = true;
+          for (int c = 0; c < 3; ++c) s_rz[c] = rzn[c];
+          for (int c = 0; c < A.D; ++c) d &= !(s_rz[c] > A.tol * A.tol * s_scale[c]);
+          s_done = d ? 1 : 0;
+        }
       }
       __syncthreads();
     }
@@ -1415,15 +1453,30 @@ static cudaError_t interpolate(ibl_ctx* c, const Geo& g) {
 
 static int g_num_sms = 0;
 
-cudaError_t ib_step(ibl_ctx* c) {
+int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_num_sms = n > 0 ? n : 1;
+  }
+  return g_num_sms;
+}
+
+// Blocks of the cooperative solve: by default half the SMs (the other half
+// runs the bulk collide concurrently when the step is split), fixed per
+// context so that the solve's reduction order does not depend on the split.
+int pcg_block_count(const ibl_ctx* c) {
+  const int want = c->pcg_blocks > 0 ? c->pcg_blocks : num_sms() / 2;
+  return std::max(1, std::min(std::min(std::min(want, num_sms()), MAX_PCG_BLOCKS), c->m_total));
+}
+
+// Kinematics and the band tiles of the step (the bulk collide may start
+// once these are enqueued).
+cudaError_t ib_step_front(ibl_ctx* c) {
   const int m = c->m_total;
   if (m == 0) return cudaSuccess;
-  if (!g_num_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
+  num_sms();
   Geo g = make_geo(c);
   if (!c->cand_ready) {
     IBL_CU(cudaMemsetAsync(c->d_mixed + 1, 0, sizeof(int), c->stream));
@@ -1448,7 +1501,6 @@ cudaError_t ib_step(ibl_ctx* c) {
   const int mb = (m + tb - 1) / tb;
   k_kinematics<<<mb, tb, 0, c->stream>>>(bt, m, c->d_body, c->d_X0, c->d_Xp, c->d_Up, c->d_X, c->d_U,
                                          c->d_base, c->d_wts, (double)c->step, g, c->d_status);
-  const int cg_grid = std::min(c->cap_slots, 4 * g_num_sms);
   k_clear_tiles<<<std::max(1, std::min(c->cap_slots / 256 + 1, g_num_sms)), 256, 0, c->stream>>>(
       c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->d_tile_mcount, c->d_slot_body, c->cap_slots);
   // candidate-list assembly unless a body is driven by uploaded states this step
@@ -1460,11 +1512,22 @@ cudaError_t ib_step(ibl_ctx* c) {
   k_mark_tiles<<<mb, tb, 0, c->stream>>>(m, c->d_base, g, c->d_tile_slot);
   k_assign_slots<<<std::max(1, std::min((c->tg.n_tiles + 255) / 256, 2 * g_num_sms)), 256, 0, c->stream>>>(
       c->tg.n_tiles, c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->cap_slots, c->d_status);
+  c->launches += 4;
+  return cudaGetLastError();
+}
+
+// Marker lists, interpolation, assembly, the implicit solve and spreading.
+cudaError_t ib_step_back(ibl_ctx* c) {
+  const int m = c->m_total;
+  if (m == 0) return cudaSuccess;
+  Geo g = make_geo(c);
+  const int tb = 64;
+  const int mb = (m + tb - 1) / tb;
   k_append_markers<<<mb, tb, 0, c->stream>>>(m, c->d_base, g, c->d_tile_slot, c->d_tile_mcount,
                                              c->d_tile_markers, c->d_status, c->d_body, c->d_slot_body,
                                              c->d_mixed);
   for (auto& b : c->bodies) b.prescribed = false;
-  c->launches += 6;
+  c->launches += 1;
   IBL_CU(cudaGetLastError());
   IBL_CU(interpolate(c, g));
   IBL_CU(cudaMemsetAsync(c->d_Gdiag_max, 0, sizeof(double) * MAX_BODIES, c->stream));
@@ -1473,7 +1536,7 @@ cudaError_t ib_step(ibl_ctx* c) {
                                                  c->d_Gval, c->d_Gnnz, (unsigned long long*)c->d_Gdiag_max,
                                                  c->d_status, c->d_cand, c->d_ncand, c->d_mixed,
                                                  c->d_mixed + 1);
-  c->launches += 2;
+  c->launches += 1;
   IBL_CU(cudaGetLastError());
   // PCG (cooperative)
   PcgArgs A;
@@ -1500,7 +1563,21 @@ cudaError_t ib_step(ibl_ctx* c) {
     }
     A.vtotal = vo;
   }
-  A.smem_floats = (int)(PCG_SMEM / sizeof(float));
+  // shared memory: a staging area (z in FP64 for the SpMV, or the FP32
+  // preconditioner input) and, when they fit, this block's preconditioner rows
+  const int pcg_blocks = pcg_block_count(c);
+  {
+    // vectors larger than PCG_SMEM are read from L2 instead of being staged
+    size_t stage = std::max<size_t>((size_t)3 * m * sizeof(double), (size_t)A.vtotal * sizeof(float));
+    stage = std::max(std::min((stage + 15) & ~(size_t)15, PCG_SMEM), GJ_SMEM);
+    int slot = 0;
+    for (int b = 0; b < A.nbodies; ++b) slot = std::max(slot, precond_ld(c->bodies[b].m));
+    const size_t rows = (size_t)(m + pcg_blocks - 1) / pcg_blocks;
+    const size_t need = stage + rows * (size_t)slot * sizeof(float);
+    A.smem_floats = (int)(stage / sizeof(float));
+    A.row_slot = need <= PCG_SMEM_MAX ? slot : 0;
+    c->pcg_smem = A.row_slot ? need : stage;
+  }
   A.tol = c->solver_tol > 0 ? c->solver_tol
                              : (c->prec == IBL_FP64 ? PCG_TOL : (c->prec == IBL_FP32 ? PCG_TOL_FP32 : PCG_TOL_HALF));
   A.M = c->d_M; A.red = c->d_red; A.info = c->d_cg_info; A.res = c->d_cg_res;
@@ -1521,16 +1598,16 @@ cudaError_t ib_step(ibl_ctx* c) {
   A.step = c->step;
   static bool smem_set = false;
   if (!smem_set) {
-    IBL_CU(cudaFuncSetAttribute((const void*)k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCG_SMEM));
+    IBL_CU(cudaFuncSetAttribute((const void*)k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCG_SMEM_MAX));
     smem_set = true;
   }
-  int pcg_blocks = std::max(1, std::min(std::min(g_num_sms, MAX_PCG_BLOCKS), m));
   void* args[] = {&A};
-  IBL_CU(cudaLaunchCooperativeKernel((void*)k_pcg, dim3(pcg_blocks), dim3(PCG_THREADS), args, PCG_SMEM, c->stream));
+  IBL_CU(cudaLaunchCooperativeKernel((void*)k_pcg, dim3(pcg_blocks), dim3(PCG_THREADS), args, c->pcg_smem,
+                                     c->stream));
   c->launches++;
   c->warm = true;
   c->warm_steps++;
-  // spreading: fixed-point scatter, then F = 2 rho du
+  // spreading: fixed-point scatter (the collision forms F = 2 rho du)
   {
     const int nn = c->D == 3 ? 64 : 16;
     const long long tot = (long long)m * nn;
@@ -1538,14 +1615,13 @@ cudaError_t ib_step(ibl_ctx* c) {
                                                                             c->d_tile_slot, g, c->d_acc, c->d_status);
     c->launches++;
   }
-  c->launches++;
   IBL_CU(cudaGetLastError());
   return cudaSuccess;
 }
 
-cudaError_t ib_after_collide(ibl_ctx* c) {
-  (void)c;   // the body forces are reduced at the end of the solve
-  return cudaSuccess;
+cudaError_t ib_step(ibl_ctx* c) {
+  IBL_CU(ib_step_front(c));
+  return ib_step_back(c);
 }
 
 cudaError_t launch_force_field(ibl_ctx* c, double* d_out) {

@@ -73,6 +73,11 @@ struct ibl_ctx {
   double tau = 1.0;
   int device = 0;
   cudaStream_t stream = nullptr;
+  // collide of the cells outside the IB band, concurrent with the IB chain
+  cudaStream_t stream_bulk = nullptr;
+  cudaEvent_t ev_tiles = nullptr;   // band tiles of the step assigned (stream)
+  cudaEvent_t ev_bulk = nullptr;    // bulk collide done (stream_bulk)
+  int overlap = -1;                 // -1 automatic, 0 off, 1 on
   size_t elem = 4;               // bytes per stored population
   void* f[2] = {nullptr, nullptr};
   int cur = 0;
@@ -80,7 +85,7 @@ struct ibl_ctx {
   bool poststream = true;        // current buffer holds post-streaming populations
   long long step = 0;
   long long launches = 0;
-  int* d_status = nullptr;       // device status bits
+  int* d_status = nullptr;       // [0] step status bits, [1] point-operator flag
   int sticky = 0;                // host copy of status bits seen so far
   std::string err;
 
@@ -144,10 +149,15 @@ struct ibl_ctx {
   bool extrapolate = true;
   int refresh_every = 128;       // steps between scheduled preconditioner rebuilds
   double solver_tol = 0.0;       // 0: default for the storage precision
+  int pcg_blocks = 0;            // blocks of the cooperative solve (0: half the SMs)
+  size_t pcg_smem = 0;           // dynamic shared memory of the last solve launch
   double* d_wprev = nullptr;     // m x 3 solution of the previous step
   // optional per-step event timing (ibl_profile)
   bool profiling = false;
-  std::vector<cudaEvent_t> prof_ev;   // 4 events per step: ib0, collide0, collide1, ib1
+  // 6 events per step: [0] start, [1] IB chain done, [2] collide done,
+  // [3] end (stream); [4], [5] bulk collide start/end (stream_bulk, when split)
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<char> prof_split;
   long long prof_steps = 0;
   // host copies of the bodies' marker sets (uploaded when the IB buffers are sized)
   std::vector<double> h_X0;      // m x 3
@@ -170,6 +180,8 @@ ibl_status sync_and_collect(ibl_ctx* c);   // drain the stream, fold device stat
 cudaError_t launch_init_eq(ibl_ctx* c, const double* d_rho, const double* d_u);
 cudaError_t launch_set_pop(ibl_ctx* c, const double* d_f);
 cudaError_t launch_collide(ibl_ctx* c, bool with_ib);
+cudaError_t launch_collide_bulk(ibl_ctx* c, int blocks);   // on stream_bulk
+cudaError_t launch_collide_band(ibl_ctx* c, int blocks);
 cudaError_t launch_fields(ibl_ctx* c, double* d_rho, double* d_u, double* d_pop);
 cudaError_t launch_mass(ibl_ctx* c, double* d_partials, int nparts, double* d_out);
 
@@ -177,7 +189,10 @@ cudaError_t launch_mass(ibl_ctx* c, double* d_partials, int nparts, double* d_ou
 cudaError_t ib_alloc(ibl_ctx* c);
 void ib_free(ibl_ctx* c);
 cudaError_t ib_step(ibl_ctx* c);          // kinematics .. spreading, before the collision
-cudaError_t ib_after_collide(ibl_ctx* c); // force reduction
+cudaError_t ib_step_front(ibl_ctx* c);    // kinematics and the band tiles of the step
+cudaError_t ib_step_back(ibl_ctx* c);     // interpolation .. solve .. spreading
+int num_sms();
+int pcg_block_count(const ibl_ctx* c);
 cudaError_t launch_force_field(ibl_ctx* c, double* d_out);
 
 }  // namespace ibl

@@ -132,13 +132,13 @@ __device__ __forceinline__ void gather_fast(const DirPtrs<Q, T>& P, int x, int y
   }
 }
 
+// One cell of the fused step: pull (with faces), IB velocity correction of
+// band cells, collision with forcing, store; the same arithmetic whichever
+// kernel runs it, so every launch split gives bitwise the same populations.
 template <int Q, class T, bool PULL, bool IB>
-__global__ void __launch_bounds__(256) k_collide(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p) {
+__device__ __forceinline__ void collide_cell(const DirPtrs<Q, T>& P, const FluidParams<typename Store<T>::R>& p,
+                                             int x, int y, int z) {
   using R = typename Store<T>::R;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= p.nx || y >= p.ny) return;
   const int cell = (z * p.ny + y) * p.nx + x;
   R g[Q];
   if (!PULL) {
@@ -162,6 +162,58 @@ __global__ void __launch_bounds__(256) k_collide(DirPtrs<Q, T> P, FluidParams<ty
     p.band_F[band] = F[0] - p.G[0];
     p.band_F[band + TILE_CELLS] = F[1] - p.G[1];
     p.band_F[band + 2 * TILE_CELLS] = F[2] - p.G[2];
+  }
+}
+
+// Every cell, 64 x 4 cells per block; IB selects the band lookup.
+template <int Q, class T, bool PULL, bool IB>
+__global__ void __launch_bounds__(256) k_collide(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= p.nx || y >= p.ny) return;
+  collide_cell<Q, T, PULL, IB>(P, p, x, y, z);
+}
+
+// Cells outside the IB band, while the IB chain runs on other SMs: a
+// persistent grid of 1024-thread blocks (one per SM: each holds the whole
+// register file, so the SMs it does not take stay free for the solve), each
+// walking 64 x 16-cell units of one z-plane; band tiles are skipped and
+// left to k_collide_band.
+constexpr int BULK_THREADS = 1024;
+template <int Q, class T, bool PULL>
+__global__ void __launch_bounds__(BULK_THREADS, 1) k_collide_bulk(DirPtrs<Q, T> P,
+                                                                   FluidParams<typename Store<T>::R> p) {
+  const int ux = (p.nx + 63) >> 6, uy = (p.ny + 15) >> 4;
+  const int units = ux * uy * p.nz;
+  const int lx = threadIdx.x & 63, ly = threadIdx.x >> 6;
+  const TileGeom& t = p.tg;
+  for (int u = blockIdx.x; u < units; u += gridDim.x) {
+    const int bx = u % ux, r = u / ux;
+    const int x = ((bx) << 6) + lx, y = ((r % uy) << 4) + ly, z = r / uy;
+    if (x >= p.nx || y >= p.ny) continue;
+    const int tile = ((z / t.tz) * t.nty + (y / t.ty)) * t.ntx + (x / t.tx);
+    if (p.tile_slot[tile] >= 0) continue;
+    collide_cell<Q, T, PULL, false>(P, p, x, y, z);
+  }
+}
+
+// Cells of the IB band: one tile (TILE_CELLS cells) per block iteration over
+// the assigned slots.
+template <int Q, class T, bool PULL>
+__global__ void __launch_bounds__(TILE_CELLS) k_collide_band(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p,
+                                                             const int* __restrict__ slot_tile,
+                                                             const int* __restrict__ band_count, int cap) {
+  const TileGeom& t = p.tg;
+  const int n = min(*band_count, cap);
+  const int lx = threadIdx.x % t.tx, ly = (threadIdx.x / t.tx) % t.ty, lz = threadIdx.x / (t.tx * t.ty);
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    const int tile = slot_tile[s];
+    const int x = (tile % t.ntx) * t.tx + lx;
+    const int y = ((tile / t.ntx) % t.nty) * t.ty + ly;
+    const int z = (tile / (t.ntx * t.nty)) * t.tz + lz;
+    if (x >= p.nx || y >= p.ny || z >= p.nz) continue;
+    collide_cell<Q, T, PULL, true>(P, p, x, y, z);
   }
 }
 
@@ -287,9 +339,7 @@ static dim3 cell_grid(ibl_ctx* c, dim3 b) {
 }
 
 template <int Q, class T>
-cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
-  using R = typename Store<T>::R;
-  auto p = make_params<R>(c, with_ib);
+DirPtrs<Q, T> dir_ptrs(ibl_ctx* c) {
   const T* src = (const T*)c->f[c->cur];
   T* dst = (T*)c->f[c->cur ^ 1];
   DirPtrs<Q, T> P;
@@ -297,6 +347,14 @@ cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
     P.s[i] = src + (size_t)i * c->N;
     P.d[i] = dst + (size_t)i * c->N;
   }
+  return P;
+}
+
+template <int Q, class T>
+cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
+  using R = typename Store<T>::R;
+  auto p = make_params<R>(c, with_ib);
+  const DirPtrs<Q, T> P = dir_ptrs<Q, T>(c);
   dim3 b = cell_block(c), g = cell_grid(c, b);
   if (c->poststream) {
     if (with_ib) k_collide<Q, T, false, true><<<g, b, 0, c->stream>>>(P, p);
@@ -305,6 +363,32 @@ cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
     if (with_ib) k_collide<Q, T, true, true><<<g, b, 0, c->stream>>>(P, p);
     else k_collide<Q, T, true, false><<<g, b, 0, c->stream>>>(P, p);
   }
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int Q, class T>
+cudaError_t collide_bulk_q(ibl_ctx* c, int blocks) {
+  using R = typename Store<T>::R;
+  auto p = make_params<R>(c, true);
+  const DirPtrs<Q, T> P = dir_ptrs<Q, T>(c);
+  if (c->poststream) k_collide_bulk<Q, T, false><<<blocks, BULK_THREADS, 0, c->stream_bulk>>>(P, p);
+  else k_collide_bulk<Q, T, true><<<blocks, BULK_THREADS, 0, c->stream_bulk>>>(P, p);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <int Q, class T>
+cudaError_t collide_band_q(ibl_ctx* c, int blocks) {
+  using R = typename Store<T>::R;
+  auto p = make_params<R>(c, true);
+  const DirPtrs<Q, T> P = dir_ptrs<Q, T>(c);
+  if (c->poststream)
+    k_collide_band<Q, T, false><<<blocks, TILE_CELLS, 0, c->stream>>>(P, p, c->d_slot_tile, c->d_band_count,
+                                                                       c->cap_slots);
+  else
+    k_collide_band<Q, T, true><<<blocks, TILE_CELLS, 0, c->stream>>>(P, p, c->d_slot_tile, c->d_band_count,
+                                                                      c->cap_slots);
   c->launches++;
   return cudaGetLastError();
 }
@@ -372,6 +456,8 @@ cudaError_t setpop_q(ibl_ctx* c, const double* d_f) {
   } while (0)
 
 cudaError_t launch_collide(ibl_ctx* c, bool with_ib) { IBL_DISPATCH(collide_q, with_ib); }
+cudaError_t launch_collide_bulk(ibl_ctx* c, int blocks) { IBL_DISPATCH(collide_bulk_q, blocks); }
+cudaError_t launch_collide_band(ibl_ctx* c, int blocks) { IBL_DISPATCH(collide_band_q, blocks); }
 cudaError_t launch_fields(ibl_ctx* c, double* d_rho, double* d_u, double* d_pop) {
   IBL_DISPATCH(fields_q, d_rho, d_u, d_pop);
 }

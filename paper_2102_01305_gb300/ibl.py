@@ -85,6 +85,10 @@ _SIGS = {
     "ibl_get_markers": ([_P, C.c_int32, _D, _D, _D], C.c_int),
     "ibl_mass": ([_P, _D], C.c_int),
     "ibl_mass_noalloc": ([_P, C.c_int32, _D], C.c_int),
+    "ibl_set_overlap": ([_P, C.c_int32], C.c_int),
+    "ibl_solver_blocks": ([_P, C.c_int32], C.c_int),
+    "ibl_interpolate_points": ([_P, C.c_int32, _P, _P, _P], C.c_int),
+    "ibl_spread_points": ([_P, C.c_int32, _P, _P, _P, _P], C.c_int),
     "ibl_lattice_velocities": ([C.c_int32, _I32, _I32, _D], C.c_int),
     "ibl_solver_stats": ([_P, _I32, _D, _I64], C.c_int),
     "ibl_solver_trace": ([_P, _I64, C.c_int32, _I32], C.c_int),
@@ -159,6 +163,30 @@ def _wave(w: dict | None):
         wv.table = _dptr(keep)
         wv.n_table = keep.size
     return wv, keep
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _device_f64(t, name, ndim, last):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if t.dim() != ndim or (last is not None and t.shape[-1] != last):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}")
+    return t.contiguous()
+
+
+def _device_out(t, shape, like):
+    torch = _torch()
+    if t is None:
+        return torch.empty(shape, dtype=torch.float64, device=like.device)
+    t = _device_f64(t, "output", len(shape), shape[-1])
+    if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"output must be a contiguous {shape} tensor")
+    return t
 
 
 class Context:
@@ -302,6 +330,45 @@ class Context:
         m = C.c_double()
         _check(self.h, _lib.ibl_mass_noalloc(self.h, int(nparts), C.byref(m)), allow)
         return m.value
+
+    def ibl_solver_blocks(self, blocks):
+        """Blocks of the cooperative solve (0: half the SMs)."""
+        _check(self.h, _lib.ibl_solver_blocks(self.h, int(blocks)))
+
+    def ibl_set_overlap(self, mode):
+        """-1 automatic, 0 one collide kernel after the IB chain, 1 split step."""
+        _check(self.h, _lib.ibl_set_overlap(self.h, int(mode)))
+
+    def ibl_interpolate_points(self, X, U=None, rho=None):
+        """rho and u* of the current populations at points X (Eq. 17).
+
+        X: CUDA float64 tensor [m, 3]; returns (U [m, d], rho [m]), freshly
+        allocated unless given.  Torch's current stream is synchronised first.
+        """
+        X = _device_f64(X, "X", 2, 3)
+        m = X.shape[0]
+        U = _device_out(U, (m, self.d), X)
+        rho = _device_out(rho, (m,), X)
+        _torch().cuda.current_stream(X.device).synchronize()
+        _check(self.h, _lib.ibl_interpolate_points(self.h, m, X.data_ptr(), U.data_ptr(), rho.data_ptr()))
+        return U, rho
+
+    def ibl_spread_points(self, X, V, ds, out=None):
+        """sum_l V_l ds_l D(x - X_l) on the grid (Eq. 15): [d, nz, ny, nx] float64.
+
+        X [m, 3], V [m, d], ds [m]: CUDA float64 tensors.
+        """
+        X = _device_f64(X, "X", 2, 3)
+        m = X.shape[0]
+        V = _device_f64(V, "V", 2, self.d)
+        ds = _device_f64(ds, "ds", 1, None)
+        if V.shape[0] != m or ds.shape[0] != m:
+            raise ValueError("X, V and ds need the same number of points")
+        out = _device_out(out, (self.d,) + self.shape, X)
+        _torch().cuda.current_stream(X.device).synchronize()
+        _check(self.h, _lib.ibl_spread_points(self.h, m, X.data_ptr(), V.data_ptr(), ds.data_ptr(),
+                                              out.data_ptr()))
+        return out
 
     def ibl_solver_stats(self, allow=()):
         it, res, ref = C.c_int32(), C.c_double(), C.c_int64()

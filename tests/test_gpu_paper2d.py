@@ -1,0 +1,68 @@
+"""GPU parity on the paper's own 2D cases, through the C ABI.
+
+* Clap and fling (Sec. 3.3): two elliptic foils of chord/thickness 5 hinged
+  at their trailing edges, gap c/2, opening per reading R8, in a 50c x 25c
+  box with a Zou-He velocity inlet and pressure outlet (chord 16 here).
+* Figure-eight hovering (Sec. 3.2, Eqs. 20-22): one foil of chord/thickness
+  7.5 pitching about its centre while sweeping along a stroke plane at 60
+  degrees, fluid at rest in a periodic 50c x 25c box.
+
+The oracle runs each case once (D2Q9 FP64, dense direct solve); the GPU runs
+it in FP64 and in FP32 storage.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.parity import (TOL_COEF_FP32, TOL_FIELD_FP32, TOL_FIELD_FP64, compare_fields,
+                          oracle_from_workload)
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 120
+
+
+def _cases():
+    return {
+        "clap_fling": lambda prec: W.clap_fling_2d(chord=16.0, Re=50.0, J=1.67e-3, period=800.0,
+                                                   precision=prec),
+        "figure_eight": lambda prec: W.figure_eight_2d(chord=16.0, Re=75.0, period=2000.0, precision=prec),
+    }
+
+
+@pytest.fixture(scope="module")
+def oracle_runs():
+    runs = {}
+    for name, make in _cases().items():
+        sim = oracle_from_workload(make("fp64"))
+        sim.step(STEPS)
+        runs[name] = sim
+    return runs
+
+
+def _coef_err(ctx, sim, body):
+    hist = ctx.ibl_force_history(body, STEPS)
+    ref = np.array(sim.history[body][-len(hist):])
+    scale = max(np.abs(ref[:, 0]).max(), np.abs(ref[:, 1]).max())
+    return (np.abs(hist[:, 0] - ref[:, 0]).max() / scale, np.abs(hist[:, 1] - ref[:, 1]).max() / scale)
+
+
+@pytest.mark.parametrize("name", ["clap_fling", "figure_eight"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_paper_2d_case(ibl, oracle_runs, name, prec):
+    cfg = _cases()[name](prec)
+    sim = oracle_runs[name]
+    ctx = ibl.from_workload(cfg)
+    ctx.ibl_step(STEPS)
+    tol_f, tol_c = (TOL_FIELD_FP64, 1e-7) if prec == "fp64" else (TOL_FIELD_FP32, TOL_COEF_FP32)
+    eu, er = compare_fields(ctx, sim, ibl, tol_f)
+    worst = 0.0
+    for b in range(len(cfg["bodies"])):
+        worst = max(worst, *_coef_err(ctx, sim, b))
+    print(f"{name} {prec} {STEPS} steps: u {eu:.2e} rho {er:.2e} coef {worst:.2e}")
+    assert worst < tol_c
+    if name == "clap_fling":
+        # mirror symmetry about the mid-plane: equal and opposite lateral lifts
+        hist = np.array(ctx.ibl_force_history(0, STEPS)), np.array(ctx.ibl_force_history(1, STEPS))
+        scale = np.abs(hist[0][:, 0]).max()
+        assert np.abs(hist[0][:, 0] - hist[1][:, 0]).max() < (1e-9 if prec == "fp64" else 1e-4) * scale

@@ -191,3 +191,29 @@ def test_cylinder_drag_is_positive_and_lift_small():
     CL, CT, CD = sim.history[0][-1]
     assert CD > 0 and abs(CT + CD) < 1e-15
     assert abs(CL) < 0.05 * CD
+
+
+def test_figure_eight_kinematics():
+    """Sec. 3.2 hovering wing (Eqs. 20-22): the centre sweeps +-A0/2 along the
+    stroke plane at beta = 60 deg, the pitch is 45 deg at t = 0 and 0 at
+    t = T/4, and the largest centre speed is Eq. 22's U_tip = pi f A0."""
+    from oracle.kinematics import marker_state
+    cfg = W.figure_eight_2d(chord=16.0, Re=75.0, period=2000.0)
+    b = cfg["bodies"][0]
+    p = cfg["params"]
+    org = np.array(b["origin"][:2])
+    es = np.array([0.5, math.sqrt(3.0) / 2.0])
+    T = 2000.0
+    probe = dict(b, X0=np.array([[0.0, 0.0], [-1.0, 0.0]]))   # centre, a point towards the leading edge
+    for t, A, alpha in ((0.0, p["A0"] / 2, math.pi / 4), (T / 4, 0.0, 0.0), (T / 2, -p["A0"] / 2, math.pi / 4)):
+        X, _ = marker_state(probe, t, 2)
+        assert np.abs(X[0] - (org + A * es)).max() < 1e-9
+        v = X[1] - X[0]
+        ang = math.atan2(v[1], v[0])
+        assert abs(((ang - (math.pi + alpha)) + math.pi) % (2 * math.pi) - math.pi) < 1e-9
+    speeds = []
+    for t in np.linspace(0.0, T, 401):
+        _, U = marker_state(probe, t, 2)
+        speeds.append(np.linalg.norm(U[0]))
+    assert abs(max(speeds) - p["u_tip"]) < 1e-12
+    assert abs(p["u_tip"] - math.pi * p["f"] * p["A0"]) < 1e-15

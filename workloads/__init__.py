@@ -245,6 +245,30 @@ def clap_fling_2d(chord=20.0, Re=100.0, J=1.67e-3, period=4000.0, thickness_rati
             "params": p}
 
 
+def figure_eight_2d(chord=16.0, Re=75.0, period=2000.0, domain=(50, 25), precision="fp64"):
+    """Sec. 3.2 hovering wing: an elliptic foil (chord/thickness 7.5) pitching
+    about its centre while sweeping along a stroke plane inclined at beta:
+    A(t) = (A0/2) cos(2 pi t/T + phi) (Eq. 20), alpha(t) = pi/4 - (pi/4)
+    sin(2 pi t/T + phi) (Eq. 21), A0/c = 2.5, beta = pi/3, phi = 0; Re =
+    pi f A0 c / nu (Eq. 22); fluid at rest in a periodic 50c x 25c box."""
+    f = 1.0 / period
+    A0 = 2.5 * chord
+    u_tip = math.pi * f * A0
+    nu = u_tip * chord / Re
+    nx, ny = int(domain[0] * chord), int(domain[1] * chord)
+    X0, ds = ellipse_foil_markers(chord, chord / 7.5)
+    body = {"X0": X0, "ds": ds, "hinge": (0.0, 0.0, 0.0), "axis": (0.0, 0.0, 1.0),
+            "origin": (0.5 * nx, 0.5 * ny, 0.0),
+            "A": {"kind": WAVE_COS, "amp": 0.5 * A0, "offset": 0.0},
+            "alpha": {"kind": WAVE_SIN, "amp": -0.25 * math.pi, "offset": 0.25 * math.pi},
+            "beta": math.pi / 3.0, "phi": 0.0, "f": f, "J": 0.0, "lift_axis": (0.0, 1.0, 0.0)}
+    return {"lattice": 9, "tau": 3.0 * nu + 0.5,
+            "grid": grid(nx, ny, 1, [PERIODIC] * 6, precision=precision),
+            "bodies": [body], "rho0": 1.0, "u0": (0.0, 0.0, 0.0),
+            "reference": {"U_ref": u_tip, "L": chord, "rho_ref": 1.0},
+            "params": {"f": f, "A0": A0, "u_tip": u_tip, "nu": nu, "Re": Re}}
+
+
 def taylor_green_3d(n=64, u0=0.05, tau=0.6, precision="fp32"):
     """Periodic D3Q19 Taylor-Green vortex on an n^3 cube (pure LBM, no markers)."""
     return {"lattice": 19, "tau": tau,
