@@ -22,6 +22,7 @@
 //   (end of k_pcg)   F_w = -sum_l 2 rho_l w_l per body in FP64, fixed order.
 #include <cooperative_groups.h>
 
+#include "df.cuh"
 #include "ib_stencil.cuh"
 
 namespace cg = cooperative_groups;
@@ -353,7 +354,7 @@ __device__ __forceinline__ bool pair_entry(const Geo& g, const int* bl, const do
 __global__ void k_assemble(int m_total, const int* __restrict__ base, const double* __restrict__ wts,
                            const int* __restrict__ tile_slot, const int* __restrict__ tile_mcount,
                            const int* __restrict__ tile_markers, Geo g, const int* __restrict__ body_of,
-                           int* __restrict__ Gcol, double* __restrict__ Gval, int* __restrict__ Gnnz,
+                           int* __restrict__ Gcol, df* __restrict__ Gval, int* __restrict__ Gnnz,
                            unsigned long long* __restrict__ rowsum_max, int* status,
                            const int* __restrict__ cand, const int* __restrict__ ncand,
                            const int* __restrict__ use_tiles, const int* __restrict__ cand_bad) {
@@ -385,7 +386,7 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
       if (take) {
         if (pos < G_MAXNNZ) {
           Gcol[(long long)l * G_MAXNNZ + pos] = k;
-          Gval[(long long)l * G_MAXNNZ + pos] = val;
+          Gval[(long long)l * G_MAXNNZ + pos] = df_from_double(val);
         } else {
           atomicOr(status, ST_OVERFLOW);
         }
@@ -443,7 +444,7 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
     int rank = 0;
     for (int j = 0; j < count; ++j) rank += s_col[wib][j] < key;
     Gcol[(long long)l * G_MAXNNZ + rank] = key;
-    Gval[(long long)l * G_MAXNNZ + rank] = s_val[wib][i];
+    Gval[(long long)l * G_MAXNNZ + rank] = df_from_double(s_val[wib][i]);
   }
   for (int o = 16; o > 0; o >>= 1) rowsum += __shfl_xor_sync(0xffffffffu, rowsum, o);
   if (lane == 0) {
@@ -470,21 +471,23 @@ struct PcgArgs {
   int row_slot;                 // floats per resident preconditioner row (0: rows read from L2)
   const int* body_of;
   const int* Gcol;
-  const double* Gval;
+  const df* Gv;     // system matrix entries (double-float)
   const int* Gnnz;
   const unsigned long long* rowsum_max;
   const double* B;
-  double* w;
-  double* w_prev;   // solution of the step before (extrapolated warm start)
-  double* r;
-  double* p;        // 2 x m x 3 ping-pong search directions
-  double* Ap;
-  double* z;
+  double* w;        // solution, FP64 copy for the spreading
+  // double-float vectors of the recurrence (m x 3)
+  df* wd;           // solution
+  df* wprevd;       // solution of the step before (extrapolated warm start)
+  df* rd;
+  df* pd;
+  df* Apd;
+  float* zf;        // preconditioned residual M r (FP32: the preconditioner's output)
   float* rf;        // FP32 copies feeding the preconditioner: r, A p, B
   float* Apf;
   float* Bf;
   float* M;
-  double* red;      // [gridDim][8] partials
+  df* red;          // [gridDim][8] partials
   int* info;        // [0] iterations, [1] rebuild request, [2] converged flag
   double* res;      // final relative residual
   double tol;
@@ -578,30 +581,37 @@ __device__ void grid_total(const double* red, int slot, double out[NV], double* 
   for (int c = 0; c < NV; ++c) out[c] = sh[c];
 }
 
-// The same fixed-order grid totals, for warp 0 only and without a block
-// barrier: every lane of warp 0 ends with the NV totals (pairwise tree over
-// each lane's partials, then a butterfly across lanes).
-template <int NV>
-__device__ __forceinline__ void warp0_total(const double* red, int slot, double v[NV]) {
+// Block partial of three double-float sums: lane c < 3 of every warp holds
+// component c; warp c adds the warps in a fixed order and writes out[c].
+__device__ void block_partial3(df v, df* sh, df* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane < 3) sh[3 * wid + lane] = v;
+  __syncthreads();
+  if (wid < 3) {
+    df t = lane < PCG_WARPS ? sh[3 * lane + wid] : df_make(0.f, 0.f);
+    t = df_warp_sum(t);
+    if (lane == 0) out[wid] = t;
+  }
+}
+
+// Grid total of one double-float partial (slot `slot` of every block), for
+// one warp: each lane issues all of its loads at once (one memory round
+// trip), adds its blocks in order, then a butterfly; every lane ends with
+// the total.
+__device__ __forceinline__ df grid_total_df(const df* red, int slot) {
   constexpr int U = MAX_PCG_BLOCKS / 32;
-  double buf[U][NV];
+  const int lane = threadIdx.x & 31;
+  float2 v[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    const int b = threadIdx.x + 32 * u;
-#pragma unroll
-    for (int c = 0; c < NV; ++c) buf[u][c] = b < (int)gridDim.x ? __ldcg(red + b * 8 + slot + c) : 0.0;
+    const int b = lane + 32 * u;
+    v[u] = b < (int)gridDim.x ? __ldcg(reinterpret_cast<const float2*>(red + b * 8 + slot)) : make_float2(0.f, 0.f);
   }
+  df acc = df_make(0.f, 0.f);
 #pragma unroll
-  for (int w = U / 2; w >= 1; w >>= 1)
-#pragma unroll
-    for (int u = 0; u < w; ++u)
-#pragma unroll
-      for (int c = 0; c < NV; ++c) buf[u][c] += buf[u + w][c];
-#pragma unroll
-  for (int c = 0; c < NV; ++c) v[c] = buf[0][c];
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int c = 0; c < NV; ++c) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+  for (int u = 0; u < U; ++u) acc = df_add(acc, df_make(v[u].x, v[u].y));
+  return df_warp_sum(acc);
 }
 
 // Row stride of a body's dense preconditioner: padded to 4 floats so rows
@@ -723,7 +733,7 @@ constexpr size_t GJ_SMEM = sizeof(float) * 2 * GJ_NB * GS;
 constexpr size_t PCG_SMEM = 96 * 1024;
 // upper bound of the dynamic shared memory (227 KB per block, less the
 // kernel's static shared memory)
-constexpr size_t PCG_SMEM_MAX = 226 * 1024;
+constexpr size_t PCG_SMEM_MAX = 224 * 1024;
 
 // out[i0+r][j0+c] = (acc ? out : 0) + alpha * sum_q A[r][q] B[q][j0+c] over one
 // tile (r < nr, c < nc), skipping output rows in [sk0, sk1) and columns in
@@ -907,6 +917,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) float sm[];
   __shared__ double shd[3 * PCG_WARPS + 8];
+  __shared__ df shdf[3 * PCG_WARPS + 8];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -933,7 +944,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
       for (int j = 0; j < A.Gnnz[l]; ++j) {
         const int k = A.Gcol[(long long)l * G_MAXNNZ + j];
         if (A.body_of[k] != b) continue;   // block-Jacobi over bodies
-        double v = A.Gval[(long long)l * G_MAXNNZ + j];
+        double v = df_to_double(A.Gv[(long long)l * G_MAXNNZ + j]);
         if (k == l) v += sigma;
         Mb[(long long)(l - o) * ld + (k - o)] = (float)v;
       }
@@ -957,252 +968,226 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   }
   trace_mark(A, 1);
 
-  // ---- set-up: w0 = 0, the last solution, or 2 w_n-1 - w_n-2 once two exist
-  // (the solution varies smoothly in time); r = B - G w0; FP32 copies; p = A p = 0
+  // ---- set-up (double-float vectors): w0 = 0, the last solution, or
+  // 2 w_n-1 - w_n-2 once two exist (the solution varies smoothly in time);
+  // r = B - G w0; FP32 copies; p = A p = 0
+  const df dzero = df_make(0.f, 0.f);
   if (A.warm >= 2) {
     for (int i = gtid; i < 3 * m; i += nthreads) {
-      const double cur = A.w[i];
-      A.w[i] = 2.0 * cur - A.w_prev[i];
-      A.w_prev[i] = cur;
+      const df cur = A.wd[i];
+      A.wd[i] = df_sub(df_make(2.f * cur.hi, 2.f * cur.lo), A.wprevd[i]);
+      A.wprevd[i] = cur;
     }
     grid.sync();
   } else if (A.warm == 1) {
-    for (int i = gtid; i < 3 * m; i += nthreads) A.w_prev[i] = A.w[i];
+    for (int i = gtid; i < 3 * m; i += nthreads) A.wprevd[i] = A.wd[i];
   }
   for (int l = row0; l < m; l += rstep) {
-    double s0 = 0, s1 = 0, s2 = 0;
+    dfacc a0 = acc_zero(), a1 = acc_zero(), a2 = acc_zero();
     if (A.warm) {
       const int nnz = A.Gnnz[l];
       for (int j = lane; j < nnz; j += 32) {
         const int k = A.Gcol[(long long)l * G_MAXNNZ + j];
-        const double v = A.Gval[(long long)l * G_MAXNNZ + j];
-        s0 += v * A.w[3 * k];
-        s1 += v * A.w[3 * k + 1];
-        s2 += v * A.w[3 * k + 2];
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        const df v = A.Gv[(long long)l * G_MAXNNZ + j];
+        acc_fma(a0, v, A.wd[3 * k]);
+        acc_fma(a1, v, A.wd[3 * k + 1]);
+        acc_fma(a2, v, A.wd[3 * k + 2]);
       }
     }
+    const df g0 = df_warp_sum(acc_value(a0)), g1 = df_warp_sum(acc_value(a1)), g2 = df_warp_sum(acc_value(a2));
     if (lane < 3) {
       const int c = lane;
       const int vi = A.voff[A.body_of[l]] + 3 * (l - A.boff[A.body_of[l]]) + c;
-      const double gx = c == 0 ? s0 : (c == 1 ? s1 : s2);
-      const double b = A.B[3 * l + c];
-      const double r = b - gx;
-      A.r[3 * l + c] = r;
-      A.rf[vi] = (float)r;
-      A.Bf[vi] = (float)b;
-      A.p[3 * l + c] = 0.0;
-      A.Ap[3 * l + c] = 0.0;
-      if (!A.warm) A.w[3 * l + c] = 0.0;
+      const df gx = c == 0 ? g0 : (c == 1 ? g1 : g2);
+      const df b = df_from_double(A.B[3 * l + c]);
+      const df r = df_sub(b, gx);
+      A.rd[3 * l + c] = r;
+      A.rf[vi] = r.hi;
+      A.Bf[vi] = b.hi;
+      A.pd[3 * l + c] = dzero;
+      A.Apd[3 * l + c] = dzero;
+      if (!A.warm) A.wd[3 * l + c] = dzero;
     }
   }
   grid.sync();
-  // z = M r and the stopping scale B.(M B): partials r.z (slots 3..5) and B.MB (0..2)
+  // z = M r and the stopping scale B.(M B): lane c of each warp accumulates
+  // component c; partials r.z (slots 3..5) and B.MB (0..2)
   {
-    double rz3[3] = {0, 0, 0}, bb3[3] = {0, 0, 0};
+    df rz = dzero, bb = dzero;
     const float zero3[3] = {0.f, 0.f, 0.f};
     const float* xs = stage_x(A, A.rf, nullptr, zero3, sm);
     for (int l = row0; l < m; l += rstep) {
       float zr[3];
       precond_row(A, l, xs, A.rf, nullptr, zero3, zr, lane, mres);
-      if (lane == 0)
-        for (int c = 0; c < 3; ++c) {
-          A.z[3 * l + c] = zr[c];
-          rz3[c] += A.r[3 * l + c] * (double)zr[c];
-        }
+      if (lane < 3) {
+        A.zf[3 * l + lane] = zr[lane];
+        rz = df_add(rz, df_mul_f(A.rd[3 * l + lane], zr[lane]));
+      }
     }
     xs = stage_x(A, A.Bf, nullptr, zero3, sm);
     for (int l = row0; l < m; l += rstep) {
       float zb[3];
       precond_row(A, l, xs, A.Bf, nullptr, zero3, zb, lane, mres);
-      if (lane == 0)
-        for (int c = 0; c < 3; ++c) bb3[c] += A.B[3 * l + c] * (double)zb[c];
+      if (lane < 3) bb = df_add(bb, df_mul_f(df_from_double(A.B[3 * l + lane]), zb[lane]));
     }
-    block_total3(rz3, shd);
-    block_total3(bb3, shd);
-    if (threadIdx.x == 0)
-      for (int c = 0; c < 3; ++c) {
-        A.red[blockIdx.x * 8 + 3 + c] = rz3[c];
-        A.red[blockIdx.x * 8 + c] = bb3[c];
-      }
+    block_partial3(bb, shdf, A.red + blockIdx.x * 8);
+    block_partial3(rz, shdf, A.red + blockIdx.x * 8 + 3);
   }
   grid.sync();
   trace_mark(A, 2);
-  // Scalars of the recurrence live in shared memory: thread 0 of each block
-  // computes them from the grid totals (FP64 divisions are expensive on this
-  // GPU; every block gets bitwise the same values).
-  __shared__ double s_rz[3], s_scale[3], s_beta[3], s_alpha[3];
+  // Scalars of the recurrence live in shared memory: warp 0 of each block
+  // forms them from the grid totals (every block gets bitwise the same values).
+  __shared__ df s_rz[3], s_scale[3], s_beta[3], s_alpha[3];
   __shared__ float s_alphaf[3];
-  __shared__ int s_done;
-  grid_total<3>(A.red, 0, s_scale, shd);
-  grid_total<3>(A.red, 3, s_rz, shd);
-  if (threadIdx.x == 0) {
-    bool d = true;
-    for (int c = 0; c < A.D; ++c) d &= !(s_rz[c] > A.tol * A.tol * s_scale[c]);
-    s_done = d ? 1 : 0;
-    for (int c = 0; c < 3; ++c) s_beta[c] = 0.0;
+  __shared__ double s_stop[3];
+  __shared__ int s_conv[3];
+  if (wib < 3) {
+    // warp c: totals of component c; the stopping threshold tol^2 (B.MB) once per solve
+    const int c = wib;
+    const df sc = grid_total_df(A.red, c);
+    const df rz = grid_total_df(A.red, 3 + c);
+    if (lane == 0) {
+      s_scale[c] = sc;
+      s_rz[c] = rz;
+      s_beta[c] = dzero;
+      s_stop[c] = A.tol * A.tol * df_to_double(sc);
+      s_conv[c] = (c >= A.D || !(df_to_double(rz) > s_stop[c])) ? 1 : 0;
+    }
   }
   __syncthreads();
+  const int s_done = s_conv[0] & s_conv[1] & s_conv[2];
   int it = 0;
   bool done = s_done != 0;
+  // z of every marker (FP32) in shared memory for the SpMV when it fits
+  const bool stage_z = 3 * m <= A.smem_floats;
   while (!done && it < PCG_MAX_ITERS) {
     // ---- P1: p = z + beta p;  A p = G z + beta A p;  partial p.Ap;  FP32 copies of r and A p
-    // beta was formed with the convergence test at the end of the previous iteration
-    const double beta[3] = {s_beta[0], s_beta[1], s_beta[2]};
     const int ts = 8 + TRACE_PER_IT * it;
     trace_mark(A, ts);
     {
-      // 8 lanes per row, 4 rows per warp: a 3-level FP64 tree instead of 5
-      double pAp3[3] = {0, 0, 0};
-      // z of every marker in shared memory when it fits (one round trip, 128-bit)
-      const double* zs = A.z;
-      if (3 * m * (int)sizeof(double) <= A.smem_floats * (int)sizeof(float)) {
+      df pAp = dzero;
+      const float* zs = A.zf;
+      if (stage_z) {
         __syncthreads();
-        const float4* src = reinterpret_cast<const float4*>(A.z);
+        const int n4 = (3 * m) >> 2;
+        const float4* src = reinterpret_cast<const float4*>(A.zf);
         float4* dst = reinterpret_cast<float4*>(sm);
-        const int n4 = (3 * m) / 2;               // 2 doubles per 16 bytes (3m even: m padded below)
 #pragma unroll 4
         for (int q = threadIdx.x; q < n4; q += blockDim.x) dst[q] = __ldcg(src + q);
-        if (threadIdx.x == 0 && (3 * m) % 2) reinterpret_cast<double*>(sm)[3 * m - 1] = __ldcg(A.z + 3 * m - 1);
+        for (int q = 4 * n4 + threadIdx.x; q < 3 * m; q += blockDim.x) sm[q] = __ldcg(A.zf + q);
         __syncthreads();
-        zs = reinterpret_cast<const double*>(sm);
+        zs = sm;
       }
       trace_mark(A, ts + 1);
+      // 8 lanes per row, 4 rows per warp
       const int sub = lane >> 3, sl = lane & 7;
       for (int l0 = row0 * 4; l0 < m; l0 += rstep * 4) {
         const int l = l0 + sub;
-        double s0 = 0, s1 = 0, s2 = 0;
+        dfacc a0 = acc_zero(), a1 = acc_zero(), a2 = acc_zero();
         if (l < m) {
           const int nnz = A.Gnnz[l];
           const int* gc = A.Gcol + (long long)l * G_MAXNNZ;
-          const double* gv = A.Gval + (long long)l * G_MAXNNZ;
-#pragma unroll 4
+          const df* gv = A.Gv + (long long)l * G_MAXNNZ;
+#pragma unroll 2
           for (int j = sl; j < nnz; j += 8) {
             const int k = gc[j];
-            const double v = gv[j];
-            s0 += v * zs[3 * k];
-            s1 += v * zs[3 * k + 1];
-            s2 += v * zs[3 * k + 2];
+            const df v = gv[j];
+            acc_fma_f(a0, v, zs[3 * k]);
+            acc_fma_f(a1, v, zs[3 * k + 1]);
+            acc_fma_f(a2, v, zs[3 * k + 2]);
           }
         }
-        for (int o = 4; o > 0; o >>= 1) {
-          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-          s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        }
-        double contrib = 0.0;
+        const df gz0 = df_warp_sum(acc_value(a0), 8), gz1 = df_warp_sum(acc_value(a1), 8);
+        const df gz2 = df_warp_sum(acc_value(a2), 8);
+        df contrib = dzero;
         if (l < m && sl < 3) {
           const int c = sl;
           const int bd = A.body_of[l];
           const int vi = A.voff[bd] + 3 * (l - A.boff[bd]) + c;
-          const double gz = c == 0 ? s0 : (c == 1 ? s1 : s2);
-          const double pl = A.z[3 * l + c] + beta[c] * A.p[3 * l + c];
-          const double ap = gz + beta[c] * A.Ap[3 * l + c];
-          A.p[3 * l + c] = pl;
-          A.Ap[3 * l + c] = ap;
-          A.Apf[vi] = (float)ap;
-          A.rf[vi] = (float)A.r[3 * l + c];
-          contrib = pl * ap;
+          const df gz = c == 0 ? gz0 : (c == 1 ? gz1 : gz2);
+          const df beta = s_beta[c];
+          const df pl = df_add(df_from_float(A.zf[3 * l + c]), df_mul(beta, A.pd[3 * l + c]));
+          const df ap = df_add(gz, df_mul(beta, A.Apd[3 * l + c]));
+          A.pd[3 * l + c] = pl;
+          A.Apd[3 * l + c] = ap;
+          A.Apf[vi] = ap.hi;
+          A.rf[vi] = A.rd[3 * l + c].hi;
+          contrib = df_mul(pl, ap);
         }
-        // lanes 8 sub + c hold component c of row l0 + sub: lane 0 gathers them in a fixed order
-        for (int r = 0; r < 4; ++r)
-          for (int c = 0; c < 3; ++c) {
-            const double v = __shfl_sync(0xffffffffu, contrib, 8 * r + c);
-            if (lane == 0) pAp3[c] += v;
-          }
+        // lane c < 3 gathers component c of the warp's four rows, in row order
+        for (int r = 0; r < 4; ++r) {
+          const int src = 8 * r + (lane & 7);
+          const df v = df_make(__shfl_sync(0xffffffffu, contrib.hi, src), __shfl_sync(0xffffffffu, contrib.lo, src));
+          if (lane < 3) pAp = df_add(pAp, v);
+        }
       }
       trace_mark(A, ts + 2);
-      block_total3(pAp3, shd);
-      if (threadIdx.x == 0)
-        for (int c = 0; c < 3; ++c) A.red[blockIdx.x * 8 + c] = pAp3[c];
+      block_partial3(pAp, shdf, A.red + blockIdx.x * 8);
       trace_mark(A, ts + 3);
     }
     grid.sync();
     trace_mark(A, ts + 4);
     // ---- P2: alpha;  z = M (r - alpha A p) in FP32;  w += alpha p;  r -= alpha A p;  partial r.z
-    {
-      // warp 0: totals p.Ap, then lanes 0-2 form alpha of their component
-      if (threadIdx.x < 32) {
-        double pAp[3];
-        warp0_total<3>(A.red, 0, pAp);
-        if (lane < 3) {
-          const int c = lane;
-          const double a = (pAp[c] > 0.0 && s_rz[c] > 0.0) ? s_rz[c] / pAp[c] : 0.0;
-          s_alpha[c] = a;
-          s_alphaf[c] = (float)a;
-        }
+    if (wib < 3) {
+      // warp c: total p.Ap of component c and the step length
+      const int c = wib;
+      const df pAp = grid_total_df(A.red, c);
+      if (lane == 0) {
+        const df a = (pAp.hi > 0.f && s_rz[c].hi > 0.f) ? df_div(s_rz[c], pAp) : dzero;
+        s_alpha[c] = a;
+        s_alphaf[c] = a.hi;
       }
-      __syncthreads();
     }
+    __syncthreads();
     trace_mark(A, ts + 5);
-    const double alpha[3] = {s_alpha[0], s_alpha[1], s_alpha[2]};
     const float alphaf[3] = {s_alphaf[0], s_alphaf[1], s_alphaf[2]};
     {
-      double rz3[3] = {0, 0, 0};
+      df rz = dzero;
       const float* xs = stage_x(A, A.rf, A.Apf, alphaf, sm);
       trace_mark(A, ts + 6);
       for (int l = row0; l < m; l += rstep) {
         float zl[3];
         precond_row(A, l, xs, A.rf, A.Apf, alphaf, zl, lane, mres);
-        double contrib = 0.0;
         if (lane < 3) {
           const int c = lane;
-          A.w[3 * l + c] += alpha[c] * A.p[3 * l + c];
-          const double rn = A.r[3 * l + c] - alpha[c] * A.Ap[3 * l + c];
-          A.r[3 * l + c] = rn;
-          A.z[3 * l + c] = zl[c];
-          contrib = rn * (double)zl[c];
-        }
-        const double c1 = __shfl_sync(0xffffffffu, contrib, 1);
-        const double c2 = __shfl_sync(0xffffffffu, contrib, 2);
-        if (lane == 0) {
-          rz3[0] += contrib;
-          rz3[1] += c1;
-          rz3[2] += c2;
+          const df alpha = s_alpha[c];
+          A.wd[3 * l + c] = df_add(A.wd[3 * l + c], df_mul(alpha, A.pd[3 * l + c]));
+          const df rn = df_sub(A.rd[3 * l + c], df_mul(alpha, A.Apd[3 * l + c]));
+          A.rd[3 * l + c] = rn;
+          A.zf[3 * l + c] = zl[c];
+          rz = df_add(rz, df_mul_f(rn, zl[c]));
         }
       }
       trace_mark(A, ts + 7);
-      block_total3(rz3, shd);
-      if (threadIdx.x == 0)
-        for (int c = 0; c < 3; ++c) A.red[blockIdx.x * 8 + 3 + c] = rz3[c];
+      block_partial3(rz, shdf, A.red + blockIdx.x * 8 + 3);
     }
     grid.sync();
     trace_mark(A, ts + 8);
-    {
-      // warp 0: totals r.z; lanes 0-2 form beta for the next iteration; lane 0 tests convergence
-      if (threadIdx.x < 32) {
-        double rzn[3];
-        warp0_total<3>(A.red, 3, rzn);
-        if (lane < 3) {
-          const int c = lane;
-          const double prev = s_rz[c];
-          s_beta[c] = prev > 0.0 ? rzn[c] / prev : 0.0;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          bool d = true;
-          for (int c = 0; c < 3; ++c) s_rz[c] = rzn[c];
-          for (int c = 0; c < A.D; ++c) d &= !(s_rz[c] > A.tol * A.tol * s_scale[c]);
-          s_done = d ? 1 : 0;
-        }
+    // warp c: total r.z of component c, beta for the next iteration, convergence test
+    if (wib < 3) {
+      const int c = wib;
+      const df rzn = grid_total_df(A.red, 3 + c);
+      if (lane == 0) {
+        const df prev = s_rz[c];
+        s_beta[c] = prev.hi > 0.f ? df_div(rzn, prev) : dzero;
+        s_rz[c] = rzn;
+        s_conv[c] = (c >= A.D || !(df_to_double(rzn) > s_stop[c])) ? 1 : 0;
       }
-      __syncthreads();
     }
+    __syncthreads();
     ++it;
-    done = s_done != 0;
+    done = (s_conv[0] & s_conv[1] & s_conv[2]) != 0;
   }
   trace_mark(A, 3);
-  // ---- body forces F_w = -sum_l 2 rho_l w_l (Eq. 26 x ds, Sec. 3.7): block b reduces
-  // body b in a fixed order (lane-strided FP64 sums, fixed shuffle tree, warp order)
+  // ---- FP64 copy of the solution for the spreading; body forces
+  // F_w = -sum_l 2 rho_l w_l (Eq. 26 x ds, Sec. 3.7): block b reduces body b in
+  // a fixed order (lane-strided FP64 sums, fixed shuffle tree, warp order)
+  for (int i = gtid; i < 3 * m; i += nthreads) A.w[i] = df_to_double(A.wd[i]);
   for (int b = blockIdx.x; b < A.nbodies; b += gridDim.x) {
     double v[3] = {0, 0, 0};
     for (int l = A.boff[b] + threadIdx.x; l < A.boff[b + 1]; l += blockDim.x)
       for (int c = 0; c < 3; ++c) {
-        const double f = 2.0 * A.rho_l[l] * A.w[3 * l + c];   // force on the fluid
+        const double f = 2.0 * A.rho_l[l] * df_to_double(A.wd[3 * l + c]);   // force on the fluid
         A.mforce[3 * l + c] = f;
         v[c] += f;
       }
@@ -1217,7 +1202,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   if (gtid == 0) {
     double rel = 0.0;
     for (int c = 0; c < A.D; ++c)
-      if (s_scale[c] > 0.0) rel = fmax(rel, sqrt(fmax(s_rz[c], 0.0) / s_scale[c]));
+      if (s_scale[c].hi > 0.f) rel = fmax(rel, sqrt(fmax(df_to_double(s_rz[c]), 0.0) / df_to_double(s_scale[c])));
     A.info[0] = it;
     A.info[1] = (it > REFRESH_ITERS || !done) ? 1 : 0;
     A.info[2] = done ? 1 : 0;
@@ -1533,7 +1518,8 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   IBL_CU(cudaMemsetAsync(c->d_Gdiag_max, 0, sizeof(double) * MAX_BODIES, c->stream));
   k_assemble<<<(m + 7) / 8, 256, 0, c->stream>>>(m, c->d_base, c->d_wts, c->d_tile_slot,
                                                  c->d_tile_mcount, c->d_tile_markers, g, c->d_body, c->d_Gcol,
-                                                 c->d_Gval, c->d_Gnnz, (unsigned long long*)c->d_Gdiag_max,
+                                                 reinterpret_cast<df*>(c->d_Gval), c->d_Gnnz,
+                                                 (unsigned long long*)c->d_Gdiag_max,
                                                  c->d_status, c->d_cand, c->d_ncand, c->d_mixed,
                                                  c->d_mixed + 1);
   c->launches += 1;
@@ -1549,9 +1535,17 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   }
   A.boff[A.nbodies] = m;
   A.body_of = c->d_body;
-  A.Gcol = c->d_Gcol; A.Gval = c->d_Gval; A.Gnnz = c->d_Gnnz;
+  A.Gcol = c->d_Gcol; A.Gv = reinterpret_cast<const df*>(c->d_Gval); A.Gnnz = c->d_Gnnz;
   A.rowsum_max = (const unsigned long long*)c->d_Gdiag_max;
-  A.B = c->d_B; A.w = c->d_w; A.r = c->d_r; A.p = c->d_p; A.Ap = c->d_Ap; A.z = c->d_z;
+  A.B = c->d_B; A.w = c->d_w;
+  // the double-float vectors reuse the FP64 work arrays (8 bytes per entry);
+  // the search direction array holds two m x 3 vectors: p and the solution
+  A.rd = reinterpret_cast<df*>(c->d_r);
+  A.pd = reinterpret_cast<df*>(c->d_p);
+  A.wd = reinterpret_cast<df*>(c->d_p) + 3 * (size_t)m;
+  A.Apd = reinterpret_cast<df*>(c->d_Ap);
+  A.zf = reinterpret_cast<float*>(c->d_z);
+  A.wprevd = reinterpret_cast<df*>(c->d_wprev);
   A.rf = c->d_xf;
   A.Apf = c->d_xf + c->xf_floats;
   A.Bf = c->d_xf + 2 * c->xf_floats;
@@ -1563,12 +1557,12 @@ cudaError_t ib_step_back(ibl_ctx* c) {
     }
     A.vtotal = vo;
   }
-  // shared memory: a staging area (z in FP64 for the SpMV, or the FP32
-  // preconditioner input) and, when they fit, this block's preconditioner rows
+  // shared memory: a staging area (z for the SpMV, or the preconditioner
+  // input, both FP32) and, when they fit, this block's preconditioner rows
   const int pcg_blocks = pcg_block_count(c);
   {
     // vectors larger than PCG_SMEM are read from L2 instead of being staged
-    size_t stage = std::max<size_t>((size_t)3 * m * sizeof(double), (size_t)A.vtotal * sizeof(float));
+    size_t stage = std::max<size_t>((size_t)3 * m * sizeof(float), (size_t)A.vtotal * sizeof(float));
     stage = std::max(std::min((stage + 15) & ~(size_t)15, PCG_SMEM), GJ_SMEM);
     int slot = 0;
     for (int b = 0; b < A.nbodies; ++b) slot = std::max(slot, precond_ld(c->bodies[b].m));
@@ -1580,9 +1574,8 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   }
   A.tol = c->solver_tol > 0 ? c->solver_tol
                              : (c->prec == IBL_FP64 ? PCG_TOL : (c->prec == IBL_FP32 ? PCG_TOL_FP32 : PCG_TOL_HALF));
-  A.M = c->d_M; A.red = c->d_red; A.info = c->d_cg_info; A.res = c->d_cg_res;
+  A.M = c->d_M; A.red = reinterpret_cast<df*>(c->d_red); A.info = c->d_cg_info; A.res = c->d_cg_res;
   A.warm = c->warm_steps >= 2 && c->extrapolate ? 2 : (c->warm_steps >= 1 ? 1 : 0);
-  A.w_prev = c->d_wprev;
   const bool sched = !c->precond_valid || (c->step - c->last_refresh_step) >= c->refresh_every;
   A.refresh = sched ? 1 : 0;
   if (sched) {
