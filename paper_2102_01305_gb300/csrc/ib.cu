@@ -105,7 +105,7 @@ __global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ 
                              const double* __restrict__ X0, const double* __restrict__ Xp,
                              const double* __restrict__ Up, double* __restrict__ X,
                              double* __restrict__ U, int* __restrict__ base,
-                             double* __restrict__ wts, double t, Geo geo, int* status) {
+                             df* __restrict__ wts, double t, Geo geo, int* status) {
   __shared__ double sst[MAX_BODIES][8];
   if (threadIdx.x < bt.n) body_state(bt.b[threadIdx.x], t, sst[threadIdx.x]);
   __syncthreads();
@@ -141,16 +141,16 @@ __global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ 
   for (int a = 0; a < 3; ++a) {
     if (a >= geo.D) {
       base[3 * l + a] = 0;
-      wts[12 * l + 4 * a + 0] = 1.0;
-      wts[12 * l + 4 * a + 1] = 0.0;
-      wts[12 * l + 4 * a + 2] = 0.0;
-      wts[12 * l + 4 * a + 3] = 0.0;
+      wts[12 * l + 4 * a + 0] = df_make(1.f, 0.f);
+      wts[12 * l + 4 * a + 1] = df_make(0.f, 0.f);
+      wts[12 * l + 4 * a + 2] = df_make(0.f, 0.f);
+      wts[12 * l + 4 * a + 3] = df_make(0.f, 0.f);
       continue;
     }
     int b0;
     double w[4];
     if (!stencil_axis(x[a], geo.n[a], geo.per[a] != 0, b0, w)) atomicOr(status, ST_OVERFLOW);
-    for (int k = 0; k < 4; ++k) wts[12 * l + 4 * a + k] = w[k];
+    for (int k = 0; k < 4; ++k) wts[12 * l + 4 * a + k] = df_from_double(w[k]);
     base[3 * l + a] = b0;
   }
 }
@@ -244,37 +244,40 @@ __global__ void k_append_markers(int m_total, const int* __restrict__ base, Geo 
 // collision), FP64 accumulation; B = U_B - u*_l (Eq. 19).  One warp per
 // marker, 64 (3D) or 16 (2D) nodes over its lanes.
 template <int Q, class T, bool PULL>
-__global__ void k_interpolate(int m_total, const int* __restrict__ base, const double* __restrict__ wts,
+__global__ void k_interpolate(int m_total, const int* __restrict__ base, const df* __restrict__ wts,
                               const T* __restrict__ src, FluidParams<typename Store<T>::R> p, Geo g,
                               const double* __restrict__ U, double* __restrict__ rho_l,
                               double* __restrict__ B) {
+  using R = typename Store<T>::R;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= m_total) return;
   const int l = warp;
   const int* b = base + 3 * l;
-  const double* w = wts + 12 * l;
+  const df* w = wts + 12 * l;
   const int nnodes = g.D == 3 ? 64 : 16;
-  double acc[4] = {0, 0, 0, 0};
+  // double-float accumulation of sum_x D(x - X_l) (1 + drho, u*): the weight
+  // products and sums stay on the FP32 pipes
+  dfacc acc[4] = {acc_zero(), acc_zero(), acc_zero(), acc_zero()};
   for (int k = lane; k < nnodes; k += 32) {
     const int i = k & 3, j = (k >> 2) & 3, q = k >> 4;
     int node[3] = {b[0] + i, b[1] + j, g.D == 3 ? b[2] + q : 0};
     for (int a = 0; a < g.D; ++a)
       if (g.per[a]) node[a] = wrap(node[a], g.n[a]);
-    const double wt = w[i] * w[4 + j] * w[8 + (g.D == 3 ? q : 0)];
+    df wt = df_mul(w[i], w[4 + j]);
+    if (g.D == 3) wt = df_mul(wt, w[8 + q]);
     const long long cell = ((long long)node[2] * p.ny + node[1]) * p.nx + node[0];
-    double rho, u[3];
-    node_rho_u<Q, T, PULL>(src, node[0], node[1], node[2], cell, p, rho, u);
-    acc[0] += wt * rho;
-    acc[1] += wt * u[0];
-    acc[2] += wt * u[1];
-    acc[3] += wt * u[2];
+    R drho, u[3];
+    node_moments<Q, T, PULL>(src, node[0], node[1], node[2], cell, p, drho, u);
+    acc_fma(acc[0], wt, df_from_float(1.f));
+    acc_fma(acc[0], wt, to_df(drho));
+    for (int c = 0; c < 3; ++c) acc_fma(acc[1 + c], wt, to_df(u[c]));
   }
-  for (int o = 16; o > 0; o >>= 1)
-    for (int c = 0; c < 4; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+  df v[4];
+  for (int c = 0; c < 4; ++c) v[c] = df_warp_sum(acc_value(acc[c]));
   if (lane == 0) {
-    rho_l[l] = acc[0];
-    for (int a = 0; a < 3; ++a) B[3 * l + a] = (a < g.D) ? U[3 * l + a] - acc[1 + a] : 0.0;
+    rho_l[l] = df_to_double(v[0]);
+    for (int a = 0; a < 3; ++a) B[3 * l + a] = (a < g.D) ? U[3 * l + a] - df_to_double(v[1 + a]) : 0.0;
   }
 }
 
@@ -333,17 +336,17 @@ __device__ __forceinline__ int base_diff(int bk, int bl, int n, int per) {
 // the SpMV sums in a fixed order.
 // Overlap product of the two stencils of markers l and k (Eq. 18 entry
 // without ds_k); false if the stencils do not share a node.
-__device__ __forceinline__ bool pair_entry(const Geo& g, const int* bl, const double* wl, const int* bk,
-                                           const double* wk, double& val, int lo[3]) {
-  double prod = 1.0;
+__device__ __forceinline__ bool pair_entry(const Geo& g, const int* bl, const df* wl, const int* bk,
+                                           const df* wk, df& val, int lo[3]) {
+  df prod = df_make(1.f, 0.f);
   for (int a = 0; a < 3; ++a) {
     if (a >= g.D) { lo[a] = 0; continue; }
     const int d = base_diff(bk[a], bl[a], g.n[a], g.per[a]);   // base_k - base_l
     if (d < -3 || d > 3) return false;
     const int o0 = d > 0 ? d : 0, o1 = d < 0 ? 3 + d : 3;
-    double s1 = 0.0;
-    for (int o = o0; o <= o1; ++o) s1 += wl[4 * a + o] * wk[4 * a + (o - d)];
-    prod *= s1;
+    dfacc s1 = acc_zero();
+    for (int o = o0; o <= o1; ++o) acc_fma(s1, wl[4 * a + o], wk[4 * a + (o - d)]);
+    prod = df_mul(prod, acc_value(s1));
     const int node = bl[a] + o0;
     lo[a] = g.per[a] ? wrap(node, g.n[a]) : node;
   }
@@ -351,7 +354,7 @@ __device__ __forceinline__ bool pair_entry(const Geo& g, const int* bl, const do
   return true;
 }
 
-__global__ void k_assemble(int m_total, const int* __restrict__ base, const double* __restrict__ wts,
+__global__ void k_assemble(int m_total, const int* __restrict__ base, const df* __restrict__ wts,
                            const int* __restrict__ tile_slot, const int* __restrict__ tile_mcount,
                            const int* __restrict__ tile_markers, Geo g, const int* __restrict__ body_of,
                            int* __restrict__ Gcol, df* __restrict__ Gval, int* __restrict__ Gnnz,
@@ -359,22 +362,22 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
                            const int* __restrict__ cand, const int* __restrict__ ncand,
                            const int* __restrict__ use_tiles, const int* __restrict__ cand_bad) {
   __shared__ int s_col[8][G_MAXNNZ];
-  __shared__ double s_val[8][G_MAXNNZ];
+  __shared__ df s_val[8][G_MAXNNZ];
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int l = blockIdx.x * 8 + wib;
   if (l >= m_total) return;
   const int* bl = base + 3 * l;
-  const double* wl = wts + 12 * l;
+  const df* wl = wts + 12 * l;
   if (cand && !*use_tiles && !*cand_bad) {
     // rigid-body path: precomputed candidates, already in ascending order
     const int nc = ncand[l];
     int count = 0;
-    double rowsum = 0.0;
+    float rowsum = 0.f;
     for (int j0 = 0; j0 < nc; j0 += 32) {
       const int j = j0 + lane;
       bool take = false;
-      double val = 0.0;
+      df val = df_make(0.f, 0.f);
       int k = -1;
       if (j < nc) {
         k = cand[(long long)l * CAND_MAX + j];
@@ -386,25 +389,25 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
       if (take) {
         if (pos < G_MAXNNZ) {
           Gcol[(long long)l * G_MAXNNZ + pos] = k;
-          Gval[(long long)l * G_MAXNNZ + pos] = df_from_double(val);
+          Gval[(long long)l * G_MAXNNZ + pos] = val;
         } else {
           atomicOr(status, ST_OVERFLOW);
         }
-        rowsum += fabs(val);
+        rowsum += fabsf(val.hi);
       }
       count += __popc(mask);
     }
     for (int o = 16; o > 0; o >>= 1) rowsum += __shfl_xor_sync(0xffffffffu, rowsum, o);
     if (lane == 0) {
       Gnnz[l] = min(count, G_MAXNNZ);
-      atomicMax(&rowsum_max[body_of[l]], (unsigned long long)__double_as_longlong(rowsum));
+      atomicMax(&rowsum_max[body_of[l]], (unsigned long long)__double_as_longlong((double)rowsum));
     }
     return;
   }
   int tiles[8];
   const int nt = touched_tiles(g, bl, tiles);
   int count = 0;
-  double rowsum = 0.0;
+  float rowsum = 0.f;
   for (int ti = 0; ti < nt; ++ti) {
     const int t = tiles[ti];
     const int s = tile_slot[t];
@@ -413,7 +416,7 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
     for (int j0 = 0; j0 < cnt; j0 += 32) {
       const int j = j0 + lane;
       bool take = false;
-      double val = 0.0;
+      df val = df_make(0.f, 0.f);
       int k = -1;
       if (j < cnt) {
         k = tile_markers[s * TILE_MARKER_CAP + j];
@@ -431,7 +434,7 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
         } else {
           atomicOr(status, ST_OVERFLOW);
         }
-        rowsum += fabs(val);
+        rowsum += fabsf(val.hi);
       }
       count += __popc(mask);
     }
@@ -444,12 +447,12 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const doub
     int rank = 0;
     for (int j = 0; j < count; ++j) rank += s_col[wib][j] < key;
     Gcol[(long long)l * G_MAXNNZ + rank] = key;
-    Gval[(long long)l * G_MAXNNZ + rank] = df_from_double(s_val[wib][i]);
+    Gval[(long long)l * G_MAXNNZ + rank] = s_val[wib][i];
   }
   for (int o = 16; o > 0; o >>= 1) rowsum += __shfl_xor_sync(0xffffffffu, rowsum, o);
   if (lane == 0) {
     Gnnz[l] = count;
-    atomicMax(&rowsum_max[body_of[l]], (unsigned long long)__double_as_longlong(rowsum));
+    atomicMax(&rowsum_max[body_of[l]], (unsigned long long)__double_as_longlong((double)rowsum));
   }
 }
 
@@ -725,7 +728,7 @@ __device__ __forceinline__ void precond_row(const PcgArgs& A, int l, const float
 //   P <- P^-1;  row panel R <- P^-1 R;  rest S <- S - C R;  column panel C <- -C P^-1.
 // The three panel products run through one register-tiled shared-memory
 // routine (128 x 128 output tiles, 4 x 4 outputs per thread, K <= GJ_NB).
-constexpr int GT = 128;                 // output tile edge (GT x GJ_NB = 2 x 4 x PCG_THREADS floats)
+constexpr int GT = 128;                 // output tile edge (GT x GJ_NB = 2048 float4 groups)
 constexpr int GS = GT + 4;              // padded shared-memory row
 constexpr size_t GJ_SMEM = sizeof(float) * 2 * GJ_NB * GS;
 // dynamic shared memory of the solve kernel: the rebuild's tiles or, during
@@ -746,63 +749,69 @@ __device__ void tile_gemm(float* out, int ldo, const float* Ag, int lda, const f
   float* As = sm;               // [q][r], GJ_NB x GS
   float* Bs = sm + GJ_NB * GS;  // [q][c], GJ_NB x GS
   __syncthreads();
-  // 128-bit staging, two groups per thread and operand, all loads in flight
-  // (rows, columns and K are multiples of 4 except at ragged edges, where the
-  // group falls back to masked scalar loads); lda, ldb and the tile origins
-  // are multiples of 4 floats, so full groups are 16-byte aligned.
-  float4 av[2], bv[2];
+  // 128-bit staging of 2048 float4 groups per operand, two per thread and
+  // operand in flight at a time (rows, columns and K are multiples of 4
+  // except at ragged edges, where the group falls back to masked scalar
+  // loads); lda, ldb and the tile origins are multiples of 4 floats, so full
+  // groups are 16-byte aligned.
+  for (int u0 = 0; u0 < 2048 / PCG_THREADS; u0 += 2) {
+    float4 av[2], bv[2];
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int f = threadIdx.x + u * PCG_THREADS;
-    const int r = f >> 4, q4 = (f & 15) << 2;
-    if (r < nr && q4 + 3 < K) {
-      av[u] = __ldcg(reinterpret_cast<const float4*>(Ag + (long long)r * lda + q4));
-    } else {
-      float t[4];
-      for (int i = 0; i < 4; ++i) t[i] = (r < nr && q4 + i < K) ? Ag[(long long)r * lda + q4 + i] : 0.f;
-      av[u] = make_float4(t[0], t[1], t[2], t[3]);
+    for (int u = 0; u < 2; ++u) {
+      const int f = threadIdx.x + (u0 + u) * PCG_THREADS;
+      const int r = f >> 4, q4 = (f & 15) << 2;
+      if (r < nr && q4 + 3 < K) {
+        av[u] = __ldcg(reinterpret_cast<const float4*>(Ag + (long long)r * lda + q4));
+      } else {
+        float t[4];
+        for (int i = 0; i < 4; ++i) t[i] = (r < nr && q4 + i < K) ? Ag[(long long)r * lda + q4 + i] : 0.f;
+        av[u] = make_float4(t[0], t[1], t[2], t[3]);
+      }
+      const int q = f >> 5, c4 = (f & 31) << 2;
+      if (q < K && c4 + 3 < nc) {
+        bv[u] = __ldcg(reinterpret_cast<const float4*>(Bg + (long long)q * ldb + j0 + c4));
+      } else {
+        float t[4];
+        for (int i = 0; i < 4; ++i) t[i] = (q < K && c4 + i < nc) ? Bg[(long long)q * ldb + j0 + c4 + i] : 0.f;
+        bv[u] = make_float4(t[0], t[1], t[2], t[3]);
+      }
     }
-    const int q = f >> 5, c4 = (f & 31) << 2;
-    if (q < K && c4 + 3 < nc) {
-      bv[u] = __ldcg(reinterpret_cast<const float4*>(Bg + (long long)q * ldb + j0 + c4));
-    } else {
-      float t[4];
-      for (int i = 0; i < 4; ++i) t[i] = (q < K && c4 + i < nc) ? Bg[(long long)q * ldb + j0 + c4 + i] : 0.f;
-      bv[u] = make_float4(t[0], t[1], t[2], t[3]);
-    }
-  }
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int f = threadIdx.x + u * PCG_THREADS;
-    const int r = f >> 4, q4 = (f & 15) << 2;
-    As[(q4 + 0) * GS + r] = av[u].x;
-    As[(q4 + 1) * GS + r] = av[u].y;
-    As[(q4 + 2) * GS + r] = av[u].z;
-    As[(q4 + 3) * GS + r] = av[u].w;
-    const int q = f >> 5, c4 = (f & 31) << 2;
-    *reinterpret_cast<float4*>(Bs + q * GS + c4) = bv[u];
+    for (int u = 0; u < 2; ++u) {
+      const int f = threadIdx.x + (u0 + u) * PCG_THREADS;
+      const int r = f >> 4, q4 = (f & 15) << 2;
+      As[(q4 + 0) * GS + r] = av[u].x;
+      As[(q4 + 1) * GS + r] = av[u].y;
+      As[(q4 + 2) * GS + r] = av[u].z;
+      As[(q4 + 3) * GS + r] = av[u].w;
+      const int q = f >> 5, c4 = (f & 31) << 2;
+      *reinterpret_cast<float4*>(Bs + q * GS + c4) = bv[u];
+    }
   }
   __syncthreads();
-  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-  float a4[4][4];
-  for (int u = 0; u < 4; ++u)
-    for (int v = 0; v < 4; ++v) a4[u][v] = 0.f;
-  for (int q = 0; q < K; ++q) {
-    const float4 av = *reinterpret_cast<const float4*>(As + q * GS + 4 * ty);
-    const float4 bv = *reinterpret_cast<const float4*>(Bs + q * GS + 4 * tx);
-    const float ar[4] = {av.x, av.y, av.z, av.w};
-    const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+  // 32 x 32 groups of 4 x 4 outputs, PCG_THREADS / 32 row groups at a time
+  const int tx = threadIdx.x & 31;
+  for (int ty = threadIdx.x >> 5; ty < 32; ty += PCG_THREADS / 32) {
+    float a4[4][4];
     for (int u = 0; u < 4; ++u)
-      for (int v = 0; v < 4; ++v) a4[u][v] = fmaf(ar[u], br[v], a4[u][v]);
-  }
-  for (int u = 0; u < 4; ++u) {
-    const int r = 4 * ty + u, i = i0 + r;
-    if (r >= nr || (i >= sk0 && i < sk1)) continue;
-    for (int v = 0; v < 4; ++v) {
-      const int c = 4 * tx + v, j = j0 + c;
-      if (c >= nc || (j >= ck0 && j < ck1)) continue;
-      float* o = out + (long long)i * ldo + j;
-      *o = (acc ? *o : 0.f) + alpha * a4[u][v];
+      for (int v = 0; v < 4; ++v) a4[u][v] = 0.f;
+    for (int q = 0; q < K; ++q) {
+      const float4 av = *reinterpret_cast<const float4*>(As + q * GS + 4 * ty);
+      const float4 bv = *reinterpret_cast<const float4*>(Bs + q * GS + 4 * tx);
+      const float ar[4] = {av.x, av.y, av.z, av.w};
+      const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+      for (int u = 0; u < 4; ++u)
+        for (int v = 0; v < 4; ++v) a4[u][v] = fmaf(ar[u], br[v], a4[u][v]);
+    }
+    for (int u = 0; u < 4; ++u) {
+      const int r = 4 * ty + u, i = i0 + r;
+      if (r >= nr || (i >= sk0 && i < sk1)) continue;
+      for (int v = 0; v < 4; ++v) {
+        const int c = 4 * tx + v, j = j0 + c;
+        if (c >= nc || (j >= ck0 && j < ck1)) continue;
+        float* o = out + (long long)i * ldo + j;
+        *o = (acc ? *o : 0.f) + alpha * a4[u][v];
+      }
     }
   }
 }
@@ -1218,28 +1227,32 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
 // are bitwise independent of the order the atomics land in.
 constexpr double FIX_LIMIT = 9.0e18 / FIX_SCALE;   // |sum| < 1.3e5 at 2^46, resolution 1.4e-14
 
-__global__ void k_spread_scatter(int m_total, const int* __restrict__ base, const double* __restrict__ wts,
-                                 const double* __restrict__ wsol, const int* __restrict__ tile_slot, Geo g,
+__global__ void k_spread_scatter(int m_total, const int* __restrict__ base, const df* __restrict__ wts,
+                                 const df* __restrict__ wsol, const int* __restrict__ tile_slot, Geo g,
                                  unsigned long long* __restrict__ acc, int* status) {
   const int nn = g.D == 3 ? 64 : 16;
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int l = (int)(gid / nn), k = (int)(gid % nn);
   if (l >= m_total) return;
   const int* b = base + 3 * l;
-  const double* w = wts + 12 * l;
+  const df* w = wts + 12 * l;
   const int i = k & 3, j = (k >> 2) & 3, q = k >> 4;
   int node[3] = {b[0] + i, b[1] + j, g.D == 3 ? b[2] + q : 0};
   for (int a = 0; a < g.D; ++a)
     if (g.per[a]) node[a] = wrap(node[a], g.n[a]);
-  const double wt = w[i] * w[4 + j] * w[8 + (g.D == 3 ? q : 0)];
+  df wt = df_mul(w[i], w[4 + j]);
+  if (g.D == 3) wt = df_mul(wt, w[8 + q]);
   const int s = tile_slot[tile_of(g, node[0], node[1], node[2])];
   if (s < 0) return;
   const int local = ((node[2] % g.tg.tz) * g.tg.ty + (node[1] % g.tg.ty)) * g.tg.tx + (node[0] % g.tg.tx);
   unsigned long long* a3 = acc + (long long)s * 3 * TILE_CELLS + local;
   for (int c = 0; c < g.D; ++c) {
-    const double v = wt * wsol[3 * l + c];
-    if (!(fabs(v) < FIX_LIMIT)) { atomicOr(status, ST_OVERFLOW); continue; }
-    atomicAdd(a3 + c * TILE_CELLS, (unsigned long long)__double2ll_rn(v * FIX_SCALE));
+    // the double-float product in fixed point: both parts scale exactly by
+    // 2^46 and round to integers separately (error <= 1 unit of 2^-46)
+    const df v = df_mul(wt, wsol[3 * l + c]);
+    if (!(fabsf(v.hi) < (float)FIX_LIMIT)) { atomicOr(status, ST_OVERFLOW); continue; }
+    const long long fx = __float2ll_rn(v.hi * (float)FIX_SCALE) + __float2ll_rn(v.lo * (float)FIX_SCALE);
+    atomicAdd(a3 + c * TILE_CELLS, (unsigned long long)fx);
   }
 }
 
@@ -1412,9 +1425,11 @@ static cudaError_t interpolate_q(ibl_ctx* c, const Geo& g) {
   const int m = c->m_total;
   const int wb = (m * 32 + 255) / 256;
   if (c->poststream)
-    k_interpolate<Q, T, false><<<wb, 256, 0, c->stream>>>(m, c->d_base, c->d_wts, src, p, g, c->d_U, c->d_rho_l, c->d_B);
+    k_interpolate<Q, T, false><<<wb, 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts), src, p, g, c->d_U,
+                                                               c->d_rho_l, c->d_B);
   else
-    k_interpolate<Q, T, true><<<wb, 256, 0, c->stream>>>(m, c->d_base, c->d_wts, src, p, g, c->d_U, c->d_rho_l, c->d_B);
+    k_interpolate<Q, T, true><<<wb, 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts), src, p, g, c->d_U,
+                                                               c->d_rho_l, c->d_B);
   c->launches++;
   return cudaGetLastError();
 }
@@ -1485,7 +1500,8 @@ cudaError_t ib_step_front(ibl_ctx* c) {
   const int tb = 64;
   const int mb = (m + tb - 1) / tb;
   k_kinematics<<<mb, tb, 0, c->stream>>>(bt, m, c->d_body, c->d_X0, c->d_Xp, c->d_Up, c->d_X, c->d_U,
-                                         c->d_base, c->d_wts, (double)c->step, g, c->d_status);
+                                         c->d_base, reinterpret_cast<df*>(c->d_wts), (double)c->step, g,
+                                         c->d_status);
   k_clear_tiles<<<std::max(1, std::min(c->cap_slots / 256 + 1, g_num_sms)), 256, 0, c->stream>>>(
       c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->d_tile_mcount, c->d_slot_body, c->cap_slots);
   // candidate-list assembly unless a body is driven by uploaded states this step
@@ -1516,7 +1532,7 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   IBL_CU(cudaGetLastError());
   IBL_CU(interpolate(c, g));
   IBL_CU(cudaMemsetAsync(c->d_Gdiag_max, 0, sizeof(double) * MAX_BODIES, c->stream));
-  k_assemble<<<(m + 7) / 8, 256, 0, c->stream>>>(m, c->d_base, c->d_wts, c->d_tile_slot,
+  k_assemble<<<(m + 7) / 8, 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts), c->d_tile_slot,
                                                  c->d_tile_mcount, c->d_tile_markers, g, c->d_body, c->d_Gcol,
                                                  reinterpret_cast<df*>(c->d_Gval), c->d_Gnnz,
                                                  (unsigned long long*)c->d_Gdiag_max,
@@ -1604,7 +1620,8 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   {
     const int nn = c->D == 3 ? 64 : 16;
     const long long tot = (long long)m * nn;
-    k_spread_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(m, c->d_base, c->d_wts, c->d_w,
+    k_spread_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts),
+                                                                            reinterpret_cast<const df*>(c->d_p) + 3 * (size_t)m,
                                                                             c->d_tile_slot, g, c->d_acc, c->d_status);
     c->launches++;
   }

@@ -3,6 +3,7 @@
 // moments (Eq. 11) of one node's post-streaming populations.
 #pragma once
 
+#include "df.cuh"
 #include "lbm_gather.cuh"
 
 namespace ibl {
@@ -34,12 +35,13 @@ __device__ __forceinline__ bool stencil_axis(double x, int n, bool per, int& bas
   return finite && fl - 1.0 >= 0.0 && fl + 2.0 < (double)n;
 }
 
-// rho and u* of one node from its post-streaming deviations (Eq. 11 with
-// the uniform body force G: u* = (m + G/2) / rho, formed as m - m drho / rho).
+// drho and u* of one node from its post-streaming deviations, in the
+// storage's compute precision (Eq. 11 with the uniform body force G:
+// u* = (m + G/2) / rho, formed as m - m drho / rho).
 template <int Q, class T, bool PULL>
-__device__ __forceinline__ void node_rho_u(const T* __restrict__ src, int x, int y, int z, long long cell,
-                                           const FluidParams<typename Store<T>::R>& p, double& rho,
-                                           double u[3]) {
+__device__ __forceinline__ void node_moments(const T* __restrict__ src, int x, int y, int z, long long cell,
+                                             const FluidParams<typename Store<T>::R>& p,
+                                             typename Store<T>::R& drho_out, typename Store<T>::R u[3]) {
   using R = typename Store<T>::R;
   R gg[Q];
   gather_q<Q, T, PULL, R>(src, x, y, z, cell, p, gg);
@@ -57,10 +59,27 @@ __device__ __forceinline__ void node_rho_u(const T* __restrict__ src, int x, int
   u0 -= u0 * qd;
   u1 -= u1 * qd;
   u2 -= u2 * qd;
-  rho = 1.0 + (double)drho;
-  u[0] = (double)u0;
-  u[1] = (double)u1;
-  u[2] = (double)u2;
+  drho_out = drho;
+  u[0] = u0;
+  u[1] = u1;
+  u[2] = u2;
 }
+
+// The same moments as FP64 rho and u*.
+template <int Q, class T, bool PULL>
+__device__ __forceinline__ void node_rho_u(const T* __restrict__ src, int x, int y, int z, long long cell,
+                                           const FluidParams<typename Store<T>::R>& p, double& rho,
+                                           double u[3]) {
+  typename Store<T>::R drho, uu[3];
+  node_moments<Q, T, PULL>(src, x, y, z, cell, p, drho, uu);
+  rho = 1.0 + (double)drho;
+  u[0] = (double)uu[0];
+  u[1] = (double)uu[1];
+  u[2] = (double)uu[2];
+}
+
+// A storage-precision value as a double-float (exact).
+__device__ __forceinline__ df to_df(float v) { return df_from_float(v); }
+__device__ __forceinline__ df to_df(double v) { return df_from_double(v); }
 
 }  // namespace ibl

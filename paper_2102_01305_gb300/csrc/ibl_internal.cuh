@@ -112,7 +112,7 @@ struct ibl_ctx {
   int* d_tile_markers = nullptr; // cap_slots x TILE_MARKER_CAP
   void* d_band_F = nullptr;      // cap_slots x 3 x TILE_CELLS (real)
   int* d_base = nullptr;         // m x 3 stencil base nodes (unwrapped)
-  double* d_wts = nullptr;       // m x 3 x 4 delta weights per axis (FP64)
+  double* d_wts = nullptr;       // m x 3 x 4 delta weights per axis (double-float pairs, 8 B each)
   double* d_rho_l = nullptr;     // m interpolated density
   double* d_B = nullptr;         // m x 3 right-hand side
   double* d_w = nullptr;         // m x 3 solution (du_B * ds)
