@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--overlap", type=int, default=-1, choices=[-1, 0, 1],
                     help="collide scheduling: -1 automatic, 0 one kernel after the IB chain, 1 split")
     ap.add_argument("--solver-blocks", type=int, default=0, help="blocks of the implicit solve (0: default)")
+    ap.add_argument("--refresh-every", type=int, default=0,
+                    help="steps between preconditioner rebuilds (0: the library default)")
     ap.add_argument("--ib-sweep", action="store_true",
                     help="IB-stage throughput: interpolate + spread of random point clouds (no solve)")
     ap.add_argument("--ib-markers", default="1000,10000,100000,1000000")
@@ -225,6 +227,9 @@ def pcg_trace_summary(tr, iters):
     med = lambda v: round(statistics.median(v), 3) if v else None
     out = {"total_us": (tr[3] - tr[0]) / 1e3, "rebuild_us": (tr[1] - tr[0]) / 1e3,
            "setup_us": (tr[2] - tr[1]) / 1e3}
+    if tr[4] and tr[7] and tr[1] - tr[0] > 1000:
+        out["rebuild_first_pivot_us"] = [round((tr[j] - tr[j - 1]) / 1e3, 3) for j in range(5, 8)]
+        out["rebuild_first_pivot_us"].insert(0, round((tr[4] - tr[0]) / 1e3, 3))
     prev_end = [tr[2]] + [tr[b + 8] for b in base[:-1]]
     out["scalars_us"] = med([(tr[b] - e) / 1e3 for b, e in zip(base, prev_end)])
     for j, name in enumerate(PCG_PHASES):
@@ -286,6 +291,8 @@ def run_ours(args):
     ctx = ibl.from_workload(cfg)
     ctx.ibl_set_overlap(args.overlap)
     ctx.ibl_solver_blocks(args.solver_blocks)
+    if args.refresh_every:
+        ctx.ibl_solver_config(args.refresh_every, 0.0, 1)
     ctx.ibl_step(args.warmup)
     ctx.ibl_sync(allow=(ibl.IBL_ENOTCONV,))
     stream = torch.cuda.ExternalStream(ctx.ibl_stream())

@@ -253,7 +253,7 @@ ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_resid
 
 /* Settings of the implicit IB solve (preconditioned conjugate gradients on
  * the system of Eqs. 18-19): the dense FP32 approximate inverse used as
- * preconditioner is rebuilt every refresh_every steps (default 128) and
+ * preconditioner is rebuilt every refresh_every steps (default 256) and
  * early when a solve needed more than 40 iterations; tol is the relative
  * residual in the preconditioner's norm (0 = default: 1e-10 for FP64
  * storage, 1e-7 for FP32, 1e-6 for FP16/BF16); extrapolate != 0 starts each solve from
@@ -277,7 +277,9 @@ ibl_status ibl_set_overlap(ibl_ctx* ctx, int32_t mode);
 
 /* Phase timestamps (GPU global timer, ns, taken by block 0) of the last
  * implicit solve: [0] start, [1] after the optional preconditioner rebuild,
- * [2] after set-up, [3] end; iteration k (k < 27) at 8 + 9k: recurrence
+ * [2] after set-up, [3] end; [4]-[7] the four phases of the rebuild's first
+ * pivot block (pivot inverse, row panel, trailing update, column panel);
+ * iteration k (k < 27) at 8 + 9k: recurrence
  * scalars ready, search direction input staged, SpMV rows done, block
  * reduction done, grid barrier passed, step length ready, preconditioner
  * input staged, preconditioner rows done, grid barrier passed.  Unused

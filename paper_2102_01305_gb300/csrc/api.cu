@@ -147,10 +147,6 @@ ibl_status ibl_destroy(ibl_ctx* c) {
   if (c->ev_tiles) cudaEventDestroy(c->ev_tiles);
   if (c->ev_bulk) cudaEventDestroy(c->ev_bulk);
   ib_free(c);
-  for (auto& b : c->bodies) {
-    if (b.tableA) cudaFree(b.tableA);
-    if (b.tableAlpha) cudaFree(b.tableAlpha);
-  }
   if (c->f[0]) cudaFree(c->f[0]);
   if (c->f[1]) cudaFree(c->f[1]);
   if (c->d_status) cudaFree(c->d_status);
@@ -245,12 +241,11 @@ ibl_status ibl_set_markers(ibl_ctx* c, int32_t m, const double* X0, const double
   return IBL_OK;
 }
 
-static ibl_status copy_wave(ibl_ctx* c, const ibl_wave* w, Wave& out, double*& dev) {
+static ibl_status copy_wave(ibl_ctx* c, const ibl_wave* w, Wave& out, std::vector<double>& table) {
   out.kind = IBL_WAVE_CONST;
   out.amp = 0;
   out.offset = 0;
-  out.table = nullptr;
-  out.n_table = 0;
+  table.clear();
   if (!w) return IBL_OK;
   if (w->kind < IBL_WAVE_CONST || w->kind > IBL_WAVE_TABLE) return fail(c, IBL_EINVAL, "unknown wave kind");
   out.kind = w->kind;
@@ -258,12 +253,7 @@ static ibl_status copy_wave(ibl_ctx* c, const ibl_wave* w, Wave& out, double*& d
   out.offset = w->offset;
   if (w->kind == IBL_WAVE_TABLE) {
     if (!w->table || w->n_table <= 0) return fail(c, IBL_EINVAL, "table wave needs samples");
-    if (dev) cudaFree(dev);
-    dev = nullptr;
-    CK(cudaMalloc(&dev, sizeof(double) * w->n_table), "wave table alloc");
-    CK(cudaMemcpy(dev, w->table, sizeof(double) * w->n_table, cudaMemcpyHostToDevice), "wave table copy");
-    out.table = dev;
-    out.n_table = w->n_table;
+    table.assign(w->table, w->table + w->n_table);
   }
   return IBL_OK;
 }
@@ -275,11 +265,9 @@ ibl_status ibl_set_kinematics(ibl_ctx* c, int32_t body_id, const ibl_wave* A, co
   if (!std::isfinite(beta) || !std::isfinite(phi) || !std::isfinite(f) || !std::isfinite(J))
     return fail(c, IBL_EINVAL, "kinematic parameters must be finite");
   Body& b = c->bodies[body_id];
-  // tables are replaced only after the stream drained, they may be in use
-  CK(cudaStreamSynchronize(c->stream), "sync");
-  ibl_status s = copy_wave(c, A, b.A, b.tableA);
+  ibl_status s = copy_wave(c, A, b.A, b.hostA);
   if (s != IBL_OK) return s;
-  s = copy_wave(c, alpha, b.alpha, b.tableAlpha);
+  s = copy_wave(c, alpha, b.alpha, b.hostAlpha);
   if (s != IBL_OK) return s;
   b.beta = beta;
   b.phi = phi;

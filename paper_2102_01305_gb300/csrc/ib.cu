@@ -22,6 +22,8 @@
 //   (end of k_pcg)   F_w = -sum_l 2 rho_l w_l per body in FP64, fixed order.
 #include <cooperative_groups.h>
 
+#include <cmath>
+
 #include "df.cuh"
 #include "ib_stencil.cuh"
 
@@ -59,56 +61,11 @@ __device__ __forceinline__ int wrap(int v, int n) {
   return v;
 }
 
-__device__ void wave_eval(const Wave& w, double t, double f, double phi, double& v, double& vd) {
-  const double om = 2.0 * 3.14159265358979323846 * f;
-  const double th = om * t + phi;
-  switch (w.kind) {
-    case IBL_WAVE_COS: v = w.offset + w.amp * cos(th); vd = -w.amp * om * sin(th); break;
-    case IBL_WAVE_SIN: v = w.offset + w.amp * sin(th); vd = w.amp * om * cos(th); break;
-    case IBL_WAVE_ABS_SIN: {
-      const double s = sin(th);
-      const double sg = s >= 0.0 ? 1.0 : -1.0;
-      v = w.offset + w.amp * fabs(s);
-      vd = w.amp * om * cos(th) * sg;
-      break;
-    }
-    case IBL_WAVE_TABLE: {
-      const long long n = w.n_table;
-      long long k = llround(t);
-      const long long i0 = ((k % n) + n) % n, ip = (((k + 1) % n) + n) % n, im = (((k - 1) % n) + n) % n;
-      v = w.table[i0];
-      vd = 0.5 * (w.table[ip] - w.table[im]);
-      break;
-    }
-    default: v = w.offset; vd = 0.0; break;
-  }
-}
-
-// ------------------------------------------------------------------ kinematics + stencil
-// Wave values and rates (Eqs. 20-23) and the rotation's cosine and sine at
-// time t for body b, shared by all of the body's markers.
-__device__ void body_state(const BodyDev& B, double t, double st[8]) {
-  double A, Ad, al, ald;
-  wave_eval(B.A, t, B.f, B.phi, A, Ad);
-  wave_eval(B.alpha, t, B.f, B.phi, al, ald);
-  st[0] = A;
-  st[1] = Ad;
-  st[2] = ald;
-  st[3] = cos(al);
-  st[4] = sin(al);
-  st[5] = cos(B.beta);
-  st[6] = sin(B.beta);
-  st[7] = al;
-}
-
 __global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ body_of,
                              const double* __restrict__ X0, const double* __restrict__ Xp,
                              const double* __restrict__ Up, double* __restrict__ X,
                              double* __restrict__ U, int* __restrict__ base,
                              df* __restrict__ wts, double t, Geo geo, int* status) {
-  __shared__ double sst[MAX_BODIES][8];
-  if (threadIdx.x < bt.n) body_state(bt.b[threadIdx.x], t, sst[threadIdx.x]);
-  __syncthreads();
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= m_total) return;
   const BodyDev& B = bt.b[body_of[l]];
@@ -116,8 +73,8 @@ __global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ 
   if (B.prescribed) {
     for (int a = 0; a < 3; ++a) { x[a] = Xp[3 * l + a]; u[a] = Up[3 * l + a]; }
   } else {
-    // per-body motion state of this step: A, A', alpha', cos, sin, e_s
-    const double* st = sst[body_of[l]];
+    // per-body motion state of this step (formed on the host): A, A', alpha', cos, sin, e_s
+    const double* st = B.st;
     const double A = st[0], Ad = st[1], ald = st[2], c = st[3], s = st[4];
     const double es[3] = {st[5], st[6], 0.0};
     const double* e = B.axis;
@@ -219,24 +176,26 @@ __global__ void k_assign_slots(int n_tiles, int* __restrict__ tile_slot, int* __
   }
 }
 
+// One thread per (marker, touched tile): the appends of a marker are
+// independent, so none waits on another's atomics.
 __global__ void k_append_markers(int m_total, const int* __restrict__ base, Geo g,
                                  const int* __restrict__ tile_slot, int* __restrict__ tile_mcount,
                                  int* __restrict__ tile_markers, int* status, const int* __restrict__ body_of,
                                  int* __restrict__ slot_body, int* __restrict__ mixed) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = gid >> 3, i = gid & 7;
   if (l >= m_total) return;
   int t[8];
   const int n = touched_tiles(g, base + 3 * l, t);
+  if (i >= n) return;
+  const int s = tile_slot[t[i]];
+  if (s < 0) return;
   const int bl = body_of[l];
-  for (int i = 0; i < n; ++i) {
-    const int s = tile_slot[t[i]];
-    if (s < 0) continue;
-    const int prev = atomicCAS(&slot_body[s], -1, bl);
-    if (prev != -1 && prev != bl) *mixed = 1;   // two bodies' stencils share a tile
-    const int pos = atomicAdd(&tile_mcount[s], 1);
-    if (pos < TILE_MARKER_CAP) tile_markers[s * TILE_MARKER_CAP + pos] = l;
-    else atomicOr(status, ST_OVERFLOW);
-  }
+  const int prev = atomicCAS(&slot_body[s], -1, bl);
+  if (prev != -1 && prev != bl) *mixed = 1;   // two bodies' stencils share a tile
+  const int pos = atomicAdd(&tile_mcount[s], 1);
+  if (pos < TILE_MARKER_CAP) tile_markers[s * TILE_MARKER_CAP + pos] = l;
+  else atomicOr(status, ST_OVERFLOW);
 }
 
 // rho_l and u*_l (Eq. 17) gathered straight from the populations of each
@@ -806,11 +765,23 @@ __device__ void tile_gemm(float* out, int ldo, const float* Ag, int lda, const f
     for (int u = 0; u < 4; ++u) {
       const int r = 4 * ty + u, i = i0 + r;
       if (r >= nr || (i >= sk0 && i < sk1)) continue;
+      const int c0 = 4 * tx, jj = j0 + c0;
+      float* o = out + (long long)i * ldo + jj;
+      // four whole columns outside the skipped range: one 128-bit access
+      // (ldo and the tile origins are multiples of 4 floats)
+      if (c0 + 3 < nc && (jj + 3 < ck0 || jj >= ck1)) {
+        float4 ov = acc ? *reinterpret_cast<float4*>(o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        ov.x += alpha * a4[u][0];
+        ov.y += alpha * a4[u][1];
+        ov.z += alpha * a4[u][2];
+        ov.w += alpha * a4[u][3];
+        *reinterpret_cast<float4*>(o) = ov;
+        continue;
+      }
       for (int v = 0; v < 4; ++v) {
-        const int c = 4 * tx + v, j = j0 + c;
+        const int c = c0 + v, j = jj + v;
         if (c >= nc || (j >= ck0 && j < ck1)) continue;
-        float* o = out + (long long)i * ldo + j;
-        *o = (acc ? *o : 0.f) + alpha * a4[u][v];
+        o[v] = (acc ? o[v] : 0.f) + alpha * a4[u][v];
       }
     }
   }
@@ -859,6 +830,7 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
         Mb[(long long)(k0 + e / kn) * ld + k0 + e % kn] = piv[e];
     }
     grid.sync();
+    if (kb == 0) trace_mark(A, 4);
     // phase 2: row panel R <- P^-1 R (tiles of GJ_NB rows x GT columns)
     {
       int done = 0;
@@ -877,6 +849,7 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
       }
     }
     grid.sync();
+    if (kb == 0) trace_mark(A, 5);
     // phase 3a: S <- S - C R (rows and columns outside the pivot block)
     {
       int done = 0;
@@ -895,6 +868,7 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
       }
     }
     grid.sync();
+    if (kb == 0) trace_mark(A, 6);
     // phase 3b: C <- -C P^-1 (rows outside, columns inside the pivot block)
     {
       int done = 0;
@@ -913,6 +887,7 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
       }
     }
     grid.sync();
+    if (kb == 0) trace_mark(A, 7);
   }
 }
 
@@ -1092,6 +1067,11 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
       const int sub = lane >> 3, sl = lane & 7;
       for (int l0 = row0 * 4; l0 < m; l0 += rstep * 4) {
         const int l = l0 + sub;
+        // this lane's epilogue operands, fetched before the row product
+        const int ce = sl < 3 ? sl : 0;
+        const int le = l < m ? l : 0;
+        const float z0 = A.zf[3 * le + ce];
+        const df p0 = A.pd[3 * le + ce], ap0 = A.Apd[3 * le + ce], r0 = A.rd[3 * le + ce];
         dfacc a0 = acc_zero(), a1 = acc_zero(), a2 = acc_zero();
         if (l < m) {
           const int nnz = A.Gnnz[l];
@@ -1115,12 +1095,12 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
           const int vi = A.voff[bd] + 3 * (l - A.boff[bd]) + c;
           const df gz = c == 0 ? gz0 : (c == 1 ? gz1 : gz2);
           const df beta = s_beta[c];
-          const df pl = df_add(df_from_float(A.zf[3 * l + c]), df_mul(beta, A.pd[3 * l + c]));
-          const df ap = df_add(gz, df_mul(beta, A.Apd[3 * l + c]));
+          const df pl = df_add(df_from_float(z0), df_mul(beta, p0));
+          const df ap = df_add(gz, df_mul(beta, ap0));
           A.pd[3 * l + c] = pl;
           A.Apd[3 * l + c] = ap;
           A.Apf[vi] = ap.hi;
-          A.rf[vi] = A.rd[3 * l + c].hi;
+          A.rf[vi] = r0.hi;
           contrib = df_mul(pl, ap);
         }
         // lane c < 3 gathers component c of the warp's four rows, in row order
@@ -1155,13 +1135,16 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
       const float* xs = stage_x(A, A.rf, A.Apf, alphaf, sm);
       trace_mark(A, ts + 6);
       for (int l = row0; l < m; l += rstep) {
+        // the row's vector entries are fetched before the product so that
+        // their latency overlaps it
+        const int c = lane < 3 ? lane : 0;
+        const df w0 = A.wd[3 * l + c], p0 = A.pd[3 * l + c], r0 = A.rd[3 * l + c], ap0 = A.Apd[3 * l + c];
         float zl[3];
         precond_row(A, l, xs, A.rf, A.Apf, alphaf, zl, lane, mres);
         if (lane < 3) {
-          const int c = lane;
           const df alpha = s_alpha[c];
-          A.wd[3 * l + c] = df_add(A.wd[3 * l + c], df_mul(alpha, A.pd[3 * l + c]));
-          const df rn = df_sub(A.rd[3 * l + c], df_mul(alpha, A.Apd[3 * l + c]));
+          A.wd[3 * l + c] = df_add(w0, df_mul(alpha, p0));
+          const df rn = df_sub(r0, df_mul(alpha, ap0));
           A.rd[3 * l + c] = rn;
           A.zf[3 * l + c] = zl[c];
           rz = df_add(rz, df_mul_f(rn, zl[c]));
@@ -1471,6 +1454,52 @@ int pcg_block_count(const ibl_ctx* c) {
   return std::max(1, std::min(std::min(std::min(want, num_sms()), MAX_PCG_BLOCKS), c->m_total));
 }
 
+// Wave value and rate at time t (Eqs. 20-23 and the reading of Eq. 23 as
+// |sin|; TABLE: samples per step, central difference for the rate), in
+// FP64 on the host: a handful of values per body and step, kept off the
+// GPU's slow FP64 pipe.
+static void wave_eval(const Wave& w, const std::vector<double>& table, double t, double f, double phi,
+                      double& v, double& vd) {
+  const double om = 2.0 * 3.14159265358979323846 * f;
+  const double th = om * t + phi;
+  switch (w.kind) {
+    case IBL_WAVE_COS: v = w.offset + w.amp * std::cos(th); vd = -w.amp * om * std::sin(th); break;
+    case IBL_WAVE_SIN: v = w.offset + w.amp * std::sin(th); vd = w.amp * om * std::cos(th); break;
+    case IBL_WAVE_ABS_SIN: {
+      const double sn = std::sin(th);
+      const double sg = sn >= 0.0 ? 1.0 : -1.0;
+      v = w.offset + w.amp * std::fabs(sn);
+      vd = w.amp * om * std::cos(th) * sg;
+      break;
+    }
+    case IBL_WAVE_TABLE: {
+      const long long n = (long long)table.size();
+      const long long k = std::llround(t);
+      const long long i0 = ((k % n) + n) % n, ip = (((k + 1) % n) + n) % n, im = (((k - 1) % n) + n) % n;
+      v = table[i0];
+      vd = 0.5 * (table[ip] - table[im]);
+      break;
+    }
+    default: v = w.offset; vd = 0.0; break;
+  }
+}
+
+// Motion state of body b at time t shared by all of its markers: A, A',
+// alpha', cos alpha, sin alpha, the stroke direction e_s (cos beta, sin beta), alpha.
+static void body_state(const Body& B, double t, double st[8]) {
+  double A, Ad, al, ald;
+  wave_eval(B.A, B.hostA, t, B.f, B.phi, A, Ad);
+  wave_eval(B.alpha, B.hostAlpha, t, B.f, B.phi, al, ald);
+  st[0] = A;
+  st[1] = Ad;
+  st[2] = ald;
+  st[3] = std::cos(al);
+  st[4] = std::sin(al);
+  st[5] = std::cos(B.beta);
+  st[6] = std::sin(B.beta);
+  st[7] = al;
+}
+
 // Kinematics and the band tiles of the step (the bulk collide may start
 // once these are enqueued).
 cudaError_t ib_step_front(ibl_ctx* c) {
@@ -1492,9 +1521,7 @@ cudaError_t ib_step_front(ibl_ctx* c) {
     BodyDev& d = bt.b[b];
     d.offset = h.offset; d.m = h.m;
     for (int a = 0; a < 3; ++a) { d.hinge[a] = h.hinge[a]; d.axis[a] = h.axis[a]; d.origin[a] = h.origin[a]; }
-    d.beta = h.beta; d.phi = h.phi; d.f = h.f;
-    d.A = h.A; d.alpha = h.alpha;
-    d.A.table = h.tableA; d.alpha.table = h.tableAlpha;
+    body_state(h, (double)c->step, d.st);
     d.prescribed = h.prescribed ? 1 : 0;
   }
   const int tb = 64;
@@ -1524,7 +1551,7 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   Geo g = make_geo(c);
   const int tb = 64;
   const int mb = (m + tb - 1) / tb;
-  k_append_markers<<<mb, tb, 0, c->stream>>>(m, c->d_base, g, c->d_tile_slot, c->d_tile_mcount,
+  k_append_markers<<<(8 * m + 255) / 256, 256, 0, c->stream>>>(m, c->d_base, g, c->d_tile_slot, c->d_tile_mcount,
                                              c->d_tile_markers, c->d_status, c->d_body, c->d_slot_body,
                                              c->d_mixed);
   for (auto& b : c->bodies) b.prescribed = false;

@@ -36,15 +36,12 @@ namespace ibl {
 struct Wave {
   int kind;
   double amp, offset;
-  const double* table;   // device copy (TABLE only)
-  long long n_table;
 };
 
 struct BodyDev {
   int offset, m;
   double hinge[3], axis[3], origin[3];
-  double beta, phi, f;
-  Wave A, alpha;
+  double st[8];          // motion state of the step (A, A', alpha', cos, sin, e_s, alpha)
   int prescribed;        // 1: use the uploaded X/U for this step
 };
 
@@ -52,9 +49,8 @@ struct Body {
   int offset = 0, m = 0;
   double hinge[3] = {0, 0, 0}, axis[3] = {0, 0, 1}, origin[3] = {0, 0, 0};
   double beta = 0, phi = 0, f = 0, J = 0;
-  Wave A{0, 0, 0, nullptr, 0}, alpha{0, 0, 0, nullptr, 0};
-  double* tableA = nullptr;
-  double* tableAlpha = nullptr;
+  Wave A{0, 0, 0}, alpha{0, 0, 0};
+  std::vector<double> hostA, hostAlpha;   // TABLE samples
   double lift[3] = {0, 1, 0};
   bool prescribed = false;
   int precond_offset = 0;   // offset of this body's dense preconditioner (floats)
@@ -147,7 +143,7 @@ struct ibl_ctx {
   bool warm = false;             // d_w holds the previous solution
   long long warm_steps = 0;      // consecutive solves behind d_w (2+: extrapolate)
   bool extrapolate = true;
-  int refresh_every = 128;       // steps between scheduled preconditioner rebuilds
+  int refresh_every = 256;       // steps between scheduled preconditioner rebuilds
   double solver_tol = 0.0;       // 0: default for the storage precision
   int pcg_blocks = 0;            // blocks of the cooperative solve (0: half the SMs)
   size_t pcg_smem = 0;           // dynamic shared memory of the last solve launch
