@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--overlap", type=int, default=-1, choices=[-1, 0, 1],
                     help="collide scheduling: -1 automatic, 0 one kernel after the IB chain, 1 split")
     ap.add_argument("--solver-blocks", type=int, default=0, help="blocks of the implicit solve (0: default)")
+    ap.add_argument("--phases", action="store_true", help="also time every phase of the step (events)")
     ap.add_argument("--refresh-every", type=int, default=0,
                     help="steps between preconditioner rebuilds (0: the library default)")
     ap.add_argument("--ib-sweep", action="store_true",
@@ -227,7 +228,7 @@ def pcg_trace_summary(tr, iters):
     med = lambda v: round(statistics.median(v), 3) if v else None
     out = {"total_us": (tr[3] - tr[0]) / 1e3, "rebuild_us": (tr[1] - tr[0]) / 1e3,
            "setup_us": (tr[2] - tr[1]) / 1e3}
-    if tr[4] and tr[7] and tr[1] - tr[0] > 1000:
+    if tr[4] and tr[7] and tr[1] - tr[0] > 100000 and tr[4] > tr[0]:
         out["rebuild_first_pivot_us"] = [round((tr[j] - tr[j - 1]) / 1e3, 3) for j in range(5, 8)]
         out["rebuild_first_pivot_us"].insert(0, round((tr[4] - tr[0]) / 1e3, 3))
     prev_end = [tr[2]] + [tr[b + 8] for b in base[:-1]]
@@ -298,7 +299,7 @@ def run_ours(args):
     stream = torch.cuda.ExternalStream(ctx.ibl_stream())
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    ctx.ibl_profile(True)
+    ctx.ibl_profile(2 if args.phases else 1)
     l0 = ctx.ibl_launch_count()
     clocks = ClockSampler()
     clocks.start()
@@ -322,6 +323,8 @@ def run_ours(args):
     except ibl.IblError as e:
         status = str(e)
     collide_ms, ib_ms, nprof = ctx.ibl_profile_read()
+    phases = ({k: round(v / max(nprof, 1), 5) for k, v in ctx.ibl_profile_phases().items()}
+              if args.phases else None)
     iters, res, refreshes = ctx.ibl_solver_stats(allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
     trace = None
     if cfg["bodies"]:
@@ -395,6 +398,8 @@ def run_ours(args):
                 "solver": {"pcg_iterations_last_step": iters, "rel_residual_last_step": res,
                            "preconditioner_rebuilds": refreshes, "trace_last_step": trace},
                 "C_L_last_step_body0": cl[0] if cl else None}
+        if phases:
+            line["phase_ms_per_step"] = phases
         print(json.dumps(line), flush=True)
     if WORLD > 1:
         dist.destroy_process_group()

@@ -286,13 +286,22 @@ ibl_status ibl_set_overlap(ibl_ctx* ctx, int32_t mode);
  * slots are 0.  Copies min(max, 256) values into ns. */
 ibl_status ibl_solver_trace(ibl_ctx* ctx, int64_t* ns, int32_t max, int32_t* n);
 
-/* Enable (1) or disable (0) CUDA-event timing of the collide-stream
+/* Enable (1 or 2) or disable (0) CUDA-event timing of the collide-stream
  * kernel(s) and of the IB chain (kinematics .. spreading and the force
  * reduction) of every step enqueued while enabled.  In a split step (see
  * ibl_set_overlap) the bulk collide is timed on its own stream, concurrently
  * with the IB chain.  Enabling resets the totals.  Adds events only; the
  * launch sequence is unchanged. */
 ibl_status ibl_profile(ibl_ctx* ctx, int32_t enable);
+
+/* With ibl_profile(ctx, 2): milliseconds per phase of the step on the
+ * context's main stream since profiling was enabled, ms[0..n): 0 kinematics,
+ * 1 band tile reset, 2 tile marking, 3 slot assignment, 4 marker lists,
+ * 5 interpolation, 6 system assembly, 7 implicit solve, 8 spreading,
+ * 9 collision (the band tiles' kernel in a split step; the bulk collide on
+ * the second stream is in ibl_profile_read).  Each phase is the time from
+ * the end of the previous one, so launch gaps are included.  Synchronises. */
+ibl_status ibl_profile_phases(ibl_ctx* ctx, double* ms, int32_t n);
 
 /* Totals since the last ibl_profile(ctx, 1): milliseconds in the
  * collide-stream kernel(s), milliseconds in the IB chain, steps timed.

@@ -153,6 +153,7 @@ ibl_status ibl_destroy(ibl_ctx* c) {
   for (auto& ev : c->stage_ev)
     if (ev) cudaEventDestroy(ev);
   for (auto& ev : c->prof_ev) cudaEventDestroy(ev);
+  for (auto& ev : c->pev_pool) cudaEventDestroy(ev);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -373,6 +374,7 @@ ibl_status ibl_step(ibl_ctx* c, int64_t n) {
       c->prof_steps++;
     }
     if (ev[0]) CK(cudaEventRecord(ev[0], c->stream), "event");
+    phase_mark(c, -1);
     if (split) {
       CK(ib_step_front(c), "IB step");
       CK(cudaEventRecord(c->ev_tiles, c->stream), "event");
@@ -384,12 +386,14 @@ ibl_status ibl_step(ibl_ctx* c, int64_t n) {
       CK(ib_step_back(c), "IB step");
       if (ev[1]) CK(cudaEventRecord(ev[1], c->stream), "event");
       CK(launch_collide_band(c, std::max(1, std::min(c->cap_slots, 4 * num_sms()))), "band collide");
+      phase_mark(c, 9);
       if (ev[2]) CK(cudaEventRecord(ev[2], c->stream), "event");
       CK(cudaStreamWaitEvent(c->stream, c->ev_bulk, 0), "stream wait");
     } else {
       if (with_ib) CK(ib_step(c), "IB step");
       if (ev[1]) CK(cudaEventRecord(ev[1], c->stream), "event");
       CK(launch_collide(c, with_ib), "collide");
+      phase_mark(c, 9);
       if (ev[2]) CK(cudaEventRecord(ev[2], c->stream), "event");
     }
     if (ev[3]) CK(cudaEventRecord(ev[3], c->stream), "event");
@@ -591,8 +595,11 @@ ibl_status ibl_profile(ibl_ctx* c, int32_t enable) {
   if (!c) return IBL_EINVAL;
   CK(cudaStreamSynchronize(c->stream), "sync");
   c->profiling = enable != 0;
+  c->prof_level = enable;
   c->prof_steps = 0;
   c->prof_split.clear();
+  c->pev_used = 0;
+  c->pev_log.clear();
   return IBL_OK;
 }
 
@@ -619,6 +626,22 @@ ibl_status ibl_profile_read(ibl_ctx* c, double* collide_ms, double* ib_ms, int64
   if (collide_ms) *collide_ms = tc;
   if (ib_ms) *ib_ms = ti;
   if (steps) *steps = c->prof_steps;
+  return IBL_OK;
+}
+
+ibl_status ibl_profile_phases(ibl_ctx* c, double* ms, int32_t n) {
+  if (!c || n < 0 || (n > 0 && !ms)) return IBL_EINVAL;
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  for (int i = 0; i < n; ++i) ms[i] = 0.0;
+  cudaEvent_t prev = nullptr;
+  for (auto& pe : c->pev_log) {
+    if (pe.first >= 0 && prev && pe.first < n) {
+      float t = 0;
+      CK(cudaEventElapsedTime(&t, prev, pe.second), "elapsed");
+      ms[pe.first] += t;
+    }
+    prev = pe.second;
+  }
   return IBL_OK;
 }
 

@@ -1274,6 +1274,35 @@ static size_t real_size(ibl_ctx* c) { return c->prec == IBL_FP64 ? sizeof(double
     if (e_ != cudaSuccess) return e_;   \
   } while (0)
 
+// The dense preconditioner is re-read by every iteration of every solve;
+// while the bulk collide streams the populations through L2 on the other
+// SMs it would be evicted each time.  Mark it persisting in L2 for the
+// context's stream (the set-aside is a property of this process's context
+// and ends with it).  Best effort: without support the solve only runs slower.
+static void keep_in_l2(ibl_ctx* c, const void* ptr, size_t bytes) {
+  int dev = 0, max_persist = 0, max_window = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+  cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+  if (max_persist <= 0 || max_window <= 0) return;
+  size_t cur = 0;
+  cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
+  const size_t want = std::min<size_t>(bytes, (size_t)max_persist);
+  if (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaStreamAttrValue attr = {};
+  attr.accessPolicyWindow.base_ptr = const_cast<void*>(ptr);
+  attr.accessPolicyWindow.num_bytes = std::min<size_t>(bytes, (size_t)max_window);
+  attr.accessPolicyWindow.hitRatio =
+      (float)std::min(1.0, (double)want / (double)attr.accessPolicyWindow.num_bytes);
+  attr.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+  attr.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+  if (cudaStreamSetAttribute(c->stream, cudaStreamAttributeAccessPolicyWindow, &attr) != cudaSuccess)
+    cudaGetLastError();
+}
+
 cudaError_t ib_alloc(ibl_ctx* c) {
   ib_free(c);
   const int m = c->m_total;
@@ -1336,6 +1365,7 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   }
   c->M_floats = mf;
   IBL_CU(cudaMalloc(&c->d_M, sizeof(float) * mf));
+  keep_in_l2(c, c->d_M, sizeof(float) * mf);
   IBL_CU(cudaMalloc(&c->d_red, sizeof(double) * 8 * 1024));
   IBL_CU(cudaMalloc(&c->d_cg_info, sizeof(int) * 4));
   IBL_CU(cudaMemsetAsync(c->d_cg_info, 0, sizeof(int) * 4, c->stream));
@@ -1446,6 +1476,18 @@ int num_sms() {
   return g_num_sms;
 }
 
+void phase_mark(ibl_ctx* c, int phase) {
+  if (c->prof_level < 2) return;
+  if (c->pev_used == c->pev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c->pev_pool.push_back(e);
+  }
+  cudaEvent_t e = c->pev_pool[c->pev_used++];
+  cudaEventRecord(e, c->stream);
+  c->pev_log.emplace_back(phase, e);
+}
+
 // Blocks of the cooperative solve: by default half the SMs (the other half
 // runs the bulk collide concurrently when the step is split), fixed per
 // context so that the solve's reduction order does not depend on the split.
@@ -1529,6 +1571,7 @@ cudaError_t ib_step_front(ibl_ctx* c) {
   k_kinematics<<<mb, tb, 0, c->stream>>>(bt, m, c->d_body, c->d_X0, c->d_Xp, c->d_Up, c->d_X, c->d_U,
                                          c->d_base, reinterpret_cast<df*>(c->d_wts), (double)c->step, g,
                                          c->d_status);
+  phase_mark(c, 0);
   k_clear_tiles<<<std::max(1, std::min(c->cap_slots / 256 + 1, g_num_sms)), 256, 0, c->stream>>>(
       c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->d_tile_mcount, c->d_slot_body, c->cap_slots);
   // candidate-list assembly unless a body is driven by uploaded states this step
@@ -1537,9 +1580,12 @@ cudaError_t ib_step_front(ibl_ctx* c) {
   const int use_tiles_host = any_prescribed ? 1 : 0;
   IBL_CU(cudaMemsetAsync(c->d_mixed, use_tiles_host, sizeof(int), c->stream));
   IBL_CU(cudaMemsetAsync(c->d_band_count, 0, sizeof(int), c->stream));
+  phase_mark(c, 1);
   k_mark_tiles<<<mb, tb, 0, c->stream>>>(m, c->d_base, g, c->d_tile_slot);
+  phase_mark(c, 2);
   k_assign_slots<<<std::max(1, std::min((c->tg.n_tiles + 255) / 256, 2 * g_num_sms)), 256, 0, c->stream>>>(
       c->tg.n_tiles, c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->cap_slots, c->d_status);
+  phase_mark(c, 3);
   c->launches += 4;
   return cudaGetLastError();
 }
@@ -1554,10 +1600,12 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   k_append_markers<<<(8 * m + 255) / 256, 256, 0, c->stream>>>(m, c->d_base, g, c->d_tile_slot, c->d_tile_mcount,
                                              c->d_tile_markers, c->d_status, c->d_body, c->d_slot_body,
                                              c->d_mixed);
+  phase_mark(c, 4);
   for (auto& b : c->bodies) b.prescribed = false;
   c->launches += 1;
   IBL_CU(cudaGetLastError());
   IBL_CU(interpolate(c, g));
+  phase_mark(c, 5);
   IBL_CU(cudaMemsetAsync(c->d_Gdiag_max, 0, sizeof(double) * MAX_BODIES, c->stream));
   k_assemble<<<(m + 7) / 8, 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts), c->d_tile_slot,
                                                  c->d_tile_mcount, c->d_tile_markers, g, c->d_body, c->d_Gcol,
@@ -1565,6 +1613,7 @@ cudaError_t ib_step_back(ibl_ctx* c) {
                                                  (unsigned long long*)c->d_Gdiag_max,
                                                  c->d_status, c->d_cand, c->d_ncand, c->d_mixed,
                                                  c->d_mixed + 1);
+  phase_mark(c, 6);
   c->launches += 1;
   IBL_CU(cudaGetLastError());
   // PCG (cooperative)
@@ -1640,6 +1689,7 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   void* args[] = {&A};
   IBL_CU(cudaLaunchCooperativeKernel((void*)k_pcg, dim3(pcg_blocks), dim3(PCG_THREADS), args, c->pcg_smem,
                                      c->stream));
+  phase_mark(c, 7);
   c->launches++;
   c->warm = true;
   c->warm_steps++;
@@ -1647,11 +1697,12 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   {
     const int nn = c->D == 3 ? 64 : 16;
     const long long tot = (long long)m * nn;
-    k_spread_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts),
+  k_spread_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts),
                                                                             reinterpret_cast<const df*>(c->d_p) + 3 * (size_t)m,
                                                                             c->d_tile_slot, g, c->d_acc, c->d_status);
     c->launches++;
   }
+  phase_mark(c, 8);
   IBL_CU(cudaGetLastError());
   return cudaSuccess;
 }

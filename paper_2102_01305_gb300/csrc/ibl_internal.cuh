@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "ibl.h"
@@ -155,6 +156,12 @@ struct ibl_ctx {
   std::vector<cudaEvent_t> prof_ev;
   std::vector<char> prof_split;
   long long prof_steps = 0;
+  // ibl_profile(ctx, 2): an event after every kernel of the step on the
+  // main stream, logged as (phase, event); phase -1 opens a step
+  int prof_level = 0;
+  std::vector<cudaEvent_t> pev_pool;
+  size_t pev_used = 0;
+  std::vector<std::pair<int, cudaEvent_t>> pev_log;
   // host copies of the bodies' marker sets (uploaded when the IB buffers are sized)
   std::vector<double> h_X0;      // m x 3
   std::vector<double> h_ds;      // m
@@ -188,6 +195,7 @@ cudaError_t ib_step(ibl_ctx* c);          // kinematics .. spreading, before the
 cudaError_t ib_step_front(ibl_ctx* c);    // kinematics and the band tiles of the step
 cudaError_t ib_step_back(ibl_ctx* c);     // interpolation .. solve .. spreading
 int num_sms();
+void phase_mark(ibl_ctx* c, int phase);   // ibl_profile level 2 only
 int pcg_block_count(const ibl_ctx* c);
 cudaError_t launch_force_field(ibl_ctx* c, double* d_out);
 

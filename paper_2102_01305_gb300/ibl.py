@@ -86,6 +86,7 @@ _SIGS = {
     "ibl_mass": ([_P, _D], C.c_int),
     "ibl_mass_noalloc": ([_P, C.c_int32, _D], C.c_int),
     "ibl_set_overlap": ([_P, C.c_int32], C.c_int),
+    "ibl_profile_phases": ([_P, _D, C.c_int32], C.c_int),
     "ibl_solver_blocks": ([_P, C.c_int32], C.c_int),
     "ibl_interpolate_points": ([_P, C.c_int32, _P, _P, _P], C.c_int),
     "ibl_spread_points": ([_P, C.c_int32, _P, _P, _P, _P], C.c_int),
@@ -187,6 +188,10 @@ def _device_out(t, shape, like):
     if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
         raise ValueError(f"output must be a contiguous {shape} tensor")
     return t
+
+
+PHASES = ["kinematics", "tile_reset", "tile_mark", "slot_assign", "marker_lists", "interpolation",
+          "assembly", "solve", "spreading", "collide"]
 
 
 class Context:
@@ -335,6 +340,12 @@ class Context:
         """Blocks of the cooperative solve (0: half the SMs)."""
         _check(self.h, _lib.ibl_solver_blocks(self.h, int(blocks)))
 
+    def ibl_profile_phases(self):
+        """Per-phase milliseconds (ibl_profile level 2): dict phase name -> ms."""
+        ms = np.zeros(10)
+        _check(self.h, _lib.ibl_profile_phases(self.h, ms.ctypes.data_as(_D), 10))
+        return dict(zip(PHASES, ms.tolist()))
+
     def ibl_set_overlap(self, mode):
         """-1 automatic, 0 one collide kernel after the IB chain, 1 split step."""
         _check(self.h, _lib.ibl_set_overlap(self.h, int(mode)))
@@ -384,8 +395,9 @@ class Context:
         _check(self.h, _lib.ibl_solver_trace(self.h, out.ctypes.data_as(_I64), 256, C.byref(n)), allow)
         return out[:n.value]
 
-    def ibl_profile(self, enable: bool):
-        _check(self.h, _lib.ibl_profile(self.h, 1 if enable else 0))
+    def ibl_profile(self, enable):
+        """0 off, 1 (or True) collide / IB chain totals, 2 also per-phase events."""
+        _check(self.h, _lib.ibl_profile(self.h, int(enable)))
 
     def ibl_profile_read(self):
         a, b, n = C.c_double(), C.c_double(), C.c_int64()
