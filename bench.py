@@ -350,9 +350,19 @@ def run_ours(args):
     per_launch_s = collide_ms / max(nprof, 1) * 1e-3
     alg_bytes = bytes_per_cell * cells
     achieved = alg_bytes / per_launch_s / 1e9
-    # the recorded traffic belongs to the wing workload's FP32 kernel (band lookup on)
-    rec = traffic_record(source_hash()) if (args.precision == "fp32" and args.workload == "wings") else None
-    roofline = {"bound": "hbm", "kernel": "k_collide (collide + stream + faces, D3Q19)",
+    split = bool(cfg["bodies"]) and (args.overlap == 1 or (args.overlap == -1 and cells >= (1 << 20)))
+    # the recorded traffic belongs to the wing workload's FP32 split-step kernels
+    rec = (traffic_record(source_hash())
+           if (args.precision == "fp32" and args.workload == "wings" and split and not args.solver_blocks)
+           else None)
+    if split:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        pcg_blocks = min(args.solver_blocks or sms // 2, sms)
+        kernel = (f"k_collide_bulk + k_collide_band (split step: the bulk collide runs on the "
+                  f"{sms - pcg_blocks} of {sms} SMs the solve leaves free, concurrently with the IB chain)")
+    else:
+        kernel = "k_collide (collide + stream + faces, D3Q19)"
+    roofline = {"bound": "hbm", "kernel": kernel,
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_src,
                 "traffic": rec["traffic_bytes_per_launch"] if rec else None,
@@ -361,6 +371,8 @@ def run_ours(args):
                 "ib_chain_ms_per_step": round(ib_ms / max(nprof, 1), 5),
                 "step_ms": round(ms / args.steps, 5),
                 "step_frac_of_roofline": round(alg_bytes / (ms / args.steps * 1e-3) / 1e9 / peak, 4)}
+    if split:
+        roofline["frac_of_sm_share"] = round(achieved / (peak * (sms - pcg_blocks) / sms), 4)
 
     cpu = None
     if RANK == 0 and WORLD == 1 and not args.no_cpu_baseline:
