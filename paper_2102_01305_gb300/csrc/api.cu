@@ -150,6 +150,8 @@ ibl_status ibl_destroy(ibl_ctx* c) {
   if (c->f[0]) cudaFree(c->f[0]);
   if (c->f[1]) cudaFree(c->f[1]);
   if (c->d_status) cudaFree(c->d_status);
+  if (c->d_pt_perm) cudaFree(c->d_pt_perm);
+  if (c->d_pt_bins) cudaFree(c->d_pt_bins);
   for (auto& ev : c->stage_ev)
     if (ev) cudaEventDestroy(ev);
   for (auto& ev : c->prof_ev) cudaEventDestroy(ev);

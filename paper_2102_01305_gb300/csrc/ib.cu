@@ -689,6 +689,7 @@ __device__ __forceinline__ void precond_row(const PcgArgs& A, int l, const float
 // routine (128 x 128 output tiles, 4 x 4 outputs per thread, K <= GJ_NB).
 constexpr int GT = 128;                 // output tile edge (GT x GJ_NB = 2048 float4 groups)
 constexpr int GS = GT + 4;              // padded shared-memory row
+constexpr int GJ_PS = GJ_NB + 1;        // padded row of the pivot block
 constexpr size_t GJ_SMEM = sizeof(float) * 2 * GJ_NB * GS;
 // dynamic shared memory of the solve kernel: the rebuild's tiles or, during
 // the iterations, one staged FP32 vector of all bodies (up to 24k markers)
@@ -795,39 +796,52 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
   }
   for (int kb = 0; kb < maxnb; ++kb) {
     const int k0 = kb * GJ_NB;
-    // phase 1: invert the pivot block of body b in block b (Gauss-Jordan in shared memory)
+    // phase 1: invert the pivot block of body b in block b (Gauss-Jordan in
+    // shared memory): 64 sequential pivots, so 4 warps with a named barrier
+    // do it (a block-wide barrier over 32 warps per pivot costs more than
+    // the arithmetic); rows padded to GJ_PS floats so that a warp's 16 rows
+    // fall in different banks
     for (int b = blockIdx.x; b < A.nbodies; b += gridDim.x) {
       const int mb = A.boff[b + 1] - A.boff[b];
       if (k0 >= mb) continue;
       const int kn = min(GJ_NB, mb - k0), ld = precond_ld(mb);
       float* Mb = A.M + A.poff[b];
-      float* piv = sm;                    // kn x kn
-      float* rowk = sm + GJ_NB * GJ_NB;   // pivot row and column copies
+      float* piv = sm;                    // kn x GJ_PS
+      float* rowk = sm + GJ_NB * GJ_PS;   // pivot row and column copies
       float* colk = rowk + GJ_NB;
       __syncthreads();
       for (int e = threadIdx.x; e < kn * kn; e += blockDim.x)
-        piv[e] = Mb[(long long)(k0 + e / kn) * ld + k0 + e % kn];
+        piv[(e / kn) * GJ_PS + e % kn] = Mb[(long long)(k0 + e / kn) * ld + k0 + e % kn];
       __syncthreads();
-      for (int k = 0; k < kn; ++k) {
-        if (threadIdx.x < kn) {
-          rowk[threadIdx.x] = piv[k * kn + threadIdx.x];
-          colk[threadIdx.x] = piv[threadIdx.x * kn + k];
+      if (threadIdx.x < 128) {
+        const int i = threadIdx.x >> 1, j0 = (threadIdx.x & 1) * 32;
+        for (int k = 0; k < kn; ++k) {
+          if (threadIdx.x < kn) {
+            rowk[threadIdx.x] = piv[k * GJ_PS + threadIdx.x];
+            colk[threadIdx.x] = piv[threadIdx.x * GJ_PS + k];
+          }
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          const float pk = 1.0f / rowk[k];
+          if (i < kn) {
+            const float ci = colk[i];
+            float* prow = piv + i * GJ_PS;
+            for (int jj = 0; jj < 32; ++jj) {
+              const int j = j0 + jj;
+              if (j >= kn) break;
+              float v;
+              if (i == k && j == k) v = pk;
+              else if (i == k) v = rowk[j] * pk;
+              else if (j == k) v = -ci * pk;
+              else v = prow[j] - ci * rowk[j] * pk;
+              prow[j] = v;
+            }
+          }
+          asm volatile("bar.sync 1, 128;" ::: "memory");
         }
-        __syncthreads();
-        const float pk = 1.0f / rowk[k];
-        for (int e = threadIdx.x; e < kn * kn; e += blockDim.x) {
-          const int i = e / kn, j = e % kn;
-          float v;
-          if (i == k && j == k) v = pk;
-          else if (i == k) v = rowk[j] * pk;
-          else if (j == k) v = -colk[i] * pk;
-          else v = piv[e] - colk[i] * rowk[j] * pk;
-          piv[e] = v;
-        }
-        __syncthreads();
       }
+      __syncthreads();
       for (int e = threadIdx.x; e < kn * kn; e += blockDim.x)
-        Mb[(long long)(k0 + e / kn) * ld + k0 + e % kn] = piv[e];
+        Mb[(long long)(k0 + e / kn) * ld + k0 + e % kn] = piv[(e / kn) * GJ_PS + e % kn];
     }
     grid.sync();
     if (kb == 0) trace_mark(A, 4);

@@ -83,6 +83,9 @@ struct ibl_ctx {
   long long step = 0;
   long long launches = 0;
   int* d_status = nullptr;       // [0] step status bits, [1] point-operator flag
+  int* d_pt_perm = nullptr;      // point operators: sorted point order (pt_cap ints)
+  int* d_pt_bins = nullptr;      // point operators: per-tile counters / offsets (n_tiles ints)
+  size_t pt_cap = 0;
   int sticky = 0;                // host copy of status bits seen so far
   std::string err;
 

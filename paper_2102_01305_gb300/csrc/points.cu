@@ -1,7 +1,8 @@
 // Stand-alone immersed-boundary transfers on an arbitrary point cloud: the
 // interpolation of Eq. 17 and the spreading of Eq. 15 on device arrays,
 // without the implicit solve.  They run the same per-node arithmetic as the
-// IB step (stencil_axis, node_rho_u), one warp per point.
+// IB step (stencil_axis, node_moments, double-float weights and sums), one
+// warp per point.
 #include "ib_stencil.cuh"
 
 namespace ibl {
@@ -20,22 +21,30 @@ struct PtGeo {
 
 __device__ __forceinline__ int wrap_once(int v, int n) { return v >= n ? v - n : v; }
 
-// Stencil of point l: bases and per-axis weights; false (flag set) if it
-// leaves a bounded axis, in which case the caller touches no memory.
+// Stencil of point l, computed once per warp: lane a < D evaluates axis a
+// (Eq. 14 in FP64), the bases and double-float weights are broadcast to all
+// lanes.  False (flag set) if it leaves a bounded axis, in which case the
+// caller touches no memory.  Every lane must call it.
 __device__ __forceinline__ bool point_stencil(const PtGeo& g, const double* X, int l, int b[3],
-                                              double w[3][4], int* flag) {
+                                              df w[3][4], int* flag) {
+  const int lane = threadIdx.x & 31;
+  int mb = 0;
+  df mw[4] = {df_make(1.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
   bool ok = true;
-  for (int a = 0; a < 3; ++a) {
-    if (a < g.D) {
-      ok &= stencil_axis(X[3 * l + a], g.n[a], g.per[a] != 0, b[a], w[a]);
-    } else {
-      b[a] = 0;
-      w[a][0] = 1.0;
-      w[a][1] = w[a][2] = w[a][3] = 0.0;
-    }
+  if (lane < g.D) {
+    double wd[4];
+    ok = stencil_axis(X[3 * l + lane], g.n[lane], g.per[lane] != 0, mb, wd);
+    for (int k = 0; k < 4; ++k) mw[k] = df_from_double(wd[k]);
   }
-  if (!ok) atomicOr(flag, PT_BAD_STENCIL);
-  return ok;
+  const bool all_ok = __all_sync(0xffffffffu, ok);
+  for (int a = 0; a < 3; ++a) {
+    b[a] = __shfl_sync(0xffffffffu, mb, a);
+    for (int k = 0; k < 4; ++k)
+      w[a][k] = df_make(__shfl_sync(0xffffffffu, mw[k].hi, a), __shfl_sync(0xffffffffu, mw[k].lo, a));
+    if (a >= g.D) b[a] = 0;
+  }
+  if (!all_ok && lane == 0) atomicOr(flag, PT_BAD_STENCIL);
+  return all_ok;
 }
 
 __device__ __forceinline__ long long stencil_node(const PtGeo& g, const int b[3], int k, int node[3]) {
@@ -51,31 +60,33 @@ __device__ __forceinline__ long long stencil_node(const PtGeo& g, const int b[3]
 template <int Q, class T, bool PULL>
 __global__ void k_points_interpolate(int m, const double* __restrict__ X, const T* __restrict__ src,
                                      FluidParams<typename Store<T>::R> p, PtGeo g, double* __restrict__ U,
-                                     double* __restrict__ rho_out, int* flag) {
-  const int l = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+                                     double* __restrict__ rho_out, int* flag, const int* __restrict__ perm) {
+  const int wl = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (l >= m) return;
+  if (wl >= m) return;
+  const int l = perm ? perm[wl] : wl;
   int b[3];
-  double w[3][4];
+  df w[3][4];
   if (!point_stencil(g, X, l, b, w, flag)) return;
+  using R = typename Store<T>::R;
   const int nn = g.D == 3 ? 64 : 16;
-  double acc[4] = {0, 0, 0, 0};
+  dfacc acc[4] = {acc_zero(), acc_zero(), acc_zero(), acc_zero()};
   for (int k = lane; k < nn; k += 32) {
     int node[3];
     const long long cell = stencil_node(g, b, k, node);
-    const double wt = w[0][k & 3] * w[1][(k >> 2) & 3] * w[2][g.D == 3 ? k >> 4 : 0];
-    double rho, u[3];
-    node_rho_u<Q, T, PULL>(src, node[0], node[1], node[2], cell, p, rho, u);
-    acc[0] += wt * rho;
-    acc[1] += wt * u[0];
-    acc[2] += wt * u[1];
-    acc[3] += wt * u[2];
+    df wt = df_mul(w[0][k & 3], w[1][(k >> 2) & 3]);
+    if (g.D == 3) wt = df_mul(wt, w[2][k >> 4]);
+    R drho, u[3];
+    node_moments<Q, T, PULL>(src, node[0], node[1], node[2], cell, p, drho, u);
+    acc_fma(acc[0], wt, df_from_float(1.f));
+    acc_fma(acc[0], wt, to_df(drho));
+    for (int c = 0; c < 3; ++c) acc_fma(acc[1 + c], wt, to_df(u[c]));
   }
-  for (int o = 16; o > 0; o >>= 1)
-    for (int c = 0; c < 4; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+  df v[4];
+  for (int c = 0; c < 4; ++c) v[c] = df_warp_sum(acc_value(acc[c]));
   if (lane == 0) {
-    if (rho_out) rho_out[l] = acc[0];
-    for (int a = 0; a < g.D; ++a) U[(long long)g.D * l + a] = acc[1 + a];
+    if (rho_out) rho_out[l] = df_to_double(v[0]);
+    for (int a = 0; a < g.D; ++a) U[(long long)g.D * l + a] = df_to_double(v[1 + a]);
   }
 }
 
@@ -83,27 +94,34 @@ __global__ void k_points_interpolate(int m, const double* __restrict__ X, const 
 // (the same 8 bytes per entry): integer sums do not depend on atomic order.
 __global__ void k_points_spread(int m, const double* __restrict__ X, const double* __restrict__ V,
                                 const double* __restrict__ ds, PtGeo g, long long N,
-                                unsigned long long* __restrict__ acc, int* flag) {
-  const int l = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+                                unsigned long long* __restrict__ acc, int* flag, const int* __restrict__ perm) {
+  const int wl = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (l >= m) return;
+  if (wl >= m) return;
+  const int l = perm ? perm[wl] : wl;
   int b[3];
-  double w[3][4];
+  df w[3][4];
   if (!point_stencil(g, X, l, b, w, flag)) return;
-  double v[3] = {0, 0, 0};
-  for (int a = 0; a < g.D; ++a) v[a] = V[(long long)g.D * l + a] * ds[l];
+  // V_l ds_l per component, formed by lane c and broadcast
+  df vc = df_make(0.f, 0.f);
+  if (lane < g.D) vc = df_from_double(V[(long long)g.D * l + lane] * ds[l]);
+  df v[3];
+  for (int c = 0; c < 3; ++c) v[c] = df_make(__shfl_sync(0xffffffffu, vc.hi, c), __shfl_sync(0xffffffffu, vc.lo, c));
   const int nn = g.D == 3 ? 64 : 16;
   for (int k = lane; k < nn; k += 32) {
     int node[3];
     const long long cell = stencil_node(g, b, k, node);
-    const double wt = w[0][k & 3] * w[1][(k >> 2) & 3] * w[2][g.D == 3 ? k >> 4 : 0];
+    df wt = df_mul(w[0][k & 3], w[1][(k >> 2) & 3]);
+    if (g.D == 3) wt = df_mul(wt, w[2][k >> 4]);
     for (int c = 0; c < g.D; ++c) {
-      const double val = wt * v[c];
-      if (!(fabs(val) < PT_FIX_LIMIT)) {
+      // the double-float product in fixed point, part by part (error <= 1 unit of 2^-46)
+      const df val = df_mul(wt, v[c]);
+      if (!(fabsf(val.hi) < (float)PT_FIX_LIMIT)) {
         atomicOr(flag, PT_BAD_RANGE);
         continue;
       }
-      atomicAdd(acc + c * N + cell, (unsigned long long)__double2ll_rn(val * PT_FIX_SCALE));
+      const long long fx = __float2ll_rn(val.hi * (float)PT_FIX_SCALE) + __float2ll_rn(val.lo * (float)PT_FIX_SCALE);
+      atomicAdd(acc + c * N + cell, (unsigned long long)fx);
     }
   }
 }
@@ -112,6 +130,68 @@ __global__ void k_fixed_to_double(unsigned long long* a, long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     reinterpret_cast<double*>(a)[i] = (double)(long long)a[i] * (1.0 / PT_FIX_SCALE);
+}
+
+// ---- spatial order of the points: a counting sort by the 16 x 4 x 4 (2D:
+// 16 x 16) tile holding each point's cell, so that neighbouring warps touch
+// neighbouring cells (cache and atomic locality); the results do not depend
+// on the order (interpolation is per point, spreading sums in fixed point).
+__device__ __forceinline__ int point_bin(const double* X, int l, const PtGeo& g, const TileGeom& t) {
+  int c[3] = {0, 0, 0};
+  for (int a = 0; a < g.D; ++a) {
+    const double x = X[3 * l + a];
+    double f = isfinite(x) ? floor(x) : 0.0;
+    if (g.per[a]) {
+      f = fmod(f, (double)g.n[a]);
+      if (f < 0.0) f += (double)g.n[a];
+    }
+    c[a] = (int)fmin(fmax(f, 0.0), (double)(g.n[a] - 1));
+  }
+  return ((c[2] / t.tz) * t.nty + (c[1] / t.ty)) * t.ntx + (c[0] / t.tx);
+}
+
+__global__ void k_pt_count(int m, const double* __restrict__ X, PtGeo g, TileGeom t, int* __restrict__ cnt) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < m) atomicAdd(&cnt[point_bin(X, l, g, t)], 1);
+}
+
+// Exclusive scan of n counters in place, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_pt_scan(int n, int* __restrict__ cnt) {
+  __shared__ int wsum[32];
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
+  int s = 0;
+  for (int i = b0; i < b1; ++i) s += cnt[i];
+  // inclusive scan of the per-thread sums across the block
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int v = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) wsum[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int x = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += t;
+    }
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  int run = v - s + (w > 0 ? wsum[w - 1] : 0);   // exclusive prefix of this thread's chunk
+  for (int i = b0; i < b1; ++i) {
+    const int c = cnt[i];
+    cnt[i] = run;
+    run += c;
+  }
+}
+
+__global__ void k_pt_scatter(int m, const double* __restrict__ X, PtGeo g, TileGeom t, int* __restrict__ off,
+                             int* __restrict__ perm) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < m) perm[atomicAdd(&off[point_bin(X, l, g, t)], 1)] = l;
 }
 
 PtGeo pt_geo(const ibl_ctx* c) {
@@ -124,10 +204,41 @@ PtGeo pt_geo(const ibl_ctx* c) {
   return g;
 }
 
+// Sorted point order in the context's scratch (grown on demand); nullptr
+// (identity order) for small clouds, where the sort costs more than it saves.
+constexpr int SORT_MIN_POINTS = 4096;
+const int* point_order(ibl_ctx* c, int m, const double* X, cudaError_t& e) {
+  e = cudaSuccess;
+  if (m < SORT_MIN_POINTS) return nullptr;
+  const int nb = c->tg.n_tiles;
+  if (c->pt_cap < (size_t)m || !c->d_pt_bins) {
+    if (c->d_pt_perm) cudaFree(c->d_pt_perm);
+    if (c->d_pt_bins) cudaFree(c->d_pt_bins);
+    c->d_pt_perm = nullptr;
+    c->d_pt_bins = nullptr;
+    c->pt_cap = 0;
+    e = cudaMalloc(&c->d_pt_perm, sizeof(int) * (size_t)m);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_pt_bins, sizeof(int) * (size_t)nb);
+    if (e != cudaSuccess) return nullptr;
+    c->pt_cap = (size_t)m;
+  }
+  const PtGeo g = pt_geo(c);
+  e = cudaMemsetAsync(c->d_pt_bins, 0, sizeof(int) * (size_t)nb, c->stream);
+  if (e != cudaSuccess) return nullptr;
+  const unsigned b = (unsigned)((m + 255) / 256);
+  k_pt_count<<<b, 256, 0, c->stream>>>(m, X, g, c->tg, c->d_pt_bins);
+  k_pt_scan<<<1, 1024, 0, c->stream>>>(nb, c->d_pt_bins);
+  k_pt_scatter<<<b, 256, 0, c->stream>>>(m, X, g, c->tg, c->d_pt_bins, c->d_pt_perm);
+  c->launches += 3;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? c->d_pt_perm : nullptr;
+}
+
 unsigned point_blocks(int m) { return (unsigned)(((long long)m * 32 + 255) / 256); }
 
 template <int Q, class T>
-void launch_interpolate(ibl_ctx* c, int m, const double* X, double* U, double* rho, int* flag) {
+void launch_interpolate(ibl_ctx* c, int m, const double* X, double* U, double* rho, int* flag,
+                        const int* perm) {
   using R = typename Store<T>::R;
   FluidParams<R> p{};
   p.nx = c->nx;
@@ -145,18 +256,19 @@ void launch_interpolate(ibl_ctx* c, int m, const double* X, double* U, double* r
   const T* src = (const T*)c->f[c->cur];
   const PtGeo g = pt_geo(c);
   if (c->poststream)
-    k_points_interpolate<Q, T, false><<<point_blocks(m), 256, 0, c->stream>>>(m, X, src, p, g, U, rho, flag);
+    k_points_interpolate<Q, T, false><<<point_blocks(m), 256, 0, c->stream>>>(m, X, src, p, g, U, rho, flag, perm);
   else
-    k_points_interpolate<Q, T, true><<<point_blocks(m), 256, 0, c->stream>>>(m, X, src, p, g, U, rho, flag);
+    k_points_interpolate<Q, T, true><<<point_blocks(m), 256, 0, c->stream>>>(m, X, src, p, g, U, rho, flag, perm);
 }
 
 template <int Q>
-void launch_interpolate_q(ibl_ctx* c, int m, const double* X, double* U, double* rho, int* flag) {
+void launch_interpolate_q(ibl_ctx* c, int m, const double* X, double* U, double* rho, int* flag,
+                          const int* perm) {
   switch (c->prec) {
-    case IBL_FP64: launch_interpolate<Q, double>(c, m, X, U, rho, flag); break;
-    case IBL_FP32: launch_interpolate<Q, float>(c, m, X, U, rho, flag); break;
-    case IBL_FP16DEV: launch_interpolate<Q, __half>(c, m, X, U, rho, flag); break;
-    default: launch_interpolate<Q, __nv_bfloat16>(c, m, X, U, rho, flag); break;
+    case IBL_FP64: launch_interpolate<Q, double>(c, m, X, U, rho, flag, perm); break;
+    case IBL_FP32: launch_interpolate<Q, float>(c, m, X, U, rho, flag, perm); break;
+    case IBL_FP16DEV: launch_interpolate<Q, __half>(c, m, X, U, rho, flag, perm); break;
+    default: launch_interpolate<Q, __nv_bfloat16>(c, m, X, U, rho, flag, perm); break;
   }
 }
 
@@ -194,8 +306,11 @@ ibl_status ibl_interpolate_points(ibl_ctx* c, int32_t m, const double* d_X, doub
   const ibl_status s = sync_and_collect(c);
   if (s != IBL_OK && s != IBL_ENOTCONV) return s;
   if (m == 0) return s;
-  if (c->Q == 9) launch_interpolate_q<9>(c, m, d_X, d_U, d_rho, c->d_status + 1);
-  else launch_interpolate_q<19>(c, m, d_X, d_U, d_rho, c->d_status + 1);
+  cudaError_t pe;
+  const int* perm = point_order(c, m, d_X, pe);
+  if (pe != cudaSuccess) return cuda_check(c, pe, "ibl_interpolate_points: point order");
+  if (c->Q == 9) launch_interpolate_q<9>(c, m, d_X, d_U, d_rho, c->d_status + 1, perm);
+  else launch_interpolate_q<19>(c, m, d_X, d_U, d_rho, c->d_status + 1, perm);
   c->launches++;
   const ibl_status r = finish(c, cudaGetLastError(), "ibl_interpolate_points");
   return r != IBL_OK ? r : s;
@@ -212,9 +327,11 @@ ibl_status ibl_spread_points(ibl_ctx* c, int32_t m, const double* d_X, const dou
   const long long tot = (long long)c->D * c->N;
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(d_out);
   cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * tot, c->stream);
+  const int* perm = nullptr;
+  if (e == cudaSuccess && m > 0) perm = point_order(c, m, d_X, e);
   if (e == cudaSuccess && m > 0) {
     k_points_spread<<<point_blocks(m), 256, 0, c->stream>>>(m, d_X, d_V, d_ds, pt_geo(c), c->N, acc,
-                                                            c->d_status + 1);
+                                                            c->d_status + 1, perm);
     c->launches++;
     e = cudaGetLastError();
   }
