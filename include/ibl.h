@@ -296,8 +296,10 @@ ibl_status ibl_profile(ibl_ctx* ctx, int32_t enable);
 
 /* With ibl_profile(ctx, 2): milliseconds per phase of the step on the
  * context's main stream since profiling was enabled, ms[0..n): 0 kinematics,
- * 1 band tile reset, 2 tile marking, 3 slot assignment, 4 marker lists,
- * 5 interpolation, 6 system assembly, 7 implicit solve, 8 spreading,
+ * 1 band counters reset, 2 tile marking, 3 slot assignment (which also
+ * resets the previous band), 4 marker lists,
+ * 5 interpolation and system assembly (one kernel; 6 is kept for the
+ * assembly and reads 0), 7 implicit solve, 8 spreading,
  * 9 collision (the band tiles' kernel in a split step; the bulk collide on
  * the second stream is in ibl_profile_read).  Each phase is the time from
  * the end of the previous one, so launch gaps are included.  Synchronises. */

@@ -54,6 +54,9 @@ __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (do
 
 __device__ __forceinline__ df df_neg(df a) { return df_make(-a.hi, -a.lo); }
 
+// a > b for normalised double-floats (hi carries the rounded value).
+__device__ __forceinline__ bool df_greater(df a, df b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+
 // a + b with the accurate (IEEE-style) double-float addition.  Commutative:
 // both error terms are exact, so a + b and b + a give the same bits.
 __device__ __forceinline__ df df_add(df a, df b) {

@@ -3,19 +3,23 @@
 //
 // Per step, in the paper's order:
 //   k_kinematics     marker positions X and wall velocities U_B (Eqs. 20-23,
-//                    rotational velocity of Sec. 3.3), stencil base nodes and
-//                    the 4-point cosine weights (Eq. 14) in FP64;
+//                    rotational velocity of Sec. 3.3; the per-body motion
+//                    state comes from the host), stencil base nodes and the
+//                    4-point cosine weights (Eq. 14, FP64, stored as FP32 pairs);
 //   k_mark/assign/append
 //                    grid tiles touched by a stencil get a band slot and a
 //                    list of the markers that touch them;
-//   k_interpolate    rho_l and u*_l (Eq. 17) from the populations of the stencil
-//                    nodes (moments of Eq. 11); B = U_B - u*_l (Eq. 19);
-//   k_assemble       sparse G_lk = sum_x D(x-X_l) D(x-X_k) (Eq. 18 without
-//                    ds_k: the solve is run on w = ds * du_B, G w = B);
+//   k_interp_assemble
+//                    one launch, two block ranges: rho_l and u*_l (Eq. 17)
+//                    from the populations of the stencil nodes (moments of
+//                    Eq. 11), B = U_B - u*_l (Eq. 19); and the sparse
+//                    G_lk = sum_x D(x-X_l) D(x-X_k) (Eq. 18 without ds_k: the
+//                    solve is run on w = ds * du_B, G w = B);
 //   k_pcg            preconditioned conjugate gradients for the three velocity
-//                    components at once, FP64 vectors and SpMV, an FP32 dense
-//                    per-body approximate inverse as preconditioner, rebuilt
-//                    in-kernel (blocked Gauss-Jordan) every few steps;
+//                    components at once in double-float arithmetic, an FP32
+//                    dense per-body approximate inverse as preconditioner,
+//                    rebuilt in-kernel (blocked Gauss-Jordan) every few hundred
+//                    steps;
 //   k_spread_scatter du(x) = sum_l w_l D(x - X_l) (Eq. 15) into 64-bit
 //                    fixed-point band accumulators (order-independent sums);
 //                    the collide kernel forms F = 2 rho du (Eq. 26) from them;
@@ -61,17 +65,22 @@ __device__ __forceinline__ int wrap(int v, int n) {
   return v;
 }
 
+// One thread per (marker, axis): the axis's position, wall velocity, stencil
+// base and weights (the rotation is recomputed by each of the three threads,
+// which is cheaper than serialising the three stencils on one thread).
 __global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ body_of,
                              const double* __restrict__ X0, const double* __restrict__ Xp,
                              const double* __restrict__ Up, double* __restrict__ X,
                              double* __restrict__ U, int* __restrict__ base,
                              df* __restrict__ wts, double t, Geo geo, int* status) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = gid / 3, a = gid - 3 * (gid / 3);
   if (l >= m_total) return;
   const BodyDev& B = bt.b[body_of[l]];
-  double x[3], u[3];
+  double x, u;
   if (B.prescribed) {
-    for (int a = 0; a < 3; ++a) { x[a] = Xp[3 * l + a]; u[a] = Up[3 * l + a]; }
+    x = Xp[3 * l + a];
+    u = Up[3 * l + a];
   } else {
     // per-body motion state of this step (formed on the host): A, A', alpha', cos, sin, e_s
     const double* st = B.st;
@@ -79,37 +88,35 @@ __global__ void k_kinematics(BodyTable bt, int m_total, const int* __restrict__ 
     const double es[3] = {st[5], st[6], 0.0};
     const double* e = B.axis;
     double d[3];
-    for (int a = 0; a < 3; ++a) d[a] = X0[3 * l + a] - B.hinge[a];
+    for (int k = 0; k < 3; ++k) d[k] = X0[3 * l + k] - B.hinge[k];
     // Rodrigues: r = d cos + (e x d) sin + e (e.d)(1 - cos)
     const double ed = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
     const double exd[3] = {e[1] * d[2] - e[2] * d[1], e[2] * d[0] - e[0] * d[2],
                            e[0] * d[1] - e[1] * d[0]};
     double r[3];
-    for (int a = 0; a < 3; ++a) r[a] = d[a] * c + exd[a] * s + e[a] * ed * (1.0 - c);
-    const double exr[3] = {e[1] * r[2] - e[2] * r[1], e[2] * r[0] - e[0] * r[2],
-                           e[0] * r[1] - e[1] * r[0]};
-    for (int a = 0; a < 3; ++a) {
-      x[a] = B.origin[a] + B.hinge[a] + r[a] + A * es[a];
-      u[a] = Ad * es[a] + ald * exr[a];
-    }
+    for (int k = 0; k < 3; ++k) r[k] = d[k] * c + exd[k] * s + e[k] * ed * (1.0 - c);
+    const int a1 = a == 2 ? 0 : a + 1, a2 = a == 0 ? 2 : a - 1;
+    const double exr = e[a1] * r[a2] - e[a2] * r[a1];
+    x = B.origin[a] + B.hinge[a] + r[a] + A * es[a];
+    u = Ad * es[a] + ald * exr;
   }
-  if (geo.D == 2) { x[2] = 0.0; u[2] = 0.0; }
-  for (int a = 0; a < 3; ++a) { X[3 * l + a] = x[a]; U[3 * l + a] = u[a]; }
-  for (int a = 0; a < 3; ++a) {
-    if (a >= geo.D) {
-      base[3 * l + a] = 0;
-      wts[12 * l + 4 * a + 0] = df_make(1.f, 0.f);
-      wts[12 * l + 4 * a + 1] = df_make(0.f, 0.f);
-      wts[12 * l + 4 * a + 2] = df_make(0.f, 0.f);
-      wts[12 * l + 4 * a + 3] = df_make(0.f, 0.f);
-      continue;
-    }
-    int b0;
-    double w[4];
-    if (!stencil_axis(x[a], geo.n[a], geo.per[a] != 0, b0, w)) atomicOr(status, ST_OVERFLOW);
-    for (int k = 0; k < 4; ++k) wts[12 * l + 4 * a + k] = df_from_double(w[k]);
-    base[3 * l + a] = b0;
+  if (a >= geo.D) {
+    X[3 * l + a] = 0.0;
+    U[3 * l + a] = 0.0;
+    base[3 * l + a] = 0;
+    wts[12 * l + 4 * a + 0] = df_make(1.f, 0.f);
+    wts[12 * l + 4 * a + 1] = df_make(0.f, 0.f);
+    wts[12 * l + 4 * a + 2] = df_make(0.f, 0.f);
+    wts[12 * l + 4 * a + 3] = df_make(0.f, 0.f);
+    return;
   }
+  X[3 * l + a] = x;
+  U[3 * l + a] = u;
+  int b0;
+  double w[4];
+  if (!stencil_axis(x, geo.n[a], geo.per[a] != 0, b0, w)) atomicOr(status, ST_OVERFLOW);
+  for (int k = 0; k < 4; ++k) wts[12 * l + 4 * a + k] = df_from_double(w[k]);
+  base[3 * l + a] = b0;
 }
 
 // ------------------------------------------------------------------ band tiles
@@ -140,16 +147,6 @@ __device__ int touched_tiles(const Geo& g, const int* b, int out[8]) {
   return n;
 }
 
-__global__ void k_clear_tiles(int* __restrict__ tile_slot, const int* __restrict__ slot_tile,
-                              const int* __restrict__ band_count, int* __restrict__ tile_mcount,
-                              int* __restrict__ slot_body, int cap) {
-  const int n = min(*band_count, cap);
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    tile_slot[slot_tile[s]] = -1;
-    tile_mcount[s] = 0;
-    slot_body[s] = -1;
-  }
-}
 
 __global__ void k_mark_tiles(int m_total, const int* __restrict__ base, Geo g,
                              int* __restrict__ tile_slot) {
@@ -160,18 +157,26 @@ __global__ void k_mark_tiles(int m_total, const int* __restrict__ base, Geo g,
   for (int i = 0; i < n; ++i) tile_slot[t[i]] = -2;
 }
 
+// Every tile: marked (-2) ones get a band slot with cleared per-slot state;
+// all others, including the last step's band, get -1.  (No separate reset of
+// the last band is needed.)
 __global__ void k_assign_slots(int n_tiles, int* __restrict__ tile_slot, int* __restrict__ slot_tile,
-                               int* __restrict__ band_count, int cap, int* status) {
+                               int* __restrict__ band_count, int cap, int* __restrict__ tile_mcount,
+                               int* __restrict__ slot_body, int* status) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
     if (tile_slot[t] == -2) {
       const int s = atomicAdd(band_count, 1);
       if (s < cap) {
         tile_slot[t] = s;
         slot_tile[s] = t;
+        tile_mcount[s] = 0;
+        slot_body[s] = -1;
       } else {
         tile_slot[t] = -1;
         atomicOr(status, ST_OVERFLOW);
       }
+    } else {
+      tile_slot[t] = -1;
     }
   }
 }
@@ -203,12 +208,12 @@ __global__ void k_append_markers(int m_total, const int* __restrict__ base, Geo 
 // collision), FP64 accumulation; B = U_B - u*_l (Eq. 19).  One warp per
 // marker, 64 (3D) or 16 (2D) nodes over its lanes.
 template <int Q, class T, bool PULL>
-__global__ void k_interpolate(int m_total, const int* __restrict__ base, const df* __restrict__ wts,
+__device__ __forceinline__ void interpolate_body(int vblock, int m_total, const int* __restrict__ base, const df* __restrict__ wts,
                               const T* __restrict__ src, FluidParams<typename Store<T>::R> p, Geo g,
                               const double* __restrict__ U, double* __restrict__ rho_l,
                               double* __restrict__ B) {
   using R = typename Store<T>::R;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int warp = (vblock * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= m_total) return;
   const int l = warp;
@@ -313,7 +318,7 @@ __device__ __forceinline__ bool pair_entry(const Geo& g, const int* bl, const df
   return true;
 }
 
-__global__ void k_assemble(int m_total, const int* __restrict__ base, const df* __restrict__ wts,
+__device__ __forceinline__ void assemble_body(int vblock, int m_total, const int* __restrict__ base, const df* __restrict__ wts,
                            const int* __restrict__ tile_slot, const int* __restrict__ tile_mcount,
                            const int* __restrict__ tile_markers, Geo g, const int* __restrict__ body_of,
                            int* __restrict__ Gcol, df* __restrict__ Gval, int* __restrict__ Gnnz,
@@ -324,7 +329,7 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const df* 
   __shared__ df s_val[8][G_MAXNNZ];
   const int wib = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int l = blockIdx.x * 8 + wib;
+  const int l = vblock * 8 + wib;
   if (l >= m_total) return;
   const int* bl = base + 3 * l;
   const df* wl = wts + 12 * l;
@@ -412,6 +417,40 @@ __global__ void k_assemble(int m_total, const int* __restrict__ base, const df* 
   if (lane == 0) {
     Gnnz[l] = count;
     atomicMax(&rowsum_max[body_of[l]], (unsigned long long)__double_as_longlong((double)rowsum));
+  }
+}
+
+// Interpolation (blocks [0, nb_interp): one warp per marker) and system
+// assembly (the remaining blocks: one warp per row) in one launch: both
+// need only the step's marker lists, and their latencies overlap.
+struct AssembleArgs {
+  const int* tile_slot;
+  const int* tile_mcount;
+  const int* tile_markers;
+  const int* body_of;
+  int* Gcol;
+  df* Gval;
+  int* Gnnz;
+  unsigned long long* rowsum_max;
+  int* status;
+  const int* cand;
+  const int* ncand;
+  const int* use_tiles;
+  const int* cand_bad;
+};
+
+template <int Q, class T, bool PULL>
+__global__ void __launch_bounds__(256) k_interp_assemble(int nb_interp, int m_total, const int* __restrict__ base,
+                                                         const df* __restrict__ wts, const T* __restrict__ src,
+                                                         FluidParams<typename Store<T>::R> p, Geo g,
+                                                         const double* __restrict__ U, double* __restrict__ rho_l,
+                                                         double* __restrict__ B, AssembleArgs aa) {
+  if ((int)blockIdx.x < nb_interp) {
+    interpolate_body<Q, T, PULL>(blockIdx.x, m_total, base, wts, src, p, g, U, rho_l, B);
+  } else {
+    assemble_body(blockIdx.x - nb_interp, m_total, base, wts, aa.tile_slot, aa.tile_mcount, aa.tile_markers, g,
+                  aa.body_of, aa.Gcol, aa.Gval, aa.Gnnz, aa.rowsum_max, aa.status, aa.cand, aa.ncand,
+                  aa.use_tiles, aa.cand_bad);
   }
 }
 
@@ -559,8 +598,8 @@ __device__ void block_partial3(df v, df* sh, df* out) {
 
 // Grid total of one double-float partial (slot `slot` of every block), for
 // one warp: each lane issues all of its loads at once (one memory round
-// trip), adds its blocks in order, then a butterfly; every lane ends with
-// the total.
+// trip), adds its blocks in a fixed pairwise tree, then a butterfly; every
+// lane ends with the total.
 __device__ __forceinline__ df grid_total_df(const df* red, int slot) {
   constexpr int U = MAX_PCG_BLOCKS / 32;
   const int lane = threadIdx.x & 31;
@@ -570,10 +609,15 @@ __device__ __forceinline__ df grid_total_df(const df* red, int slot) {
     const int b = lane + 32 * u;
     v[u] = b < (int)gridDim.x ? __ldcg(reinterpret_cast<const float2*>(red + b * 8 + slot)) : make_float2(0.f, 0.f);
   }
-  df acc = df_make(0.f, 0.f);
+  // pairwise tree over the lane's blocks (depth log2 U instead of U)
+  df t[U];
 #pragma unroll
-  for (int u = 0; u < U; ++u) acc = df_add(acc, df_make(v[u].x, v[u].y));
-  return df_warp_sum(acc);
+  for (int u = 0; u < U; ++u) t[u] = df_make(v[u].x, v[u].y);
+#pragma unroll
+  for (int w = U / 2; w >= 1; w >>= 1)
+#pragma unroll
+    for (int u = 0; u < w; ++u) t[u] = df_add(t[u], t[u + w]);
+  return df_warp_sum(t[0]);
 }
 
 // Row stride of a body's dense preconditioner: padded to 4 floats so rows
@@ -1037,7 +1081,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   // forms them from the grid totals (every block gets bitwise the same values).
   __shared__ df s_rz[3], s_scale[3], s_beta[3], s_alpha[3];
   __shared__ float s_alphaf[3];
-  __shared__ double s_stop[3];
+  __shared__ df s_stop[3];
   __shared__ int s_conv[3];
   if (wib < 3) {
     // warp c: totals of component c; the stopping threshold tol^2 (B.MB) once per solve
@@ -1048,8 +1092,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
       s_scale[c] = sc;
       s_rz[c] = rz;
       s_beta[c] = dzero;
-      s_stop[c] = A.tol * A.tol * df_to_double(sc);
-      s_conv[c] = (c >= A.D || !(df_to_double(rz) > s_stop[c])) ? 1 : 0;
+      s_stop[c] = df_from_double(A.tol * A.tol * df_to_double(sc));
+      s_conv[c] = (c >= A.D || !df_greater(rz, s_stop[c])) ? 1 : 0;
     }
   }
   __syncthreads();
@@ -1177,7 +1221,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
         const df prev = s_rz[c];
         s_beta[c] = prev.hi > 0.f ? df_div(rzn, prev) : dzero;
         s_rz[c] = rzn;
-        s_conv[c] = (c >= A.D || !(df_to_double(rzn) > s_stop[c])) ? 1 : 0;
+        s_conv[c] = (c >= A.D || !df_greater(rzn, s_stop[c])) ? 1 : 0;
       }
     }
     __syncthreads();
@@ -1450,13 +1494,29 @@ static cudaError_t interpolate_q(ibl_ctx* c, const Geo& g) {
   p.status = c->d_status;
   const T* src = (const T*)c->f[c->cur];
   const int m = c->m_total;
-  const int wb = (m * 32 + 255) / 256;
+  const int wb = (m * 32 + 255) / 256;   // interpolation blocks (8 markers each)
+  const int ab = (m + 7) / 8;            // assembly blocks (8 rows each)
+  AssembleArgs aa;
+  aa.tile_slot = c->d_tile_slot;
+  aa.tile_mcount = c->d_tile_mcount;
+  aa.tile_markers = c->d_tile_markers;
+  aa.body_of = c->d_body;
+  aa.Gcol = c->d_Gcol;
+  aa.Gval = reinterpret_cast<df*>(c->d_Gval);
+  aa.Gnnz = c->d_Gnnz;
+  aa.rowsum_max = (unsigned long long*)c->d_Gdiag_max;
+  aa.status = c->d_status;
+  aa.cand = c->d_cand;
+  aa.ncand = c->d_ncand;
+  aa.use_tiles = c->d_mixed;
+  aa.cand_bad = c->d_mixed + 1;
+  const df* w = reinterpret_cast<const df*>(c->d_wts);
   if (c->poststream)
-    k_interpolate<Q, T, false><<<wb, 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts), src, p, g, c->d_U,
-                                                               c->d_rho_l, c->d_B);
+    k_interp_assemble<Q, T, false><<<wb + ab, 256, 0, c->stream>>>(wb, m, c->d_base, w, src, p, g, c->d_U, c->d_rho_l,
+                                                                     c->d_B, aa);
   else
-    k_interpolate<Q, T, true><<<wb, 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts), src, p, g, c->d_U,
-                                                               c->d_rho_l, c->d_B);
+    k_interp_assemble<Q, T, true><<<wb + ab, 256, 0, c->stream>>>(wb, m, c->d_base, w, src, p, g, c->d_U, c->d_rho_l,
+                                                                    c->d_B, aa);
   c->launches++;
   return cudaGetLastError();
 }
@@ -1582,12 +1642,10 @@ cudaError_t ib_step_front(ibl_ctx* c) {
   }
   const int tb = 64;
   const int mb = (m + tb - 1) / tb;
-  k_kinematics<<<mb, tb, 0, c->stream>>>(bt, m, c->d_body, c->d_X0, c->d_Xp, c->d_Up, c->d_X, c->d_U,
+  k_kinematics<<<(3 * m + 127) / 128, 128, 0, c->stream>>>(bt, m, c->d_body, c->d_X0, c->d_Xp, c->d_Up, c->d_X, c->d_U,
                                          c->d_base, reinterpret_cast<df*>(c->d_wts), (double)c->step, g,
                                          c->d_status);
   phase_mark(c, 0);
-  k_clear_tiles<<<std::max(1, std::min(c->cap_slots / 256 + 1, g_num_sms)), 256, 0, c->stream>>>(
-      c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->d_tile_mcount, c->d_slot_body, c->cap_slots);
   // candidate-list assembly unless a body is driven by uploaded states this step
   bool any_prescribed = false;
   for (auto& b : c->bodies) any_prescribed |= b.prescribed;
@@ -1598,9 +1656,10 @@ cudaError_t ib_step_front(ibl_ctx* c) {
   k_mark_tiles<<<mb, tb, 0, c->stream>>>(m, c->d_base, g, c->d_tile_slot);
   phase_mark(c, 2);
   k_assign_slots<<<std::max(1, std::min((c->tg.n_tiles + 255) / 256, 2 * g_num_sms)), 256, 0, c->stream>>>(
-      c->tg.n_tiles, c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->cap_slots, c->d_status);
+      c->tg.n_tiles, c->d_tile_slot, c->d_slot_tile, c->d_band_count, c->cap_slots, c->d_tile_mcount,
+      c->d_slot_body, c->d_status);
   phase_mark(c, 3);
-  c->launches += 4;
+  c->launches += 3;
   return cudaGetLastError();
 }
 
@@ -1618,18 +1677,10 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   for (auto& b : c->bodies) b.prescribed = false;
   c->launches += 1;
   IBL_CU(cudaGetLastError());
-  IBL_CU(interpolate(c, g));
-  phase_mark(c, 5);
   IBL_CU(cudaMemsetAsync(c->d_Gdiag_max, 0, sizeof(double) * MAX_BODIES, c->stream));
-  k_assemble<<<(m + 7) / 8, 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts), c->d_tile_slot,
-                                                 c->d_tile_mcount, c->d_tile_markers, g, c->d_body, c->d_Gcol,
-                                                 reinterpret_cast<df*>(c->d_Gval), c->d_Gnnz,
-                                                 (unsigned long long*)c->d_Gdiag_max,
-                                                 c->d_status, c->d_cand, c->d_ncand, c->d_mixed,
-                                                 c->d_mixed + 1);
+  IBL_CU(interpolate(c, g));   // interpolation and assembly, one launch
+  phase_mark(c, 5);
   phase_mark(c, 6);
-  c->launches += 1;
-  IBL_CU(cudaGetLastError());
   // PCG (cooperative)
   PcgArgs A;
   A.m_total = m;

@@ -190,7 +190,7 @@ def _device_out(t, shape, like):
     return t
 
 
-PHASES = ["kinematics", "tile_reset", "tile_mark", "slot_assign", "marker_lists", "interpolation",
+PHASES = ["kinematics", "counter_reset", "tile_mark", "slot_assign", "marker_lists", "interpolation",
           "assembly", "solve", "spreading", "collide"]
 
 
