@@ -661,17 +661,16 @@ __device__ float* stage_x(const PcgArgs& A, const float* __restrict__ a, const f
 __device__ __forceinline__ void precond_row(const PcgArgs& A, int l, const float* __restrict__ xs,
                                             const float* __restrict__ a, const float* __restrict__ b,
                                             const float s[3], float out[3], int lane,
-                                            const float* __restrict__ mres) {
+                                            const float* __restrict__ rs) {
   const int bd = A.body_of[l];
   const int o = A.boff[bd], mb = A.boff[bd + 1] - o;
   const int ld = precond_ld(mb);
   const float* row = A.M + A.poff[bd] + (long long)(l - o) * ld;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
   const int nq = ld >> 2;
-  if (xs && mres) {
-    // the row is resident in shared memory for the whole solve
+  if (xs && rs) {
+    // the row is resident in shared memory (rs) for the whole solve
     const float* xb = xs + A.voff[bd];
-    const float* rs = mres + (long long)((l - (int)blockIdx.x) / (int)gridDim.x) * A.row_slot;
 #pragma unroll 4
     for (int q = lane; q < nq; q += 32) {
       const float4 mv = reinterpret_cast<const float4*>(rs)[q];
@@ -722,6 +721,55 @@ __device__ __forceinline__ void precond_row(const PcgArgs& A, int l, const float
     s2 += __shfl_xor_sync(0xffffffffu, s2, off);
   }
   out[0] = s0; out[1] = s1; out[2] = s2;
+}
+
+// Rows l0 = 2p and l1 = 2p + 1 of the preconditioner in one pass when they
+// belong to the same body (the usual case): each staged x group is read once
+// for both rows, halving the shared-memory traffic that bounds this product.
+// rs0 / rs1: the rows' resident copies or nullptr.  z1 is untouched when
+// l1 >= m.
+__device__ __forceinline__ void precond_pair(const PcgArgs& A, int p, const float* __restrict__ xs,
+                                             const float* __restrict__ a, const float* __restrict__ b,
+                                             const float s[3], float z0[3], float z1[3], int lane,
+                                             const float* __restrict__ rs0, const float* __restrict__ rs1) {
+  const int m = A.m_total;
+  const int l0 = 2 * p, l1 = 2 * p + 1;
+  const int bd = A.body_of[l0];
+  if (!xs || l1 >= m || A.body_of[l1] != bd) {
+    precond_row(A, l0, xs, a, b, s, z0, lane, rs0);
+    if (l1 < m) precond_row(A, l1, xs, a, b, s, z1, lane, rs1);
+    return;
+  }
+  const int o = A.boff[bd], ld = precond_ld(A.boff[bd + 1] - o), nq = ld >> 2;
+  const float4* r0 = reinterpret_cast<const float4*>(rs0 ? rs0 : A.M + A.poff[bd] + (long long)(l0 - o) * ld);
+  const float4* r1 = reinterpret_cast<const float4*>(rs1 ? rs1 : A.M + A.poff[bd] + (long long)(l1 - o) * ld);
+  const float* xb = xs + A.voff[bd];
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll 2
+  for (int q = lane; q < nq; q += 32) {
+    const float4 m0 = rs0 ? r0[q] : __ldcg(r0 + q);
+    const float4 m1 = rs1 ? r1[q] : __ldcg(r1 + q);
+    const float4* xv = reinterpret_cast<const float4*>(xb + 12 * q);
+    const float4 x0 = xv[0], x1 = xv[1], x2 = xv[2];
+    a0 = fmaf(m0.x, x0.x, a0); a1 = fmaf(m0.x, x0.y, a1); a2 = fmaf(m0.x, x0.z, a2);
+    a0 = fmaf(m0.y, x0.w, a0); a1 = fmaf(m0.y, x1.x, a1); a2 = fmaf(m0.y, x1.y, a2);
+    a0 = fmaf(m0.z, x1.z, a0); a1 = fmaf(m0.z, x1.w, a1); a2 = fmaf(m0.z, x2.x, a2);
+    a0 = fmaf(m0.w, x2.y, a0); a1 = fmaf(m0.w, x2.z, a1); a2 = fmaf(m0.w, x2.w, a2);
+    b0 = fmaf(m1.x, x0.x, b0); b1 = fmaf(m1.x, x0.y, b1); b2 = fmaf(m1.x, x0.z, b2);
+    b0 = fmaf(m1.y, x0.w, b0); b1 = fmaf(m1.y, x1.x, b1); b2 = fmaf(m1.y, x1.y, b2);
+    b0 = fmaf(m1.z, x1.z, b0); b1 = fmaf(m1.z, x1.w, b1); b2 = fmaf(m1.z, x2.x, b2);
+    b0 = fmaf(m1.w, x2.y, b0); b1 = fmaf(m1.w, x2.z, b1); b2 = fmaf(m1.w, x2.w, b2);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, off);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+    b0 += __shfl_xor_sync(0xffffffffu, b0, off);
+    b1 += __shfl_xor_sync(0xffffffffu, b1, off);
+    b2 += __shfl_xor_sync(0xffffffffu, b2, off);
+  }
+  z0[0] = a0; z0[1] = a1; z0[2] = a2;
+  z1[0] = b0; z1[1] = b1; z1[2] = b2;
 }
 
 // ---------------------------------------------------------------- dense rebuild
@@ -994,19 +1042,26 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     grid.sync();
     gj_invert(A, grid, sm);
   }
-  // this block's preconditioner rows (l = blockIdx.x + gridDim.x j) stay in
-  // shared memory for the whole solve when they fit; warp j % 32 owns row j
+  // the preconditioner is applied to row pairs (2p, 2p + 1), pair p owned by
+  // block p mod gridDim, warp (p / gridDim) mod 32; this block's pairs
+  // (jp-th: p = blockIdx.x + gridDim.x jp) stay in shared memory, rows 2jp
+  // and 2jp + 1, for the whole solve when they fit
+  const int npairs = (m + 1) >> 1;
+  const int prow0 = blockIdx.x + gridDim.x * wib;
   float* mres = nullptr;
   if (A.row_slot > 0) {
     mres = sm + A.smem_floats;
-    for (int j = wib, l = blockIdx.x + gridDim.x * wib; l < m; j += PCG_WARPS, l += rstep) {
-      const int bd = A.body_of[l];
-      const int o = A.boff[bd], ld = precond_ld(A.boff[bd + 1] - o);
-      const float4* src = reinterpret_cast<const float4*>(A.M + A.poff[bd] + (long long)(l - o) * ld);
-      float4* dst = reinterpret_cast<float4*>(mres + (long long)j * A.row_slot);
+    for (int jp = wib, pp = prow0; pp < npairs; jp += PCG_WARPS, pp += rstep)
+      for (int h = 0; h < 2; ++h) {
+        const int l = 2 * pp + h;
+        if (l >= m) break;
+        const int bd = A.body_of[l];
+        const int o = A.boff[bd], ld = precond_ld(A.boff[bd + 1] - o);
+        const float4* src = reinterpret_cast<const float4*>(A.M + A.poff[bd] + (long long)(l - o) * ld);
+        float4* dst = reinterpret_cast<float4*>(mres + (long long)(2 * jp + h) * A.row_slot);
 #pragma unroll 4
-      for (int q = lane; q < (ld >> 2); q += 32) dst[q] = __ldcg(src + q);
-    }
+        for (int q = lane; q < (ld >> 2); q += 32) dst[q] = __ldcg(src + q);
+      }
   }
   trace_mark(A, 1);
 
@@ -1058,19 +1113,34 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     df rz = dzero, bb = dzero;
     const float zero3[3] = {0.f, 0.f, 0.f};
     const float* xs = stage_x(A, A.rf, nullptr, zero3, sm);
-    for (int l = row0; l < m; l += rstep) {
-      float zr[3];
-      precond_row(A, l, xs, A.rf, nullptr, zero3, zr, lane, mres);
-      if (lane < 3) {
-        A.zf[3 * l + lane] = zr[lane];
-        rz = df_add(rz, df_mul_f(A.rd[3 * l + lane], zr[lane]));
+    for (int jp = wib, pp = prow0; pp < npairs; jp += PCG_WARPS, pp += rstep) {
+      float z6[2][3];
+      precond_pair(A, pp, xs, A.rf, nullptr, zero3, z6[0], z6[1], lane, mres ? mres + (long long)(2 * jp) * A.row_slot : nullptr,
+                   mres ? mres + (long long)(2 * jp + 1) * A.row_slot : nullptr);
+      const int h = lane / 3, c = lane - 3 * (lane / 3), l = 2 * pp + h;
+      if (lane < 6 && l < m) {
+        const float zv = h == 0 ? z6[0][c] : z6[1][c];
+        A.zf[3 * l + c] = zv;
+        rz = df_add(rz, df_mul_f(A.rd[3 * l + c], zv));
       }
     }
     xs = stage_x(A, A.Bf, nullptr, zero3, sm);
-    for (int l = row0; l < m; l += rstep) {
-      float zb[3];
-      precond_row(A, l, xs, A.Bf, nullptr, zero3, zb, lane, mres);
-      if (lane < 3) bb = df_add(bb, df_mul_f(df_from_double(A.B[3 * l + lane]), zb[lane]));
+    for (int jp = wib, pp = prow0; pp < npairs; jp += PCG_WARPS, pp += rstep) {
+      float z6[2][3];
+      precond_pair(A, pp, xs, A.Bf, nullptr, zero3, z6[0], z6[1], lane, mres ? mres + (long long)(2 * jp) * A.row_slot : nullptr,
+                   mres ? mres + (long long)(2 * jp + 1) * A.row_slot : nullptr);
+      const int h = lane / 3, c = lane - 3 * (lane / 3), l = 2 * pp + h;
+      if (lane < 6 && l < m)
+        bb = df_add(bb, df_mul_f(df_from_double(A.B[3 * l + c]), h == 0 ? z6[0][c] : z6[1][c]));
+    }
+    // lanes 3-5 hold the second row's components: fold them into lanes 0-2
+    {
+      const df r3 = df_make(__shfl_down_sync(0xffffffffu, rz.hi, 3), __shfl_down_sync(0xffffffffu, rz.lo, 3));
+      const df b3 = df_make(__shfl_down_sync(0xffffffffu, bb.hi, 3), __shfl_down_sync(0xffffffffu, bb.lo, 3));
+      if (lane < 3) {
+        rz = df_add(rz, r3);
+        bb = df_add(bb, b3);
+      }
     }
     block_partial3(bb, shdf, A.red + blockIdx.x * 8);
     block_partial3(rz, shdf, A.red + blockIdx.x * 8 + 3);
@@ -1192,21 +1262,31 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
       df rz = dzero;
       const float* xs = stage_x(A, A.rf, A.Apf, alphaf, sm);
       trace_mark(A, ts + 6);
-      for (int l = row0; l < m; l += rstep) {
-        // the row's vector entries are fetched before the product so that
-        // their latency overlaps it
-        const int c = lane < 3 ? lane : 0;
-        const df w0 = A.wd[3 * l + c], p0 = A.pd[3 * l + c], r0 = A.rd[3 * l + c], ap0 = A.Apd[3 * l + c];
-        float zl[3];
-        precond_row(A, l, xs, A.rf, A.Apf, alphaf, zl, lane, mres);
-        if (lane < 3) {
+      for (int jp = wib, pp = prow0; pp < npairs; jp += PCG_WARPS, pp += rstep) {
+        // lane h*3 + c (< 6) updates component c of row 2pp + h; its vector
+        // entries are fetched before the product so that their latency overlaps it
+        const int h = lane / 3, c = lane - 3 * (lane / 3);
+        const int l = 2 * pp + (lane < 6 ? h : 0);
+        const bool mine = lane < 6 && l < m;
+        const int ls = mine ? l : 2 * pp, cs = mine ? c : 0;
+        const df w0 = A.wd[3 * ls + cs], p0 = A.pd[3 * ls + cs], r0 = A.rd[3 * ls + cs], ap0 = A.Apd[3 * ls + cs];
+        float z6[2][3];
+        precond_pair(A, pp, xs, A.rf, A.Apf, alphaf, z6[0], z6[1], lane,
+                     mres ? mres + (long long)(2 * jp) * A.row_slot : nullptr,
+                     mres ? mres + (long long)(2 * jp + 1) * A.row_slot : nullptr);
+        if (mine) {
+          const float zl = h == 0 ? z6[0][c] : z6[1][c];
           const df alpha = s_alpha[c];
           A.wd[3 * l + c] = df_add(w0, df_mul(alpha, p0));
           const df rn = df_sub(r0, df_mul(alpha, ap0));
           A.rd[3 * l + c] = rn;
-          A.zf[3 * l + c] = zl[c];
-          rz = df_add(rz, df_mul_f(rn, zl[c]));
+          A.zf[3 * l + c] = zl;
+          rz = df_add(rz, df_mul_f(rn, zl));
         }
+      }
+      {
+        const df r3 = df_make(__shfl_down_sync(0xffffffffu, rz.hi, 3), __shfl_down_sync(0xffffffffu, rz.lo, 3));
+        if (lane < 3) rz = df_add(rz, r3);
       }
       trace_mark(A, ts + 7);
       block_partial3(rz, shdf, A.red + blockIdx.x * 8 + 3);
@@ -1723,7 +1803,7 @@ cudaError_t ib_step_back(ibl_ctx* c) {
     stage = std::max(std::min((stage + 15) & ~(size_t)15, PCG_SMEM), GJ_SMEM);
     int slot = 0;
     for (int b = 0; b < A.nbodies; ++b) slot = std::max(slot, precond_ld(c->bodies[b].m));
-    const size_t rows = (size_t)(m + pcg_blocks - 1) / pcg_blocks;
+    const size_t rows = 2 * (((size_t)(m + 1) / 2 + pcg_blocks - 1) / pcg_blocks);   // whole row pairs
     const size_t need = stage + rows * (size_t)slot * sizeof(float);
     A.smem_floats = (int)(stage / sizeof(float));
     A.row_slot = need <= PCG_SMEM_MAX ? slot : 0;
