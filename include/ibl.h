@@ -253,7 +253,7 @@ ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_resid
 
 /* Settings of the implicit IB solve (preconditioned conjugate gradients on
  * the system of Eqs. 18-19): the dense FP32 approximate inverse used as
- * preconditioner is rebuilt every refresh_every steps (default 256) and
+ * preconditioner is rebuilt every refresh_every steps (default 384) and
  * early when a solve needed more than 40 iterations; tol is the relative
  * residual in the preconditioner's norm (0 = default: 1e-10 for FP64
  * storage, 1e-7 for FP32, 1e-6 for FP16/BF16); extrapolate != 0 starts each solve from

@@ -147,7 +147,7 @@ struct ibl_ctx {
   bool warm = false;             // d_w holds the previous solution
   long long warm_steps = 0;      // consecutive solves behind d_w (2+: extrapolate)
   bool extrapolate = true;
-  int refresh_every = 256;       // steps between scheduled preconditioner rebuilds
+  int refresh_every = 384;       // steps between scheduled preconditioner rebuilds
   double solver_tol = 0.0;       // 0: default for the storage precision
   int pcg_blocks = 0;            // blocks of the cooperative solve (0: half the SMs)
   size_t pcg_smem = 0;           // dynamic shared memory of the last solve launch

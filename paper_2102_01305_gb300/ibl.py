@@ -386,7 +386,7 @@ class Context:
         _check(self.h, _lib.ibl_solver_stats(self.h, C.byref(it), C.byref(res), C.byref(ref)), allow)
         return it.value, res.value, ref.value
 
-    def ibl_solver_config(self, refresh_every=256, tol=0.0, extrapolate=True):
+    def ibl_solver_config(self, refresh_every=384, tol=0.0, extrapolate=True):
         _check(self.h, _lib.ibl_solver_config(self.h, int(refresh_every), float(tol), 1 if extrapolate else 0))
 
     def ibl_solver_trace(self, allow=()):

@@ -6,6 +6,8 @@
 * Figure-eight hovering (Sec. 3.2, Eqs. 20-22): one foil of chord/thickness
   7.5 pitching about its centre while sweeping along a stroke plane at 60
   degrees, fluid at rest in a periodic 50c x 25c box.
+* Stationary cylinder (Sec. 3.1): D = 8 in a 50D x 50D box, Zou-He velocity
+  inlet and pressure outlet, Re = 20.
 
 The oracle runs each case once (D2Q9 FP64, dense direct solve); the GPU runs
 it in FP64 and in FP32 storage.
@@ -27,6 +29,7 @@ def _cases():
         "clap_fling": lambda prec: W.clap_fling_2d(chord=16.0, Re=50.0, J=1.67e-3, period=800.0,
                                                    precision=prec),
         "figure_eight": lambda prec: W.figure_eight_2d(chord=16.0, Re=75.0, period=2000.0, precision=prec),
+        "cylinder_50d": lambda prec: W.cylinder_50d(diameter=8.0, Re=20.0, u_in=0.05, precision=prec),
     }
 
 
@@ -47,7 +50,7 @@ def _coef_err(ctx, sim, body):
     return (np.abs(hist[:, 0] - ref[:, 0]).max() / scale, np.abs(hist[:, 1] - ref[:, 1]).max() / scale)
 
 
-@pytest.mark.parametrize("name", ["clap_fling", "figure_eight"])
+@pytest.mark.parametrize("name", ["clap_fling", "figure_eight", "cylinder_50d"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_paper_2d_case(ibl, oracle_runs, name, prec):
     cfg = _cases()[name](prec)

@@ -178,6 +178,29 @@ def cylinder_channel(nx=200, ny=100, diameter=20.0, center=(50.0, 50.0), m=63,
             "reference": {"U_ref": u_mean, "L": diameter, "rho_ref": 1.0}}
 
 
+def cylinder_50d(diameter=8.0, Re=20.0, u_in=0.05, precision="fp64"):
+    """Sec. 3.1 validation case: a stationary cylinder in a 50D x 50D box,
+    uniform velocity inlet (Zou-He) at -x and pressure outlet at +x.  The
+    lateral faces are periodic (reading: with a blockage of 1/50 the walls
+    are 25 D away; Zou-He faces meeting walls are not supported).  The
+    cylinder sits 12.5 D behind the inlet on the centre line; nu = U D / Re;
+    the fluid starts uniform at the inflow velocity."""
+    n = int(round(50 * diameter))
+    nu = u_in * diameter / Re
+    m = max(8, int(round(math.pi * diameter)))
+    X0, ds = cylinder_markers(diameter, m)
+    body = {"X0": X0, "ds": ds, "hinge": (0.0, 0.0, 0.0), "axis": (0.0, 0.0, 1.0),
+            "origin": (12.5 * diameter, 0.5 * n, 0.0),
+            "A": {"kind": WAVE_CONST, "amp": 0.0, "offset": 0.0},
+            "alpha": {"kind": WAVE_CONST, "amp": 0.0, "offset": 0.0},
+            "beta": 0.0, "phi": 0.0, "f": 0.0, "J": 0.0}
+    return {"lattice": 9, "tau": 3.0 * nu + 0.5,
+            "grid": grid(n, n, 1, [VEL_INLET, PRESS_OUTLET, PERIODIC, PERIODIC, PERIODIC, PERIODIC],
+                         u_in=(u_in, 0.0, 0.0), precision=precision),
+            "bodies": [body], "rho0": 1.0, "u0": (u_in, 0.0, 0.0),
+            "reference": {"U_ref": u_in, "L": diameter, "rho_ref": 1.0}}
+
+
 def clap_fling_3d(nx=256, ny=192, nz=160, chord=20.0, Re=100.0, J=1e-2, period=4000.0,
                   precision="fp32", spacing=1.0, span_ratio=5.0, hinge_x=None,
                   gap_ratio=0.5, alpha_kind=WAVE_ABS_SIN, phase=0.0, faces="inlet-outlet"):
