@@ -998,11 +998,12 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
 }
 
 // Preconditioned CG on G w = B, three right-hand sides (velocity components)
-// at once, two grid barriers per iteration.  A p is updated by the
-// recurrence A p = G z + beta A p_old, so the FP64 SpMV reads z only and
-// no direction is recomputed by its neighbours; r - alpha A p is formed in
-// FP32 inside the preconditioner product.  Row l belongs to one warp of
-// block l mod gridDim, which spreads the FP64 work over all SMs.
+// at once, two grid barriers per iteration, vectors and scalars in
+// double-float.  A p is updated by the recurrence A p = G z + beta A p_old,
+// so the SpMV reads z only and no direction is recomputed by its
+// neighbours; r - alpha A p is formed in FP32 inside the preconditioner
+// product.  SpMV rows go to warps in groups of four (8 lanes per row),
+// preconditioner rows in pairs (2p, 2p + 1), pair p to block p mod gridDim.
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) float sm[];
