@@ -65,3 +65,29 @@ def test_create_without_gpu_reports_cuda_error(ibl):
     with pytest.raises(ibl.IblError) as e:
         ibl.Context({"nx": 8, "ny": 8, "nz": 8, "bc": [0] * 6}, 0.8, 19)
     assert e.value.status in (ibl.IBL_ECUDA, ibl.IBL_ENOMEM)
+
+
+def test_null_context_calls_are_einval(ibl):
+    """Every call that takes a context answers NULL with IBL_EINVAL (no GPU
+    needed: the check comes before any device work)."""
+    import ctypes as C
+    lib = C.CDLL(ibl.LIB_PATH)
+    d = C.c_double()
+    i32 = C.c_int32()
+    calls = [
+        lambda: lib.ibl_step(None, C.c_int64(1)),
+        lambda: lib.ibl_sync(None),
+        lambda: lib.ibl_set_overlap(None, C.c_int32(1)),
+        lambda: lib.ibl_solver_blocks(None, C.c_int32(8)),
+        lambda: lib.ibl_solver_config(None, C.c_int32(64), C.c_double(0.0), C.c_int32(1)),
+        lambda: lib.ibl_profile(None, C.c_int32(1)),
+        lambda: lib.ibl_profile_phases(None, C.byref(d), C.c_int32(1)),
+        lambda: lib.ibl_mass(None, C.byref(d)),
+        lambda: lib.ibl_mass_noalloc(None, C.c_int32(16), C.byref(d)),
+        lambda: lib.ibl_interpolate_points(None, C.c_int32(1), None, None, None),
+        lambda: lib.ibl_spread_points(None, C.c_int32(1), None, None, None, None),
+        lambda: lib.ibl_forces(None, C.c_int32(0), C.byref(d), C.byref(d), C.byref(d)),
+        lambda: lib.ibl_solver_stats(None, C.byref(i32), C.byref(d), None),
+    ]
+    for call in calls:
+        assert call() == ibl.IBL_EINVAL
