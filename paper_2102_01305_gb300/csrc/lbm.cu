@@ -18,13 +18,26 @@ namespace ibl {
 
 // Velocity correction du of a cell from the band's fixed-point spreading sums
 // (Eq. 15), zero elsewhere; the sums are cleared for the next step.
-template <class R>
+// Tile extents as compile-time constants of the lattice (16 x 4 x 4 in 3D,
+// 16 x 16 in 2D), so that the lookups below are shifts and masks.
+template <int Q> struct TileDim {
+  static constexpr int X = TILE_X;
+  static constexpr int Y = Lat<Q>::D == 3 ? TILE_Y : TILE_CELLS / TILE_X;
+  static constexpr int Z = Lat<Q>::D == 3 ? TILE_Z3 : 1;
+};
+
+template <int Q, class R>
+__device__ __forceinline__ int tile_index(int x, int y, int z, const FluidParams<R>& p) {
+  using TD = TileDim<Q>;
+  return ((z / TD::Z) * p.tg.nty + (y / TD::Y)) * p.tg.ntx + (x / TD::X);
+}
+
+template <int Q, class R>
 __device__ __forceinline__ int band_du(int x, int y, int z, const FluidParams<R>& p, R du[3]) {
-  const TileGeom& t = p.tg;
-  const int tile = ((z / t.tz) * t.nty + (y / t.ty)) * t.ntx + (x / t.tx);
-  const int slot = p.tile_slot[tile];
+  using TD = TileDim<Q>;
+  const int slot = p.tile_slot[tile_index<Q, R>(x, y, z, p)];
   if (slot < 0) return -1;
-  const int local = ((z % t.tz) * t.ty + (y % t.ty)) * t.tx + (x % t.tx);
+  const int local = ((z % TD::Z) * TD::Y + (y % TD::Y)) * TD::X + (x % TD::X);
   unsigned long long* a = p.band_acc + (long long)slot * 3 * TILE_CELLS + local;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -152,7 +165,7 @@ __device__ __forceinline__ void collide_cell(const DirPtrs<Q, T>& P, const Fluid
   R F[3];
   R du[3] = {R(0), R(0), R(0)};
   int band = -1;
-  if (IB) band = band_du<R>(x, y, z, p, du);
+  if (IB) band = band_du<Q, R>(x, y, z, p, du);
   const R drho = collide<Q, R>(g, F, du, p);
   if (!(drho > R(-1) && drho < R(99))) atomicOr(p.status, ST_DIVERGED);
 #pragma unroll
@@ -184,17 +197,25 @@ constexpr int BULK_THREADS = 1024;
 template <int Q, class T, bool PULL>
 __global__ void __launch_bounds__(BULK_THREADS, 1) k_collide_bulk(DirPtrs<Q, T> P,
                                                                    FluidParams<typename Store<T>::R> p) {
+  using R = typename Store<T>::R;
   const int ux = (p.nx + 63) >> 6, uy = (p.ny + 15) >> 4;
-  const int units = ux * uy * p.nz;
   const int lx = threadIdx.x & 63, ly = threadIdx.x >> 6;
-  const TileGeom& t = p.tg;
-  for (int u = blockIdx.x; u < units; u += gridDim.x) {
-    const int bx = u % ux, r = u / ux;
-    const int x = ((bx) << 6) + lx, y = ((r % uy) << 4) + ly, z = r / uy;
-    if (x >= p.nx || y >= p.ny) continue;
-    const int tile = ((z / t.tz) * t.nty + (y / t.ty)) * t.ntx + (x / t.tx);
-    if (p.tile_slot[tile] >= 0) continue;
-    collide_cell<Q, T, PULL, false>(P, p, x, y, z);
+  // unit u = blockIdx.x + k gridDim.x walked as (bx, by, z) with carries
+  // instead of three divisions per unit
+  const int G = gridDim.x;
+  const int gx = G % ux, gy = (G / ux) % uy, gz = G / (ux * uy);
+  int bx = blockIdx.x % ux, by = (blockIdx.x / ux) % uy, z = blockIdx.x / (ux * uy);
+  while (z < p.nz) {
+    const int x = (bx << 6) + lx, y = (by << 4) + ly;
+    if (x < p.nx && y < p.ny && p.tile_slot[tile_index<Q, R>(x, y, z, p)] < 0)
+      collide_cell<Q, T, PULL, false>(P, p, x, y, z);
+    bx += gx;
+    int carry = bx >= ux;
+    bx -= carry ? ux : 0;
+    by += gy + carry;
+    carry = by >= uy;
+    by -= carry ? uy : 0;
+    z += gz + carry;
   }
 }
 
