@@ -299,7 +299,8 @@ ibl_status ibl_profile(ibl_ctx* ctx, int32_t enable);
  * 1 band counters reset, 2 tile marking, 3 slot assignment (which also
  * resets the previous band), 4 marker lists,
  * 5 interpolation and system assembly (one kernel; 6 is kept for the
- * assembly and reads 0), 7 implicit solve, 8 spreading,
+ * assembly and reads 0), 7 implicit solve and spreading (one kernel; 8 is
+ * kept for the spreading and reads 0),
  * 9 collision (the band tiles' kernel in a split step; the bulk collide on
  * the second stream is in ibl_profile_read).  Each phase is the time from
  * the end of the previous one, so launch gaps are included.  Synchronises. */

@@ -20,7 +20,7 @@
 //                    dense per-body approximate inverse as preconditioner,
 //                    rebuilt in-kernel (blocked Gauss-Jordan) every few hundred
 //                    steps;
-//   k_spread_scatter du(x) = sum_l w_l D(x - X_l) (Eq. 15) into 64-bit
+//   (end of k_pcg)   du(x) = sum_l w_l D(x - X_l) (Eq. 15) into 64-bit
 //                    fixed-point band accumulators (order-independent sums);
 //                    the collide kernel forms F = 2 rho du (Eq. 26) from them;
 //   (end of k_pcg)   F_w = -sum_l 2 rho_l w_l per body in FP64, fixed order.
@@ -455,6 +455,40 @@ __global__ void __launch_bounds__(256) k_interp_assemble(int nb_interp, int m_to
 }
 
 // ------------------------------------------------------------------ PCG with in-kernel preconditioner rebuild
+// One (marker, stencil node) term of the spreading du(x) = sum_l w_l D(x - X_l)
+// (Eq. 15) into 64-bit fixed-point band accumulators: integer addition is
+// associative, so the sums are bitwise independent of the order the atomics
+// land in.  Item gid = marker * nodes + node.
+constexpr double FIX_LIMIT = 9.0e18 / FIX_SCALE;   // |sum| < 1.3e5 at 2^46, resolution 1.4e-14
+__device__ __forceinline__ void spread_node(long long gid, int m_total, const int* __restrict__ base,
+                                            const df* __restrict__ wts, const df* __restrict__ wsol,
+                                            const int* __restrict__ tile_slot, const Geo& g,
+                                            unsigned long long* __restrict__ acc, int* status) {
+  const int nn = g.D == 3 ? 64 : 16;
+  const int l = (int)(gid / nn), k = (int)(gid % nn);
+  if (l >= m_total) return;
+  const int* b = base + 3 * l;
+  const df* w = wts + 12 * l;
+  const int i = k & 3, j = (k >> 2) & 3, q = k >> 4;
+  int node[3] = {b[0] + i, b[1] + j, g.D == 3 ? b[2] + q : 0};
+  for (int a = 0; a < g.D; ++a)
+    if (g.per[a]) node[a] = wrap(node[a], g.n[a]);
+  df wt = df_mul(w[i], w[4 + j]);
+  if (g.D == 3) wt = df_mul(wt, w[8 + q]);
+  const int s = tile_slot[tile_of(g, node[0], node[1], node[2])];
+  if (s < 0) return;
+  const int local = ((node[2] % g.tg.tz) * g.tg.ty + (node[1] % g.tg.ty)) * g.tg.tx + (node[0] % g.tg.tx);
+  unsigned long long* a3 = acc + (long long)s * 3 * TILE_CELLS + local;
+  for (int c = 0; c < g.D; ++c) {
+    // the double-float product in fixed point: both parts scale exactly by
+    // 2^46 and round to integers separately (error <= 1 unit of 2^-46)
+    const df v = df_mul(wt, wsol[3 * l + c]);
+    if (!(fabsf(v.hi) < (float)FIX_LIMIT)) { atomicOr(status, ST_OVERFLOW); continue; }
+    const long long fx = __float2ll_rn(v.hi * (float)FIX_SCALE) + __float2ll_rn(v.lo * (float)FIX_SCALE);
+    atomicAdd(a3 + c * TILE_CELLS, (unsigned long long)fx);
+  }
+}
+
 constexpr int PCG_THREADS = 1024;
 constexpr int TRACE_SLOTS = 256;
 constexpr int TRACE_PER_IT = 9;   // phase marks per traced iteration, from slot 8
@@ -496,6 +530,12 @@ struct PcgArgs {
   int refresh;      // host-scheduled rebuild
   int* status;
   unsigned long long* trace;   // optional phase timestamps (ns), see ibl_solver_trace
+  // spreading of the solution at the end of the solve (Eq. 15)
+  const int* base;
+  const df* wts;
+  const int* tile_slot;
+  unsigned long long* acc;
+  Geo geo;
   // body-force reduction after the solve (Sec. 3.7)
   const double* rho_l;
   double* mforce;
@@ -1314,6 +1354,13 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   // F_w = -sum_l 2 rho_l w_l (Eq. 26 x ds, Sec. 3.7): block b reduces body b in
   // a fixed order (lane-strided FP64 sums, fixed shuffle tree, warp order)
   for (int i = gtid; i < 3 * m; i += nthreads) A.w[i] = df_to_double(A.wd[i]);
+  // every block left the loop after the same barrier: the whole solution is
+  // final, so the spreading runs here instead of in a kernel of its own
+  {
+    const long long tot = (long long)m * (A.geo.D == 3 ? 64 : 16);
+    for (long long gi = gtid; gi < tot; gi += nthreads)
+      spread_node(gi, m, A.base, A.wts, A.wd, A.tile_slot, A.geo, A.acc, A.status);
+  }
   for (int b = blockIdx.x; b < A.nbodies; b += gridDim.x) {
     double v[3] = {0, 0, 0};
     for (int l = A.boff[b] + threadIdx.x; l < A.boff[b + 1]; l += blockDim.x)
@@ -1339,42 +1386,6 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     A.info[2] = done ? 1 : 0;
     *A.res = rel;
     if (!done) atomicOr(A.status, ST_NOTCONV);
-  }
-}
-
-// ------------------------------------------------------------------ spreading and force density
-// du(x) = sum_l w_l D(x - X_l) (Eq. 15, w_l = du_B^l ds_l) as a scatter from
-// each marker's 64 (16 in 2D) stencil nodes into 64-bit fixed-point
-// accumulators of the band: integer addition is associative, so the sums
-// are bitwise independent of the order the atomics land in.
-constexpr double FIX_LIMIT = 9.0e18 / FIX_SCALE;   // |sum| < 1.3e5 at 2^46, resolution 1.4e-14
-
-__global__ void k_spread_scatter(int m_total, const int* __restrict__ base, const df* __restrict__ wts,
-                                 const df* __restrict__ wsol, const int* __restrict__ tile_slot, Geo g,
-                                 unsigned long long* __restrict__ acc, int* status) {
-  const int nn = g.D == 3 ? 64 : 16;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int l = (int)(gid / nn), k = (int)(gid % nn);
-  if (l >= m_total) return;
-  const int* b = base + 3 * l;
-  const df* w = wts + 12 * l;
-  const int i = k & 3, j = (k >> 2) & 3, q = k >> 4;
-  int node[3] = {b[0] + i, b[1] + j, g.D == 3 ? b[2] + q : 0};
-  for (int a = 0; a < g.D; ++a)
-    if (g.per[a]) node[a] = wrap(node[a], g.n[a]);
-  df wt = df_mul(w[i], w[4 + j]);
-  if (g.D == 3) wt = df_mul(wt, w[8 + q]);
-  const int s = tile_slot[tile_of(g, node[0], node[1], node[2])];
-  if (s < 0) return;
-  const int local = ((node[2] % g.tg.tz) * g.tg.ty + (node[1] % g.tg.ty)) * g.tg.tx + (node[0] % g.tg.tx);
-  unsigned long long* a3 = acc + (long long)s * 3 * TILE_CELLS + local;
-  for (int c = 0; c < g.D; ++c) {
-    // the double-float product in fixed point: both parts scale exactly by
-    // 2^46 and round to integers separately (error <= 1 unit of 2^-46)
-    const df v = df_mul(wt, wsol[3 * l + c]);
-    if (!(fabsf(v.hi) < (float)FIX_LIMIT)) { atomicOr(status, ST_OVERFLOW); continue; }
-    const long long fx = __float2ll_rn(v.hi * (float)FIX_SCALE) + __float2ll_rn(v.lo * (float)FIX_SCALE);
-    atomicAdd(a3 + c * TILE_CELLS, (unsigned long long)fx);
   }
 }
 
@@ -1823,6 +1834,11 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   c->precond_valid = true;
   A.status = c->d_status;
   A.trace = c->d_trace;
+  A.base = c->d_base;
+  A.wts = reinterpret_cast<const df*>(c->d_wts);
+  A.tile_slot = c->d_tile_slot;
+  A.acc = c->d_acc;
+  A.geo = g;
   A.rho_l = c->d_rho_l;
   A.mforce = c->d_mforce;
   A.hist = c->d_hist;
@@ -1839,16 +1855,7 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   c->launches++;
   c->warm = true;
   c->warm_steps++;
-  // spreading: fixed-point scatter (the collision forms F = 2 rho du)
-  {
-    const int nn = c->D == 3 ? 64 : 16;
-    const long long tot = (long long)m * nn;
-  k_spread_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(m, c->d_base, reinterpret_cast<const df*>(c->d_wts),
-                                                                            reinterpret_cast<const df*>(c->d_p) + 3 * (size_t)m,
-                                                                            c->d_tile_slot, g, c->d_acc, c->d_status);
-    c->launches++;
-  }
-  phase_mark(c, 8);
+  phase_mark(c, 8);   // the spreading runs at the end of the solve
   IBL_CU(cudaGetLastError());
   return cudaSuccess;
 }
