@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16dev", "bf16dev", "fp64"])
-    ap.add_argument("--workload", default="wings", choices=["wings", "tgv"],
+    ap.add_argument("--workload", default="wings", choices=["wings", "wings-large", "tgv"],
                     help="wings: the clap-and-fling wing pair (default); tgv: pure D3Q19 periodic "
                          "Taylor-Green vortex, u0=0.05, tau=0.6 (roofline sweep)")
     ap.add_argument("--size", type=int, default=256, help="cube edge of the tgv workload")
@@ -88,6 +88,12 @@ def workload(precision="fp32", scale=1.0, kind="wings", size=256):
     n = lambda v: max(8, int(round(v * scale)))
     # x-periodic box: Zou-He inlet/outlet faces at this tau (0.5126) diverge
     # within a few hundred steps on this 12.8c-long box, on the oracle and the GPU alike
+    if kind == "wings-large":
+        # 512x384x320 (63M cells), chord 40 (2 x 6283 markers), Re = 150,
+        # J = 1e-3, period 8000 steps (tau = 0.5168)
+        return W.clap_fling_3d(nx=n(512), ny=n(384), nz=n(320), chord=max(4.0, round(40.0 * scale)),
+                               Re=150.0, J=1e-3, period=8000.0 * scale, precision=precision,
+                               faces="periodic")
     cfg = W.clap_fling_3d(nx=n(256), ny=n(192), nz=n(160), chord=max(4.0, round(20.0 * scale)),
                           precision=precision, faces="periodic")
     return cfg
@@ -103,13 +109,21 @@ def describe(cfg, steps):
                 "steps_timed": steps,
                 "l2": ("no flush: populations exceed L2" if g["nx"] ** 3 * 152 > 129e6
                        else "populations fit in L2 (small cube): numbers include L2 reuse")}
+    prm = cfg.get("params", {})
+    elem = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2}[g["precision"]]
+    buf_mb = g["nx"] * g["ny"] * g["nz"] * 19 * elem / 1e6
+    period = 1.0 / prm["f"] if prm.get("f") else float("nan")
+    chord = cfg["bodies"][0]["hinge"][0] * 2
+    Re = prm["u_tip"] * chord / prm["nu"] if prm.get("nu") else float("nan")
+    J = prm["u_inf"] / prm["u_tip"] if prm.get("u_tip") else float("nan")
     return {"workload": (f"3D clap-and-fling wing pair, D3Q19 {g['precision'].upper()}, "
                          f"{g['nx']}x{g['ny']}x{g['nz']} cells, 2 elliptic wings c={cfg['bodies'][0]['hinge'][0]*2:g} "
-                         f"span 5c ({m[0]}+{m[1]} markers), Re=100, J=1e-2 (uniform initial free stream, periodic box), "
-                         f"period 4000 steps"),
+                         f"span 5c ({m[0]}+{m[1]} markers), Re={Re:.4g}, "
+                         f"J={J:.3g} (uniform initial free stream, periodic box), "
+                         f"period {period:g} steps"),
             "cells": g["nx"] * g["ny"] * g["nz"], "markers": sum(m), "tau": round(cfg["tau"], 6),
             "steps_timed": steps,
-            "l2": "no flush: every step streams 2 x 597 MB of populations, > 129 MB L2"}
+            "l2": f"no flush: every step streams 2 x {buf_mb:.0f} MB of populations, > 129 MB L2"}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -350,14 +364,16 @@ def run_ours(args):
     per_launch_s = collide_ms / max(nprof, 1) * 1e-3
     alg_bytes = bytes_per_cell * cells
     achieved = alg_bytes / per_launch_s / 1e9
-    split = bool(cfg["bodies"]) and (args.overlap == 1 or (args.overlap == -1 and cells >= (1 << 20)))
+    nmark = sum(len(b["ds"]) for b in cfg["bodies"])
+    split = bool(cfg["bodies"]) and (args.overlap == 1 or (args.overlap == -1 and cells >= (1 << 20)
+                                                           and nmark <= 8192))
     # the recorded traffic belongs to the wing workload's FP32 split-step kernels
     rec = (traffic_record(source_hash())
            if (args.precision == "fp32" and args.workload == "wings" and split and not args.solver_blocks)
            else None)
     if split:
         sms = torch.cuda.get_device_properties(0).multi_processor_count
-        pcg_blocks = min(args.solver_blocks or sms // 2, sms)
+        pcg_blocks = min(args.solver_blocks or (sms // 2 if nmark <= 8192 else sms), sms)
         kernel = (f"k_collide_bulk + k_collide_band (split step: the bulk collide runs on the "
                   f"{sms - pcg_blocks} of {sms} SMs the solve leaves free, concurrently with the IB chain)")
     else:

@@ -262,8 +262,8 @@ ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_resid
 ibl_status ibl_solver_config(ibl_ctx* ctx, int32_t refresh_every, double tol, int32_t extrapolate);
 
 /* Thread blocks (one per SM, 1024 threads) of the cooperative implicit
- * solve; 0 (default) = half the SMs, larger values are capped at the SM
- * count.  The block count fixes the solve's reduction order: runs with the
+ * solve; 0 (default) = half the SMs (all of them above 8192 markers unless
+ * the split is forced), larger values are capped at the SM count.  The block count fixes the solve's reduction order: runs with the
  * same count are bitwise reproducible. */
 ibl_status ibl_solver_blocks(ibl_ctx* ctx, int32_t blocks);
 
@@ -271,7 +271,7 @@ ibl_status ibl_solver_blocks(ibl_ctx* ctx, int32_t blocks);
  * cells after the IB chain; 1 = split: the cells outside the IB band collide
  * on a second stream while the IB chain (interpolation, solve, spreading)
  * runs, and the band tiles collide after the spreading; -1 (default) =
- * split on grids of at least 2^20 cells.  Both give bitwise the same
+ * split on grids of at least 2^20 cells with at most 8192 markers.  Both give bitwise the same
  * populations and forces (every cell runs the same arithmetic). */
 ibl_status ibl_set_overlap(ibl_ctx* ctx, int32_t mode);
 

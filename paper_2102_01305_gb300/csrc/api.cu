@@ -357,7 +357,8 @@ ibl_status ibl_step(ibl_ctx* c, int64_t n) {
   const bool with_ib = c->m_total > 0;
   // split step: the cells outside the IB band collide on a second stream
   // while the IB chain runs; the band tiles collide after the spreading
-  const bool split = with_ib && (c->overlap == 1 || (c->overlap < 0 && c->N >= (1LL << 20)));
+  const bool split = with_ib && (c->overlap == 1 || (c->overlap < 0 && c->N >= (1LL << 20) &&
+                                                     c->m_total <= SPLIT_MAX_MARKERS));
   if (split) {
     s = ensure_split(c);
     if (s != IBL_OK) return s;

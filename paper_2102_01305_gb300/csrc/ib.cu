@@ -823,11 +823,10 @@ constexpr int GT = 128;                 // output tile edge (GT x GJ_NB = 2048 f
 constexpr int GS = GT + 4;              // padded shared-memory row
 constexpr int GJ_PS = GJ_NB + 1;        // padded row of the pivot block
 constexpr size_t GJ_SMEM = sizeof(float) * 2 * GJ_NB * GS;
-// dynamic shared memory of the solve kernel: the rebuild's tiles or, during
-// the iterations, one staged FP32 vector of all bodies (up to 24k markers)
-constexpr size_t PCG_SMEM = 96 * 1024;
-// upper bound of the dynamic shared memory (227 KB per block, less the
-// kernel's static shared memory)
+// dynamic shared memory of the solve kernel: the rebuild's tiles, then one
+// staged FP32 vector of all bodies (up to ~19k markers) and, when they fit,
+// the block's preconditioner rows; at most 224 KB (227 KB per block, less
+// the kernel's static shared memory)
 constexpr size_t PCG_SMEM_MAX = 224 * 1024;
 
 // out[i0+r][j0+c] = (acc ? out : 0) + alpha * sum_q A[r][q] B[q][j0+c] over one
@@ -1437,7 +1436,8 @@ static void keep_in_l2(ibl_ctx* c, const void* ptr, size_t bytes) {
   if (max_persist <= 0 || max_window <= 0) return;
   size_t cur = 0;
   cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
-  const size_t want = std::min<size_t>(bytes, (size_t)max_persist);
+  // at most 64 MB: a larger set-aside starves the collide's streaming
+  const size_t want = std::min<size_t>(std::min<size_t>(bytes, (size_t)max_persist), (size_t)64 << 20);
   if (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
     cudaGetLastError();
     return;
@@ -1655,10 +1655,13 @@ void phase_mark(ibl_ctx* c, int phase) {
 }
 
 // Blocks of the cooperative solve: by default half the SMs (the other half
-// runs the bulk collide concurrently when the step is split), fixed per
-// context so that the solve's reduction order does not depend on the split.
+// runs the bulk collide concurrently when the step is split), all of them for
+// marker sets too large to split for (the solve then dominates the step);
+// fixed per context so that the solve's reduction order does not depend on
+// the schedule.
 int pcg_block_count(const ibl_ctx* c) {
-  const int want = c->pcg_blocks > 0 ? c->pcg_blocks : num_sms() / 2;
+  const bool half = c->overlap == 1 || c->m_total <= SPLIT_MAX_MARKERS;
+  const int want = c->pcg_blocks > 0 ? c->pcg_blocks : (half ? num_sms() / 2 : num_sms());
   return std::max(1, std::min(std::min(std::min(want, num_sms()), MAX_PCG_BLOCKS), c->m_total));
 }
 
@@ -1810,9 +1813,9 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   // input, both FP32) and, when they fit, this block's preconditioner rows
   const int pcg_blocks = pcg_block_count(c);
   {
-    // vectors larger than PCG_SMEM are read from L2 instead of being staged
+    // vectors larger than the shared memory are read from L2 instead of being staged
     size_t stage = std::max<size_t>((size_t)3 * m * sizeof(float), (size_t)A.vtotal * sizeof(float));
-    stage = std::max(std::min((stage + 15) & ~(size_t)15, PCG_SMEM), GJ_SMEM);
+    stage = std::max(std::min((stage + 15) & ~(size_t)15, PCG_SMEM_MAX), GJ_SMEM);
     int slot = 0;
     for (int b = 0; b < A.nbodies; ++b) slot = std::max(slot, precond_ld(c->bodies[b].m));
     const size_t rows = 2 * (((size_t)(m + 1) / 2 + pcg_blocks - 1) / pcg_blocks);   // whole row pairs

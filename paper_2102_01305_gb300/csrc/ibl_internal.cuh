@@ -200,6 +200,10 @@ cudaError_t ib_step_back(ibl_ctx* c);     // interpolation .. solve .. spreading
 int num_sms();
 void phase_mark(ibl_ctx* c, int phase);   // ibl_profile level 2 only
 int pcg_block_count(const ibl_ctx* c);
+// Marker count up to which the step is split automatically: beyond it the
+// solve (dense per-body preconditioner, m^2 per iteration) dominates and
+// gets every SM.
+constexpr int SPLIT_MAX_MARKERS = 8192;
 cudaError_t launch_force_field(ibl_ctx* c, double* d_out);
 
 }  // namespace ibl
