@@ -346,6 +346,21 @@ def run_ours(args):
         trace = pcg_trace_summary(tr, iters)
     cl = (ctx.ibl_forces(0, allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
           if status == "ok" and cfg["bodies"] else None)
+    rebuild_us = None
+    if status == "ok" and cfg["bodies"]:
+        # after the timed region: one more step with a forced preconditioner
+        # rebuild, to report what a rebuild costs at this size
+        ctx.ibl_solver_config(1, 0.0, 1)
+        ctx.ibl_step(1)
+        ctx.ibl_sync(allow=(ibl.IBL_ENOTCONV,))
+        tr1 = ctx.ibl_solver_trace(allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
+        if tr1[0] and tr1[1]:
+            rebuild_us = {"total": round((tr1[1] - tr1[0]) / 1e3, 1)}
+            if tr1[4] and tr1[7] and tr1[4] > tr1[0]:
+                # first pivot block: assembly + pivot inversion, row panel,
+                # rank-64 update of the rest, column panel
+                rebuild_us["first_pivot_block"] = [round((tr1[4] - tr1[0]) / 1e3, 1)] + [
+                    round((tr1[j] - tr1[j - 1]) / 1e3, 1) for j in range(5, 8)]
     ctx.close()
 
     ms, value = aggregate_over_ranks(ms, cells, args.steps, WORLD, dist if WORLD > 1 else None, "cuda")
@@ -371,9 +386,10 @@ def run_ours(args):
     rec = (traffic_record(source_hash())
            if (args.precision == "fp32" and args.workload == "wings" and split and not args.solver_blocks)
            else None)
+    half_sms = args.overlap == 1 or nmark <= 8192     # the solve's default share of the SMs
     if split:
         sms = torch.cuda.get_device_properties(0).multi_processor_count
-        pcg_blocks = min(args.solver_blocks or (sms // 2 if nmark <= 8192 else sms), sms)
+        pcg_blocks = min(args.solver_blocks or (sms // 2 if half_sms else sms), sms)
         kernel = (f"k_collide_bulk + k_collide_band (split step: the bulk collide runs on the "
                   f"{sms - pcg_blocks} of {sms} SMs the solve leaves free, concurrently with the IB chain)")
     else:
@@ -420,11 +436,13 @@ def run_ours(args):
                 "config": describe(cfg, args.steps) | {"parallelism": f"replicas x{WORLD}",
                                                        "collide_schedule": {-1: "automatic", 0: "single kernel",
                                                                             1: "split"}[args.overlap],
-                                                       "solver_blocks": args.solver_blocks or "half the SMs"},
+                                                       "solver_blocks": args.solver_blocks or (
+                                                           "half the SMs" if half_sms else "all SMs")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "status": status, "serving_sample": serving,
                 "solver": {"pcg_iterations_last_step": iters, "rel_residual_last_step": res,
-                           "preconditioner_rebuilds": refreshes, "trace_last_step": trace},
+                           "preconditioner_rebuilds": refreshes, "trace_last_step": trace,
+                           "rebuild_us_forced": rebuild_us},
                 "C_L_last_step_body0": cl[0] if cl else None}
         if phases:
             line["phase_ms_per_step"] = phases

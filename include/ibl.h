@@ -247,14 +247,18 @@ ibl_status ibl_spread_points(ibl_ctx* ctx, int32_t m, const double* d_X, const d
 ibl_status ibl_lattice_velocities(int32_t lattice, int32_t* q, int32_t* c, double* w);
 
 /* Solver statistics of the last completed step: PCG iterations and the final
- * relative residual of the implicit IB system; preconditioner refresh count. */
+ * relative residual of the implicit IB system; number of preconditioner
+ * rebuilds so far (scheduled ones plus early ones after a slow solve). */
 ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_residual,
                             int64_t* refreshes);
 
 /* Settings of the implicit IB solve (preconditioned conjugate gradients on
  * the system of Eqs. 18-19): the dense FP32 approximate inverse used as
- * preconditioner is rebuilt every refresh_every steps (default 384) and
- * early when a solve needed more than 40 iterations; tol is the relative
+ * preconditioner is rebuilt every refresh_every steps (default 384).  It is
+ * also rebuilt early after a solve that did not converge, or once the
+ * iterations spent beyond 40 and beyond the first solve after the last
+ * rebuild, summed over the solves since, pass the rebuild's cost in
+ * iterations (sum 2 m_b^3 / sum 6 m_b^2, at least 64).  tol is the relative
  * residual in the preconditioner's norm (0 = default: 1e-10 for FP64
  * storage, 1e-7 for FP32, 1e-6 for FP16/BF16); extrapolate != 0 starts each solve from
  * 2 w_{n-1} - w_{n-2} instead of w_{n-1} (default on).  Changing these

@@ -581,7 +581,7 @@ ibl_status ibl_solver_stats(ibl_ctx* c, int32_t* iterations, double* rel_residua
   }
   if (iterations) *iterations = info[0];
   if (rel_residual) *rel_residual = res;
-  if (refreshes) *refreshes = c->refreshes;
+  if (refreshes) *refreshes = c->refreshes + info[3];
   return s;
 }
 

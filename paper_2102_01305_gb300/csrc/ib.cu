@@ -44,7 +44,19 @@ constexpr double PCG_TOL = 1e-10;       // FP64
 constexpr double PCG_TOL_FP32 = 1e-7;   // FP32 deviations
 constexpr double PCG_TOL_HALF = 1e-6;   // FP16 / BF16 deviations
 
-constexpr int REFRESH_ITERS = 40;  // rebuild early if a solve needed more
+// Early rebuilds follow a rent-or-buy rule.  Since the last rebuild, every
+// solve adds to a running excess the iterations it needed beyond both the
+// first solve after that rebuild and REBUILD_ITERS_OK (below that count,
+// the iteration count varies with the flow more than with the
+// preconditioner's age).  When the excess passes the rebuild's cost in
+// iterations, the next solve rebuilds first.  That cost is the ratio of the
+// operation counts: 2 m_b^3 for an inverse, and 6 m_b^2 for one iteration's
+// preconditioner product over three right-hand sides.  Each is summed over
+// the bodies, and the ratio is floored at REBUILD_MIN_EXCESS.  Only
+// iteration counts enter the rule, so runs stay reproducible bit for bit.
+// A solve that does not converge asks for a rebuild directly.
+constexpr int REBUILD_MIN_EXCESS = 64;
+constexpr int REBUILD_ITERS_OK = 40;
 
 struct BodyTable {
   int n;
@@ -523,7 +535,9 @@ struct PcgArgs {
   float* Bf;
   float* M;
   df* red;          // [gridDim][8] partials
-  int* info;        // [0] iterations, [1] rebuild request, [2] converged flag
+  int* info;        // [0] iterations, [1] rebuild request, [2] converged flag, [3] early rebuilds,
+                    // [4] iterations of the first solve after the last rebuild, [5] excess since
+  int rebuild_excess;   // rebuild cost in iterations (early-rebuild threshold)
   double* res;      // final relative residual
   double tol;
   int warm;
@@ -1060,6 +1074,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   trace_mark(A, 0);
   const bool rebuild = A.refresh || A.info[1];
   if (rebuild) {
+    if (gtid == 0 && !A.refresh) A.info[3] += 1;   // early rebuilds (a slow previous solve)
     for (int b = 0; b < A.nbodies; ++b) {
       const int mb = A.boff[b + 1] - A.boff[b];
       const long long tot = (long long)mb * precond_ld(mb);
@@ -1381,7 +1396,13 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     for (int c = 0; c < A.D; ++c)
       if (s_scale[c].hi > 0.f) rel = fmax(rel, sqrt(fmax(df_to_double(s_rz[c]), 0.0) / df_to_double(s_scale[c])));
     A.info[0] = it;
-    A.info[1] = (it > REFRESH_ITERS || !done) ? 1 : 0;
+    if (rebuild) {
+      A.info[4] = it;
+      A.info[5] = 0;
+    } else {
+      A.info[5] = min(A.info[5] + max(it - max(A.info[4], REBUILD_ITERS_OK), 0), 1 << 30);
+    }
+    A.info[1] = (A.info[5] > A.rebuild_excess || !done) ? 1 : 0;
     A.info[2] = done ? 1 : 0;
     *A.res = rel;
     if (!done) atomicOr(A.status, ST_NOTCONV);
@@ -1517,8 +1538,8 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   IBL_CU(cudaMalloc(&c->d_M, sizeof(float) * mf));
   keep_in_l2(c, c->d_M, sizeof(float) * mf);
   IBL_CU(cudaMalloc(&c->d_red, sizeof(double) * 8 * 1024));
-  IBL_CU(cudaMalloc(&c->d_cg_info, sizeof(int) * 4));
-  IBL_CU(cudaMemsetAsync(c->d_cg_info, 0, sizeof(int) * 4, c->stream));
+  IBL_CU(cudaMalloc(&c->d_cg_info, sizeof(int) * 8));
+  IBL_CU(cudaMemsetAsync(c->d_cg_info, 0, sizeof(int) * 8, c->stream));
   IBL_CU(cudaMalloc(&c->d_cg_res, sizeof(double)));
   IBL_CU(cudaMemsetAsync(c->d_cg_res, 0, sizeof(double), c->stream));
   IBL_CU(cudaMalloc(&c->d_hist, sizeof(double) * 3 * (size_t)HIST_LEN * c->bodies.size()));
@@ -1827,6 +1848,15 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   A.tol = c->solver_tol > 0 ? c->solver_tol
                              : (c->prec == IBL_FP64 ? PCG_TOL : (c->prec == IBL_FP32 ? PCG_TOL_FP32 : PCG_TOL_HALF));
   A.M = c->d_M; A.red = reinterpret_cast<df*>(c->d_red); A.info = c->d_cg_info; A.res = c->d_cg_res;
+  {
+    double cube = 0, square = 0;
+    for (int b = 0; b < A.nbodies; ++b) {
+      const double mb = c->bodies[b].m;
+      cube += 2 * mb * mb * mb;
+      square += 6 * mb * mb;
+    }
+    A.rebuild_excess = (int)std::min(std::max(cube / std::max(square, 1.0), (double)REBUILD_MIN_EXCESS), 1e8);
+  }
   A.warm = c->warm_steps >= 2 && c->extrapolate ? 2 : (c->warm_steps >= 1 ? 1 : 0);
   const bool sched = !c->precond_valid || (c->step - c->last_refresh_step) >= c->refresh_every;
   A.refresh = sched ? 1 : 0;

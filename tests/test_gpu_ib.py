@@ -189,3 +189,23 @@ def test_split_step_full_size_bitwise(ibl):
     u0 = ctx0.ibl_get_field(ibl.IBL_FIELD_U)
     u1 = ctx1.ibl_get_field(ibl.IBL_FIELD_U)
     assert np.array_equal(u0, u1)
+
+
+def test_early_rebuilds_reproducible(ibl):
+    """With scheduled rebuilds off, only the early-rebuild rule (iteration
+    excess over the rebuild's cost in iterations) refreshes the fast-moving
+    wing pair's preconditioner; the rule depends on iteration counts only, so
+    two runs rebuild at the same steps and give bitwise the same forces."""
+    cfg = _small_wings("fp32")
+    out = []
+    for _ in range(2):
+        ctx = ibl.from_workload(cfg)
+        ctx.ibl_solver_config(100000, 0.0, 1)
+        ctx.ibl_step(400)
+        it, res, rebuilds = ctx.ibl_solver_stats()
+        out.append((rebuilds, ctx.ibl_force_history(0, 400), ctx.ibl_force_history(1, 400)))
+        ctx.close()
+    print(f"early rebuilds over 400 steps: {out[0][0] - 1}")
+    assert out[0][0] == out[1][0] and out[0][0] >= 1
+    assert res < 1e-6
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
