@@ -843,12 +843,15 @@ constexpr size_t GJ_SMEM = sizeof(float) * 2 * GJ_NB * GS;
 // the kernel's static shared memory)
 constexpr size_t PCG_SMEM_MAX = 224 * 1024;
 
+// Both routines below are compiled as separate functions: inlined into the
+// solve kernel, which runs at 64 registers a thread, the tile product's
+// accumulators spilled to local memory.
 // out[i0+r][j0+c] = (acc ? out : 0) + alpha * sum_q A[r][q] B[q][j0+c] over one
 // tile (r < nr, c < nc), skipping output rows in [sk0, sk1) and columns in
 // [ck0, ck1).  Ag points at the tile's first A row; Bg at B's row 0 (its
 // columns are absolute).  Inputs are staged in shared memory before any
 // output is written, so out may alias A or B within the tile.
-__device__ void tile_gemm(float* out, int ldo, const float* Ag, int lda, const float* Bg, int ldb, int i0,
+__device__ __noinline__ void tile_gemm(float* out, int ldo, const float* Ag, int lda, const float* Bg, int ldb, int i0,
                           int j0, int nr, int nc, int K, float alpha, bool acc, int sk0, int sk1, int ck0,
                           int ck1, float* sm) {
   float* As = sm;               // [q][r], GJ_NB x GS
@@ -908,15 +911,28 @@ __device__ void tile_gemm(float* out, int ldo, const float* Ag, int lda, const f
       for (int u = 0; u < 4; ++u)
         for (int v = 0; v < 4; ++v) a4[u][v] = fmaf(ar[u], br[v], a4[u][v]);
     }
+    // the thread's four output groups: when they are whole columns outside
+    // the skipped range, all four are read before any is written (the
+    // compiler cannot reorder loads and stores through the same pointer)
+    const int c0 = 4 * tx, jj = j0 + c0;
+    const bool whole = c0 + 3 < nc && (jj + 3 < ck0 || jj >= ck1);
+    float4 prev[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = 4 * ty + u, i = i0 + r;
+      prev[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (acc && whole && r < nr && !(i >= sk0 && i < sk1))
+        prev[u] = *reinterpret_cast<const float4*>(out + (long long)i * ldo + jj);
+    }
+#pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int r = 4 * ty + u, i = i0 + r;
       if (r >= nr || (i >= sk0 && i < sk1)) continue;
-      const int c0 = 4 * tx, jj = j0 + c0;
       float* o = out + (long long)i * ldo + jj;
       // four whole columns outside the skipped range: one 128-bit access
       // (ldo and the tile origins are multiples of 4 floats)
-      if (c0 + 3 < nc && (jj + 3 < ck0 || jj >= ck1)) {
-        float4 ov = acc ? *reinterpret_cast<float4*>(o) : make_float4(0.f, 0.f, 0.f, 0.f);
+      if (whole) {
+        float4 ov = prev[u];
         ov.x += alpha * a4[u][0];
         ov.y += alpha * a4[u][1];
         ov.z += alpha * a4[u][2];
@@ -933,7 +949,16 @@ __device__ void tile_gemm(float* out, int ldo, const float* Ag, int lda, const f
   }
 }
 
-__device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
+// Tiles of all bodies are dealt to the blocks round-robin in body order:
+// with `done` tiles of earlier bodies dealt, this block's first tile of the
+// next body is the smallest t >= 0 with (done + t) mod gridDim = blockIdx
+// (t may exceed the body's count).
+__device__ __forceinline__ int first_tile(int done) {
+  const int t = (int)blockIdx.x - done % (int)gridDim.x;
+  return t < 0 ? t + (int)gridDim.x : t;
+}
+
+__device__ __noinline__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
   int maxnb = 0;
   for (int b = 0; b < A.nbodies; ++b) {
     const int mb = A.boff[b + 1] - A.boff[b];
@@ -999,12 +1024,12 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
         const int kn = min(GJ_NB, mb - k0), ld = precond_ld(mb);
         float* Mb = A.M + A.poff[b];
         const int nt = (mb + GT - 1) / GT;
-        for (int t = 0; t < nt; ++t, ++done) {
-          if (done % gridDim.x != blockIdx.x) continue;
+        for (int t = first_tile(done); t < nt; t += gridDim.x) {
           const int j0 = t * GT;
           tile_gemm(Mb, ld, Mb + (long long)k0 * ld + k0, ld, Mb + (long long)k0 * ld, ld, k0, j0, kn,
                     min(GT, mb - j0), kn, 1.0f, false, -1, -1, k0, k0 + kn, sm);
         }
+        done += nt;
       }
     }
     grid.sync();
@@ -1018,12 +1043,12 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
         const int kn = min(GJ_NB, mb - k0), ld = precond_ld(mb);
         float* Mb = A.M + A.poff[b];
         const int nt = (mb + GT - 1) / GT;
-        for (int t = 0; t < nt * nt; ++t, ++done) {
-          if (done % gridDim.x != blockIdx.x) continue;
+        for (int t = first_tile(done); t < nt * nt; t += gridDim.x) {
           const int i0 = (t / nt) * GT, j0 = (t % nt) * GT;
           tile_gemm(Mb, ld, Mb + (long long)i0 * ld + k0, ld, Mb + (long long)k0 * ld, ld, i0, j0,
                     min(GT, mb - i0), min(GT, mb - j0), kn, -1.0f, true, k0, k0 + kn, k0, k0 + kn, sm);
         }
+        done += nt * nt;
       }
     }
     grid.sync();
@@ -1037,12 +1062,12 @@ __device__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, float* sm) {
         const int kn = min(GJ_NB, mb - k0), ld = precond_ld(mb);
         float* Mb = A.M + A.poff[b];
         const int nt = (mb + GT - 1) / GT;
-        for (int t = 0; t < nt; ++t, ++done) {
-          if (done % gridDim.x != blockIdx.x) continue;
+        for (int t = first_tile(done); t < nt; t += gridDim.x) {
           const int i0 = t * GT;
           tile_gemm(Mb, ld, Mb + (long long)i0 * ld + k0, ld, Mb + (long long)k0 * ld, ld, i0, k0,
                     min(GT, mb - i0), kn, kn, -1.0f, false, k0, k0 + kn, -1, -1, sm);
         }
+        done += nt;
       }
     }
     grid.sync();
