@@ -70,6 +70,8 @@ def parse():
                     help="collide scheduling: -1 automatic, 0 one kernel after the IB chain, 1 split")
     ap.add_argument("--solver-blocks", type=int, default=0, help="blocks of the implicit solve (0: default)")
     ap.add_argument("--phases", action="store_true", help="also time every phase of the step (events)")
+    ap.add_argument("--initial-guess", choices=("extrapolated", "previous", "zero"), default="extrapolated",
+                    help="initial guess of each implicit solve")
     ap.add_argument("--refresh-every", type=int, default=0,
                     help="steps between preconditioner rebuilds (0: the library default)")
     ap.add_argument("--ib-sweep", action="store_true",
@@ -306,8 +308,9 @@ def run_ours(args):
     ctx = ibl.from_workload(cfg)
     ctx.ibl_set_overlap(args.overlap)
     ctx.ibl_solver_blocks(args.solver_blocks)
-    if args.refresh_every:
-        ctx.ibl_solver_config(args.refresh_every, 0.0, 1)
+    guess = {"extrapolated": True, "previous": False, "zero": None}[args.initial_guess]
+    if args.refresh_every or args.initial_guess != "extrapolated":
+        ctx.ibl_solver_config(args.refresh_every or 384, 0.0, guess)
     ctx.ibl_step(args.warmup)
     ctx.ibl_sync(allow=(ibl.IBL_ENOTCONV,))
     stream = torch.cuda.ExternalStream(ctx.ibl_stream())
@@ -350,7 +353,7 @@ def run_ours(args):
     if status == "ok" and cfg["bodies"]:
         # after the timed region: one more step with a forced preconditioner
         # rebuild, to report what a rebuild costs at this size
-        ctx.ibl_solver_config(1, 0.0, 1)
+        ctx.ibl_solver_config(1, 0.0, guess)
         ctx.ibl_step(1)
         ctx.ibl_sync(allow=(ibl.IBL_ENOTCONV,))
         tr1 = ctx.ibl_solver_trace(allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))

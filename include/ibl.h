@@ -260,9 +260,10 @@ ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_resid
  * rebuild, summed over the solves since, pass the rebuild's cost in
  * iterations (sum 2 m_b^3 / sum 6 m_b^2, at least 64).  tol is the relative
  * residual in the preconditioner's norm (0 = default: 1e-10 for FP64
- * storage, 1e-7 for FP32, 1e-6 for FP16/BF16); extrapolate != 0 starts each solve from
- * 2 w_{n-1} - w_{n-2} instead of w_{n-1} (default on).  Changing these
- * changes the iterates, not the system being solved. */
+ * storage, 1e-7 for FP32, 1e-6 for FP16/BF16).  extrapolate chooses each
+ * solve's initial guess: > 0 (default 1) 2 w_{n-1} - w_{n-2}, 0 w_{n-1},
+ * < 0 zero.  Changing these changes the iterates, not the system being
+ * solved. */
 ibl_status ibl_solver_config(ibl_ctx* ctx, int32_t refresh_every, double tol, int32_t extrapolate);
 
 /* Thread blocks (one per SM, 1024 threads) of the cooperative implicit

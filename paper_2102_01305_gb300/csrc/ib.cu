@@ -1480,10 +1480,14 @@ static void keep_in_l2(ibl_ctx* c, const void* ptr, size_t bytes) {
   cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
   cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
   if (max_persist <= 0 || max_window <= 0) return;
+  // at most 64 MB: a larger set-aside starves the collide's streaming; a
+  // matrix larger than that is left to stream from HBM (a partial window
+  // saves the solve less than the smaller L2 costs the collide)
+  const size_t cap = std::min<size_t>((size_t)max_persist, (size_t)64 << 20);
+  if (bytes > cap) return;
   size_t cur = 0;
   cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize);
-  // at most 64 MB: a larger set-aside starves the collide's streaming
-  const size_t want = std::min<size_t>(std::min<size_t>(bytes, (size_t)max_persist), (size_t)64 << 20);
+  const size_t want = bytes;
   if (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
     cudaGetLastError();
     return;
@@ -1882,7 +1886,7 @@ cudaError_t ib_step_back(ibl_ctx* c) {
     }
     A.rebuild_excess = (int)std::min(std::max(cube / std::max(square, 1.0), (double)REBUILD_MIN_EXCESS), 1e8);
   }
-  A.warm = c->warm_steps >= 2 && c->extrapolate ? 2 : (c->warm_steps >= 1 ? 1 : 0);
+  A.warm = c->extrapolate < 0 ? 0 : (c->warm_steps >= 2 && c->extrapolate ? 2 : (c->warm_steps >= 1 ? 1 : 0));
   const bool sched = !c->precond_valid || (c->step - c->last_refresh_step) >= c->refresh_every;
   A.refresh = sched ? 1 : 0;
   if (sched) {

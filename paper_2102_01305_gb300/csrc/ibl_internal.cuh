@@ -146,7 +146,7 @@ struct ibl_ctx {
   bool precond_valid = false;
   bool warm = false;             // d_w holds the previous solution
   long long warm_steps = 0;      // consecutive solves behind d_w (2+: extrapolate)
-  bool extrapolate = true;
+  int extrapolate = 1;            // initial guess: 1 extrapolated, 0 last solution, -1 zero
   int refresh_every = 384;       // steps between scheduled preconditioner rebuilds
   double solver_tol = 0.0;       // 0: default for the storage precision
   int pcg_blocks = 0;            // blocks of the cooperative solve (0: half the SMs)

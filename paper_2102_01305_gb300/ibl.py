@@ -387,7 +387,9 @@ class Context:
         return it.value, res.value, ref.value
 
     def ibl_solver_config(self, refresh_every=384, tol=0.0, extrapolate=True):
-        _check(self.h, _lib.ibl_solver_config(self.h, int(refresh_every), float(tol), 1 if extrapolate else 0))
+        """extrapolate: True (2 w_n-1 - w_n-2), False (w_n-1) or None (zero)."""
+        mode = -1 if extrapolate is None else (1 if extrapolate else 0)
+        _check(self.h, _lib.ibl_solver_config(self.h, int(refresh_every), float(tol), mode))
 
     def ibl_solver_trace(self, allow=()):
         out = np.zeros(256, dtype=np.int64)
