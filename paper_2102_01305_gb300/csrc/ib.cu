@@ -835,7 +835,6 @@ __device__ __forceinline__ void precond_pair(const PcgArgs& A, int p, const floa
 // routine (128 x 128 output tiles, 4 x 4 outputs per thread, K <= GJ_NB).
 constexpr int GT = 128;                 // output tile edge (GT x GJ_NB = 2048 float4 groups)
 constexpr int GS = GT + 4;              // padded shared-memory row
-constexpr int GJ_PS = GJ_NB + 1;        // padded row of the pivot block
 constexpr size_t GJ_SMEM = sizeof(float) * 2 * GJ_NB * GS;
 // dynamic shared memory of the solve kernel: the rebuild's tiles, then one
 // staged FP32 vector of all bodies (up to ~19k markers) and, when they fit,
@@ -949,6 +948,45 @@ __device__ __noinline__ void tile_gemm(float* out, int ldo, const float* Ag, int
   }
 }
 
+// In-place inverse of the kn x kn pivot block at (k0, k0) of Mb (row stride
+// ld) by threads 0..127 of the block; buf holds 2 x GJ_NB floats of shared
+// memory.
+__device__ __noinline__ void pivot_block_invert(float* Mb, int ld, int k0, int kn, float* buf) {
+  const int i = threadIdx.x >> 1, h = threadIdx.x & 1, lane = threadIdx.x & 31;
+  float a[32];
+#pragma unroll
+  for (int jj = 0; jj < 32; ++jj) {
+    const int j = 32 * h + jj;
+    a[jj] = (i < kn && j < kn) ? Mb[(long long)(k0 + i) * ld + k0 + j] : (i == j ? 1.f : 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < GJ_NB; ++k) {
+    float* rowk = buf + (k & 1) * GJ_NB;
+    if (i == k) {
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) rowk[32 * h + jj] = a[jj];
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const float pk = 1.0f / rowk[k];
+    // element (i, k) lives in the thread of half k / 32 of row i
+    const float ci = __shfl_sync(0xffffffffu, a[k & 31], (lane & ~1) | (k >> 5));
+    const float* rh = rowk + 32 * h;
+    if (i == k) {
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) a[jj] = rh[jj] * pk;
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) a[jj] = fmaf(-ci, rh[jj] * pk, a[jj]);
+    }
+    if (h == (k >> 5)) a[k & 31] = i == k ? pk : -ci * pk;
+  }
+#pragma unroll
+  for (int jj = 0; jj < 32; ++jj) {
+    const int j = 32 * h + jj;
+    if (i < kn && j < kn) Mb[(long long)(k0 + i) * ld + k0 + j] = a[jj];
+  }
+}
+
 // Tiles of all bodies are dealt to the blocks round-robin in body order:
 // with `done` tiles of earlier bodies dealt, this block's first tile of the
 // next body is the smallest t >= 0 with (done + t) mod gridDim = blockIdx
@@ -966,52 +1004,21 @@ __device__ __noinline__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, f
   }
   for (int kb = 0; kb < maxnb; ++kb) {
     const int k0 = kb * GJ_NB;
-    // phase 1: invert the pivot block of body b in block b (Gauss-Jordan in
-    // shared memory): 64 sequential pivots, so 4 warps with a named barrier
-    // do it (a block-wide barrier over 32 warps per pivot costs more than
-    // the arithmetic); rows padded to GJ_PS floats so that a warp's 16 rows
-    // fall in different banks
+    // phase 1: invert the pivot block of body b in block b by Gauss-Jordan:
+    // 64 sequential pivots, so 4 warps with a named barrier do it (a
+    // block-wide barrier over 32 warps per pivot costs more than the
+    // arithmetic).  Thread t holds half a row in registers (row t / 2,
+    // columns 32 (t % 2) ...), the pivot loop is unrolled so that every
+    // register index is static, and the pivot row goes through one of two
+    // shared-memory buffers (one barrier per pivot).  A ragged last block is
+    // padded with the identity, whose pivots leave the kn x kn part alone.
     for (int b = blockIdx.x; b < A.nbodies; b += gridDim.x) {
       const int mb = A.boff[b + 1] - A.boff[b];
       if (k0 >= mb) continue;
       const int kn = min(GJ_NB, mb - k0), ld = precond_ld(mb);
       float* Mb = A.M + A.poff[b];
-      float* piv = sm;                    // kn x GJ_PS
-      float* rowk = sm + GJ_NB * GJ_PS;   // pivot row and column copies
-      float* colk = rowk + GJ_NB;
+      if (threadIdx.x < 2 * GJ_NB) pivot_block_invert(Mb, ld, k0, kn, sm);
       __syncthreads();
-      for (int e = threadIdx.x; e < kn * kn; e += blockDim.x)
-        piv[(e / kn) * GJ_PS + e % kn] = Mb[(long long)(k0 + e / kn) * ld + k0 + e % kn];
-      __syncthreads();
-      if (threadIdx.x < 128) {
-        const int i = threadIdx.x >> 1, j0 = (threadIdx.x & 1) * 32;
-        for (int k = 0; k < kn; ++k) {
-          if (threadIdx.x < kn) {
-            rowk[threadIdx.x] = piv[k * GJ_PS + threadIdx.x];
-            colk[threadIdx.x] = piv[threadIdx.x * GJ_PS + k];
-          }
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-          const float pk = 1.0f / rowk[k];
-          if (i < kn) {
-            const float ci = colk[i];
-            float* prow = piv + i * GJ_PS;
-            for (int jj = 0; jj < 32; ++jj) {
-              const int j = j0 + jj;
-              if (j >= kn) break;
-              float v;
-              if (i == k && j == k) v = pk;
-              else if (i == k) v = rowk[j] * pk;
-              else if (j == k) v = -ci * pk;
-              else v = prow[j] - ci * rowk[j] * pk;
-              prow[j] = v;
-            }
-          }
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-        }
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < kn * kn; e += blockDim.x)
-        Mb[(long long)(k0 + e / kn) * ld + k0 + e % kn] = piv[(e / kn) * GJ_PS + e % kn];
     }
     grid.sync();
     if (kb == 0) trace_mark(A, 4);
