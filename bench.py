@@ -349,6 +349,17 @@ def run_ours(args):
         trace = pcg_trace_summary(tr, iters)
     cl = (ctx.ibl_forces(0, allow=(ibl.IBL_ENOTCONV, ibl.IBL_EDIVERGED))
           if status == "ok" and cfg["bodies"] else None)
+    # host cost of enqueueing a step (the launch queue starts empty, so the
+    # calls do not block on the device): compared with the device time per
+    # step, it says whether the step is launch-bound
+    host_us = None
+    if status == "ok":
+        ctx.ibl_sync(allow=(ibl.IBL_ENOTCONV,))
+        ctx.ibl_profile(0)
+        t0 = time.perf_counter()
+        ctx.ibl_step(16)
+        host_us = round((time.perf_counter() - t0) / 16 * 1e6, 1)
+        ctx.ibl_sync(allow=(ibl.IBL_ENOTCONV,))
     rebuild_us = None
     if status == "ok" and cfg["bodies"]:
         # after the timed region: one more step with a forced preconditioner
@@ -443,6 +454,7 @@ def run_ours(args):
                                                            "half the SMs" if half_sms else "all SMs")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "status": status, "serving_sample": serving,
+                "host_enqueue_us_per_step": host_us,
                 "solver": {"pcg_iterations_last_step": iters, "rel_residual_last_step": res,
                            "preconditioner_rebuilds": refreshes, "trace_last_step": trace,
                            "rebuild_us_forced": rebuild_us},

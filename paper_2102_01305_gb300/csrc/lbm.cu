@@ -178,6 +178,94 @@ __device__ __forceinline__ void collide_cell(const DirPtrs<Q, T>& P, const Fluid
   }
 }
 
+// ---------------------------------------------------------------- 16-bit storage: two cells per thread
+// With 2-byte populations one cell per thread keeps too few bytes in flight
+// to cover HBM latency (the kernel then runs at ~0.56 of the bandwidth
+// bound).  Here a thread takes the x-adjacent cells (x, x + 1), x even and nx
+// even.  Directions with c_x = 0 read both sources as one aligned 32-bit
+// pair, the others as two 16-bit loads.  All 2Q loads are issued before the
+// first collision, and the stores go out as 32-bit pairs.  Each cell still
+// runs collide() on the same values, so the populations are bitwise those of
+// the one-cell kernels.
+template <class T> struct __align__(4) Pair16 {
+  T a, b;
+};
+
+template <int Q, class T, class R>
+__device__ __forceinline__ void gather_pair(const DirPtrs<Q, T>& P, int x, int y, int z, const FluidParams<R>& p,
+                                            R ga[Q], R gb[Q]) {
+  // sources x - 1 .. x + 2 (x + 1 < nx since x is even and nx even)
+  int xs[4] = {x - 1, x, x + 1, x + 2};
+  if (xs[0] < 0) xs[0] += p.nx;
+  if (xs[3] >= p.nx) xs[3] -= p.nx;
+  int ys[3] = {y - 1, y, y + 1};
+  if (ys[0] < 0) ys[0] += p.ny;
+  if (ys[2] >= p.ny) ys[2] -= p.ny;
+  int zs[3] = {z - 1, z, z + 1};
+  if (Lat<Q>::D == 3) {
+    if (zs[0] < 0) zs[0] += p.nz;
+    if (zs[2] >= p.nz) zs[2] -= p.nz;
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int dy = 1 - Lat<Q>::cy(i), dz = 1 - Lat<Q>::cz(i);
+    const int row = (zs[dz] * p.ny + ys[dy]) * p.nx;
+    if (Lat<Q>::cx(i) == 0) {
+      const Pair16<T> v = *reinterpret_cast<const Pair16<T>*>(P.s[i] + row + x);
+      ga[i] = Store<T>::ld(v.a);
+      gb[i] = Store<T>::ld(v.b);
+    } else {
+      const int dx = 1 - Lat<Q>::cx(i);
+      ga[i] = Store<T>::ld(P.s[i][row + xs[dx]]);
+      gb[i] = Store<T>::ld(P.s[i][row + xs[dx + 1]]);
+    }
+  }
+}
+
+// Band correction, collision and divergence check of one cell (the part of
+// collide_cell between the pull and the store).
+template <int Q, bool IB, class R>
+__device__ __forceinline__ void collide_only(R g[Q], const FluidParams<R>& p, int x, int y, int z) {
+  R F[3];
+  R du[3] = {R(0), R(0), R(0)};
+  int band = -1;
+  if (IB) band = band_du<Q, R>(x, y, z, p, du);
+  const R drho = collide<Q, R>(g, F, du, p);
+  if (!(drho > R(-1) && drho < R(99))) atomicOr(p.status, ST_DIVERGED);
+  if (IB && band >= 0) {
+    p.band_F[band] = F[0] - p.G[0];
+    p.band_F[band + TILE_CELLS] = F[1] - p.G[1];
+    p.band_F[band + 2 * TILE_CELLS] = F[2] - p.G[2];
+  }
+}
+
+// Every cell of a grid with even nx: 128 x 4 cells per 256-thread block.
+template <int Q, class T, bool IB>
+__global__ void __launch_bounds__(256, 3) k_collide_pairs(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p) {
+  using R = typename Store<T>::R;
+  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= p.nx || y >= p.ny) return;
+  if (on_special_face<R>(x, y, z, Lat<Q>::D, p) || on_special_face<R>(x + 1, y, z, Lat<Q>::D, p)) {
+    collide_cell<Q, T, true, IB>(P, p, x, y, z);
+    collide_cell<Q, T, true, IB>(P, p, x + 1, y, z);
+    return;
+  }
+  R ga[Q], gb[Q];
+  gather_pair<Q, T, R>(P, x, y, z, p, ga, gb);
+  collide_only<Q, IB, R>(ga, p, x, y, z);
+  collide_only<Q, IB, R>(gb, p, x + 1, y, z);
+  const int cell = (z * p.ny + y) * p.nx + x;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    Pair16<T> v;
+    v.a = Store<T>::st(ga[i]);
+    v.b = Store<T>::st(gb[i]);
+    *reinterpret_cast<Pair16<T>*>(P.d[i] + cell) = v;
+  }
+}
+
 // Every cell, 64 x 4 cells per block; IB selects the band lookup.
 template <int Q, class T, bool PULL, bool IB>
 __global__ void __launch_bounds__(256) k_collide(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p) {
@@ -377,6 +465,16 @@ cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
   auto p = make_params<R>(c, with_ib);
   const DirPtrs<Q, T> P = dir_ptrs<Q, T>(c);
   dim3 b = cell_block(c), g = cell_grid(c, b);
+  if constexpr (sizeof(T) == 2) {
+    if (!c->poststream && c->nx % 2 == 0) {
+      // 16-bit storage: two x-adjacent cells per thread
+      g.x = (c->nx / 2 + b.x - 1) / b.x;
+      if (with_ib) k_collide_pairs<Q, T, true><<<g, b, 0, c->stream>>>(P, p);
+      else k_collide_pairs<Q, T, false><<<g, b, 0, c->stream>>>(P, p);
+      c->launches++;
+      return cudaGetLastError();
+    }
+  }
   if (c->poststream) {
     if (with_ib) k_collide<Q, T, false, true><<<g, b, 0, c->stream>>>(P, p);
     else k_collide<Q, T, false, false><<<g, b, 0, c->stream>>>(P, p);

@@ -158,13 +158,16 @@ def _run_mode(ibl, cfg, mode, steps):
     return out
 
 
-@pytest.mark.parametrize("case", ["wings_fp32", "cylinder_fp64"])
+@pytest.mark.parametrize("case", ["wings_fp32", "wings_fp16dev", "wings_bf16dev", "cylinder_fp64"])
 def test_split_step_is_bitwise_identical(ibl, case):
     """The split step (cells outside the IB band collide on a second stream
     while the IB chain runs; band tiles collide after the spreading) gives
-    bitwise the populations and forces of one collide kernel after the chain."""
-    if case == "wings_fp32":
-        cfg, steps = _small_wings("fp32"), 120
+    bitwise the populations and forces of one collide kernel after the chain.
+    With 16-bit storage and even nx the single kernel takes two cells per
+    thread, so this also pins it to the one-cell kernels of the split step."""
+    if case.startswith("wings_"):
+        cfg, steps = _small_wings(case.split("_")[1]), 120
+        assert cfg["grid"]["nx"] % 2 == 0
     else:
         cfg, steps = W.cylinder_channel(), 200
     a = _run_mode(ibl, cfg, 0, steps)

@@ -44,9 +44,9 @@ def test_wings_reduced_precision(ibl, wings_oracle, prec):
     assert eu < tol_u and worst < tol_c
 
 
+@pytest.mark.parametrize("n", [(40, 36, 34), (41, 36, 34)])   # even nx: two cells per thread
 @pytest.mark.parametrize("prec", ["fp16dev", "bf16dev"])
-def test_tgv_reduced_precision(ibl, prec):
-    n = (40, 36, 34)
+def test_tgv_reduced_precision(ibl, prec, n):
     base = {"lattice": 19, "tau": 0.6, "bodies": [], "u_field": W.tgv3d_velocity(*n, 0.05)}
     sim = oracle_from_workload(dict(base, grid=W.grid(*n, [W.PERIODIC] * 6)))
     sim.step(600)
