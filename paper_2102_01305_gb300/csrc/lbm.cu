@@ -239,9 +239,11 @@ __device__ __forceinline__ void collide_only(R g[Q], const FluidParams<R>& p, in
   }
 }
 
-// Every cell of a grid with even nx: 128 x 4 cells per 256-thread block.
+// Every cell of a grid with even nx: 128 x 4 cells per 256-thread block;
+// four blocks per SM (64 registers) where that does not spill, three with
+// the band lookup.
 template <int Q, class T, bool IB>
-__global__ void __launch_bounds__(256, 3) k_collide_pairs(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p) {
+__global__ void __launch_bounds__(256, IB ? 3 : 4) k_collide_pairs(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p) {
   using R = typename Store<T>::R;
   const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
