@@ -19,7 +19,7 @@ def _declared():
     return sorted(set(re.findall(r"\b(ibl_[a-z_0-9]+)\s*\(", src)))
 
 
-def test_header_declares_the_survey_calls():
+def test_header_declares_the_core_calls():
     names = _declared()
     for must in ["ibl_create", "ibl_set_markers", "ibl_set_kinematics", "ibl_step", "ibl_forces",
                  "ibl_destroy", "ibl_get_field", "ibl_force_history", "ibl_last_error"]:
