@@ -206,10 +206,10 @@ ibl_status ibl_get_markers(ibl_ctx* ctx, int32_t body_id, double* X, double* U, 
 ibl_status ibl_mass(ibl_ctx* ctx, double* mass);
 
 /* Same total as ibl_mass, for callers that must not allocate device memory
- * after start-up: a solver embedded in a real-time control loop, code whose
- * device memory is fully claimed by another allocator (a framework's caching
- * allocator), or work recorded inside a CUDA stream capture, where cudaMalloc
- * is not allowed.  ibl_mass allocates its partial sums per call; this call
+ * after start-up: a solver embedded in a real-time control loop, where a
+ * cudaMalloc can block for an unbounded time, or code whose device memory is
+ * fully claimed by another allocator (a framework's caching allocator), where
+ * a cudaMalloc fails.  ibl_mass allocates its partial sums per call; this call
  * allocates nothing: its partials live in a static device array of 4096
  * doubles (32 KB), which every GPU that loads the library holds until the
  * process exits.  The paper has no counterpart of this call.

@@ -1,8 +1,9 @@
 """The allocation-free mass entry point against ibl_mass (GPU).
 
 ibl_mass_noalloc serves callers that may not allocate device memory after
-start-up (real-time loops, fully claimed device memory, stream capture): it
-takes its partial sums from a static device array instead of cudaMalloc.
+start-up (real-time loops, where a cudaMalloc can block; device memory fully
+claimed by another allocator, where it fails): it takes its partial sums from
+a static device array instead of cudaMalloc.
 This file is collected last so that a run stopping at the first failure has
 already run every other test; it also passes alone in a fresh process.
 """
