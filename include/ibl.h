@@ -272,6 +272,15 @@ ibl_status ibl_solver_config(ibl_ctx* ctx, int32_t refresh_every, double tol, in
  * same count are bitwise reproducible. */
 ibl_status ibl_solver_blocks(ibl_ctx* ctx, int32_t blocks);
 
+/* Preconditioner of the implicit IB solve.  kind: -1 (default) automatic,
+ * 0 the dense per-body approximate inverse (G_b + sigma I)^-1.
+ * resident_rows: -1 (default) each solve block keeps its preconditioner rows
+ * in shared memory when they fit; 0 the rows are always read from L2/HBM
+ * (the path every solve takes when they do not fit).  Both paths multiply
+ * the same FP32 rows in the same order, so they give bitwise the same
+ * results.  IBL_EINVAL for other values. */
+ibl_status ibl_solver_preconditioner(ibl_ctx* ctx, int32_t kind, int32_t resident_rows);
+
 /* How a step with markers schedules its collision: 0 = one kernel over all
  * cells after the IB chain; 1 = split: the cells outside the IB band collide
  * on a second stream while the IB chain (interpolation, solve, spreading)

@@ -414,6 +414,15 @@ ibl_status ibl_solver_blocks(ibl_ctx* c, int32_t blocks) {
   return IBL_OK;
 }
 
+ibl_status ibl_solver_preconditioner(ibl_ctx* c, int32_t kind, int32_t resident_rows) {
+  if (!c) return IBL_EINVAL;
+  if (kind < -1 || kind > 0) return fail(c, IBL_EINVAL, "preconditioner kind must be -1 or 0");
+  if (resident_rows < -1 || resident_rows > 0) return fail(c, IBL_EINVAL, "resident_rows must be -1 or 0");
+  c->precond_kind = kind;
+  c->resident_rows = resident_rows;
+  return IBL_OK;
+}
+
 ibl_status ibl_set_overlap(ibl_ctx* c, int32_t mode) {
   if (!c) return IBL_EINVAL;
   if (mode < -1 || mode > 1) return fail(c, IBL_EINVAL, "overlap mode must be -1, 0 or 1");

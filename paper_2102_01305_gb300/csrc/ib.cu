@@ -1878,7 +1878,7 @@ cudaError_t ib_step_back(ibl_ctx* c) {
     const size_t rows = 2 * (((size_t)(m + 1) / 2 + pcg_blocks - 1) / pcg_blocks);   // whole row pairs
     const size_t need = stage + rows * (size_t)slot * sizeof(float);
     A.smem_floats = (int)(stage / sizeof(float));
-    A.row_slot = need <= PCG_SMEM_MAX ? slot : 0;
+    A.row_slot = (need <= PCG_SMEM_MAX && c->resident_rows != 0) ? slot : 0;
     c->pcg_smem = A.row_slot ? need : stage;
   }
   A.tol = c->solver_tol > 0 ? c->solver_tol

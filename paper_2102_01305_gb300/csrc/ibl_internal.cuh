@@ -150,6 +150,8 @@ struct ibl_ctx {
   int refresh_every = 384;       // steps between scheduled preconditioner rebuilds
   double solver_tol = 0.0;       // 0: default for the storage precision
   int pcg_blocks = 0;            // blocks of the cooperative solve (0: half the SMs)
+  int precond_kind = -1;         // -1 automatic, 0 dense per-body inverse
+  int resident_rows = -1;        // -1 preconditioner rows in shared memory when they fit, 0 never
   size_t pcg_smem = 0;           // dynamic shared memory of the last solve launch
   double* d_wprev = nullptr;     // m x 3 solution of the previous step
   // optional per-step event timing (ibl_profile)

@@ -94,6 +94,7 @@ _SIGS = {
     "ibl_solver_stats": ([_P, _I32, _D, _I64], C.c_int),
     "ibl_solver_trace": ([_P, _I64, C.c_int32, _I32], C.c_int),
     "ibl_solver_config": ([_P, C.c_int32, C.c_double, C.c_int32], C.c_int),
+    "ibl_solver_preconditioner": ([_P, C.c_int32, C.c_int32], C.c_int),
     "ibl_profile": ([_P, C.c_int32], C.c_int),
     "ibl_profile_read": ([_P, _D, _D, _I64], C.c_int),
     "ibl_launch_count": ([_P, _I64], C.c_int),
@@ -390,6 +391,11 @@ class Context:
         """extrapolate: True (2 w_n-1 - w_n-2), False (w_n-1) or None (zero)."""
         mode = -1 if extrapolate is None else (1 if extrapolate else 0)
         _check(self.h, _lib.ibl_solver_config(self.h, int(refresh_every), float(tol), mode))
+
+    def ibl_solver_preconditioner(self, kind=-1, resident_rows=-1):
+        """kind: -1 automatic, 0 dense per-body inverse; resident_rows: -1 when
+        they fit, 0 always read from L2/HBM."""
+        _check(self.h, _lib.ibl_solver_preconditioner(self.h, int(kind), int(resident_rows)))
 
     def ibl_solver_trace(self, allow=()):
         out = np.zeros(256, dtype=np.int64)

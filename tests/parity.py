@@ -28,6 +28,27 @@ def rel_err(a, b) -> float:
     return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
 
 
+def coef_err(hist, ref) -> tuple[float, float]:
+    """Errors of a C_L / C_T history (columns 0 and 1) against the oracle's.
+
+    Each step's error is divided by that step's own force scale
+    max(|C_L|, |C_T|) of the oracle, floored at the largest scale the run
+    reaches after its start-up transient (the first max(20, n/5) steps).
+    The floor keeps steps where both coefficients cross zero from dividing
+    by ~0 (a symmetric body has C_L = 0 throughout), and leaving out the
+    impulsive start keeps its spike (several times the periodic-state
+    forces) from loosening the bound on every later step."""
+    hist = np.asarray(hist, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert hist.shape == ref.shape and len(ref) > 0
+    mag = np.maximum(np.abs(ref[:, 0]), np.abs(ref[:, 1]))
+    s0 = min(max(20, len(ref) // 5), len(ref) - 1)
+    scale = np.maximum(mag, mag[s0:].max())
+    e_l = float((np.abs(hist[:, 0] - ref[:, 0]) / scale).max())
+    e_t = float((np.abs(hist[:, 1] - ref[:, 1]) / scale).max())
+    return e_l, e_t
+
+
 def oracle_from_workload(cfg: dict, u_field=None) -> Simulation:
     sim = Simulation(cfg["lattice"], cfg["grid"], cfg["tau"])
     lat = get_lattice(cfg["lattice"])

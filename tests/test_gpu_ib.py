@@ -7,23 +7,18 @@ import numpy as np
 import pytest
 
 import workloads as W
-from tests.parity import (TOL_COEF_FP32, TOL_FIELD_FP32, TOL_FIELD_FP64, compare_fields,
+from tests.parity import (TOL_COEF_FP32, TOL_FIELD_FP32, TOL_FIELD_FP64, coef_err, compare_fields,
                           oracle_from_workload, rel_err)
 
 pytestmark = pytest.mark.gpu
 
 
 def _coef_err(ctx, sim, body, steps):
-    """Errors of the C_L and C_T histories relative to the body's force scale
-    max(|C_L|, |C_T|) over the run (a symmetric body has C_L = 0 up to rounding,
-    so a C_L-relative error would compare rounding noise with rounding noise)."""
+    """C_L and C_T errors of the last `steps` steps (per-step scale, see parity.coef_err)."""
     hist = ctx.ibl_force_history(body, steps)
     ref = np.array(sim.history[body][-len(hist):])
     assert len(hist) == min(steps, len(sim.history[body]))
-    scale = max(np.abs(ref[:, 0]).max(), np.abs(ref[:, 1]).max())
-    e_l = np.abs(hist[:, 0] - ref[:, 0]).max() / scale
-    e_t = np.abs(hist[:, 1] - ref[:, 1]).max() / scale
-    return e_l, e_t
+    return coef_err(hist[:, :2], ref[:, :2])
 
 
 def test_cylinder_channel_fp64_full_run(ibl):
@@ -76,6 +71,31 @@ def test_wings_fp64_tight(ibl):
         m = len(cfg["bodies"][b]["ds"])
         assert np.abs(X - sim.last["X"][m0:m0 + m]).max() < 1e-12
         assert np.abs(U - sim.last["U"][m0:m0 + m]).max() < 1e-15
+
+
+def test_table_wave_kinematics_fp64(ibl):
+    """Opening angles given as a table of samples per step (IBL_WAVE_TABLE):
+    positions and wall velocities (central difference of the table) on the
+    GPU equal the oracle's, and so do the fields and forces."""
+    cfg = _small_wings("fp64")
+    n = np.arange(1200)
+    table = (math.pi / 3.0) * np.abs(np.sin(2.0 * math.pi * n / 1200.0)) ** 1.5
+    for b in cfg["bodies"]:
+        b["alpha"] = {"kind": W.WAVE_TABLE, "table": table}
+    ctx = ibl.from_workload(cfg)
+    sim = oracle_from_workload(cfg)
+    ctx.ibl_step(60)
+    sim.step(60)
+    compare_fields(ctx, sim, ibl, TOL_FIELD_FP64)
+    m0 = len(cfg["bodies"][0]["ds"])
+    for b in range(2):
+        m = len(cfg["bodies"][b]["ds"])
+        X, U, _ = ctx.ibl_get_markers(b, m)
+        o = 0 if b == 0 else m0
+        assert np.abs(X - sim.last["X"][o:o + m]).max() < 1e-12
+        assert np.abs(U - sim.last["U"][o:o + m]).max() < 1e-15
+        e_l, e_t = _coef_err(ctx, sim, b, 60)
+        assert e_l < 1e-7 and e_t < 1e-7
 
 
 def test_prescribed_marker_state_and_periodic_wrap(ibl):

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from tests.parity import (TOL_COEF_FP32, TOL_FIELD_FP32, TOL_FIELD_FP64, compare_fields,
+from tests.parity import (TOL_COEF_FP32, TOL_FIELD_FP32, TOL_FIELD_FP64, coef_err, compare_fields,
                           oracle_from_workload)
 
 pytestmark = pytest.mark.gpu
@@ -46,8 +46,7 @@ def oracle_runs():
 def _coef_err(ctx, sim, body):
     hist = ctx.ibl_force_history(body, STEPS)
     ref = np.array(sim.history[body][-len(hist):])
-    scale = max(np.abs(ref[:, 0]).max(), np.abs(ref[:, 1]).max())
-    return (np.abs(hist[:, 0] - ref[:, 0]).max() / scale, np.abs(hist[:, 1] - ref[:, 1]).max() / scale)
+    return coef_err(hist[:, :2], ref[:, :2])
 
 
 @pytest.mark.parametrize("name", ["clap_fling", "figure_eight", "cylinder_50d"])

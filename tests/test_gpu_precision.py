@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from tests.parity import oracle_from_workload, rel_err
+from tests.parity import coef_err, oracle_from_workload, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -37,8 +37,7 @@ def test_wings_reduced_precision(ibl, wings_oracle, prec):
     for b in range(2):
         h = ctx.ibl_force_history(b, 600)
         ref = np.array(sim.history[b])
-        scale = max(np.abs(ref[:, 0]).max(), np.abs(ref[:, 1]).max())
-        worst = max(worst, np.abs(h[:, :2] - ref[:, :2]).max() / scale)
+        worst = max(worst, *coef_err(h[:, :2], ref[:, :2]))
     print(f"{prec} wings 600 steps: u {eu:.2e}, C_L/C_T {worst:.2e}")
     tol_u, tol_c = BOUNDS_WINGS[prec]
     assert eu < tol_u and worst < tol_c

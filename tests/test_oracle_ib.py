@@ -217,3 +217,45 @@ def test_figure_eight_kinematics():
         speeds.append(np.linalg.norm(U[0]))
     assert abs(max(speeds) - p["u_tip"]) < 1e-12
     assert abs(p["u_tip"] - math.pi * p["f"] * p["A0"]) < 1e-15
+
+
+def test_table_wave_values_and_rates():
+    """TABLE wave: value table[n mod len] at step n, rate by the central
+    difference of the neighbouring samples, wrapping at both ends.  Expected
+    values worked by hand for the table 0, 1, 4, 9, 16."""
+    w = {"kind": W.WAVE_TABLE, "table": [0.0, 1.0, 4.0, 9.0, 16.0]}
+    cases = {0: (0.0, -7.5), 1: (1.0, 2.0), 2: (4.0, 4.0), 4: (16.0, -4.5), 7: (4.0, 4.0), -1: (16.0, -4.5)}
+    for t, (v, vd) in cases.items():
+        assert kinematics.wave(w, float(t), 0.0, 0.0) == (v, vd)
+
+
+def test_table_wave_drives_the_rotation():
+    """A rotation angle given as a table turns the body by table[n mod len]
+    at step n (a marker one unit behind the hinge lands at angle pi + alpha)
+    and its wall velocity is the table's central difference times e x r."""
+    angles = [0.0, 0.1, 0.3, 0.6]
+    body = {"X0": np.array([[-1.0, 0.0, 0.0]]), "hinge": (0.0, 0.0, 0.0), "axis": (0.0, 0.0, 1.0),
+            "origin": (5.0, 6.0, 7.0), "A": {"kind": W.WAVE_CONST},
+            "alpha": {"kind": W.WAVE_TABLE, "table": angles}, "beta": 0.0, "phi": 0.0, "f": 0.0}
+    for n, (al, rate) in {1: (0.1, 0.15), 2: (0.3, 0.25), 5: (0.1, 0.15)}.items():
+        X, U = kinematics.marker_state(body, float(n), 3)
+        r = np.array([-math.cos(al), -math.sin(al), 0.0])
+        assert np.abs(X[0] - (np.array([5.0, 6.0, 7.0]) + r)).max() < 1e-15
+        assert np.abs(U[0] - rate * np.array([-r[1], r[0], 0.0])).max() < 1e-15
+
+
+def test_coefficient_normalisation_by_hand():
+    """C = F / (rho_ref U_ref^2 L / 2): with rho_ref = 0.5, U_ref = 2, L = 3
+    the dynamic-pressure scale is 3, so a body force (6, -1.5) gives
+    C_D = 2 (along +x), C_T = -2 and C_L = -0.5 along +y, +0.5 along -y."""
+    grid = W.grid(16, 16, 1, [W.PERIODIC] * 6, precision="fp64")
+    sim = Simulation(9, grid, 0.8)
+    for axis in ((0.0, 1.0, 0.0), (0.0, -1.0, 0.0)):
+        sim.add_body({"X0": np.zeros((1, 2)), "ds": np.ones(1), "hinge": (0, 0, 0), "axis": (0, 0, 1),
+                      "origin": (8.0, 8.0, 0.0), "A": {"kind": W.WAVE_CONST},
+                      "alpha": {"kind": W.WAVE_CONST}, "beta": 0.0, "phi": 0.0, "f": 0.0,
+                      "lift_axis": axis})
+    sim.set_reference(2.0, 3.0, 0.5)
+    F = np.array([6.0, -1.5])
+    assert sim.coefficients(0, F) == (-0.5, -2.0, 2.0)
+    assert sim.coefficients(1, F) == (0.5, -2.0, 2.0)
