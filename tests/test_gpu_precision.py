@@ -1,8 +1,11 @@
 """Reduced-precision storage (f - w in FP16 or BF16, collision in FP32)
 against the FP64 oracle (GPU).
 
-Bounds are the measured errors with a margin of 3-5x; the coefficient bound
-is the 1e-3 target of the reduced-precision form.  FP16 rounds each stored
+Field bounds are the measured errors with a margin of 3-5x.  Coefficient
+errors use the per-step scale of tests/parity.py (each step against its own
+force scale, floored at the largest one after the start-up); FP16 is held
+to 5e-4 (measured 1.2e-4) and BF16 to 1e-3, the C_L target of the
+reduced-precision form.  FP16 rounds each stored
 deviation to 2^-11 relative, BF16 to 2^-8, so field errors of ~1e-4..1e-3
 (FP16) and ~1e-3..1e-2 (BF16) after hundreds of steps are the arithmetic's
 own floor, not a defect."""
@@ -15,7 +18,7 @@ from tests.parity import coef_err, oracle_from_workload, rel_err
 pytestmark = pytest.mark.gpu
 
 WINGS = dict(nx=48, ny=40, nz=40, chord=6.0, Re=5.0, J=0.1, period=1200.0)
-BOUNDS_WINGS = {"fp16dev": (1e-3, 1e-4), "bf16dev": (6e-3, 1e-3)}
+BOUNDS_WINGS = {"fp16dev": (1e-3, 5e-4), "bf16dev": (6e-3, 1e-3)}
 BOUNDS_TGV = {"fp16dev": 3e-3, "bf16dev": 3e-2}
 
 
