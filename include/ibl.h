@@ -53,7 +53,9 @@ typedef enum {
   IBL_EDIVERGED = 4,   /* NaN/Inf or runaway density detected; sticky until destroy */
   IBL_ENOTCONV = 5,    /* the implicit IB solve did not reach its tolerance */
   IBL_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
-  IBL_ESTATE = 7       /* call out of order (e.g. step before the fluid is initialised) */
+  IBL_ESTATE = 7,      /* call out of order (e.g. step before the fluid is initialised) */
+  IBL_ECANCELED = 8,   /* a serving run was cancelled (ibl_server_cancel) */
+  IBL_EUNSTABLE = 9    /* a serving request lies outside the collision's stability range */
 } ibl_status;
 
 /* Lattice: D2Q9 (Sec. 2.1, Eq. 5) or D3Q19 (textbook weights 1/3, 1/18, 1/36). */
@@ -205,6 +207,23 @@ ibl_status ibl_get_markers(ibl_ctx* ctx, int32_t body_id, double* X, double* U, 
  * in a fixed order. */
 ibl_status ibl_mass(ibl_ctx* ctx, double* mass);
 
+/* Periodic FP64 mass check (failure detection).  Every `every` steps
+ * (default 500; 0 = off) ibl_step sums rho over all cells in FP64, in a fixed
+ * order, into buffers the context owns, and compares the total with the
+ * total taken when the fluid was initialised (ibl_init_fluid,
+ * ibl_set_populations).  A non-finite total or - when no face is a Zou-He
+ * inlet or outlet, so that the faces conserve mass - a relative change above
+ * rel_tol (0 = default: 1e-9 for FP64 storage, 1e-4 FP32, 1e-2 FP16/BF16)
+ * sets the sticky divergence status: the next synchronising call and every
+ * later ibl_step return IBL_EDIVERGED.  The collision kernels flag a cell
+ * whose density is non-finite or outside (0, 100) on every step as well. */
+ibl_status ibl_set_mass_check(ibl_ctx* ctx, int32_t every, double rel_tol);
+
+/* The mass check's reference total, its last checked total and the number
+ * of checks so far.  Synchronises; a divergence already flagged is returned
+ * as IBL_EDIVERGED after the values are written. */
+ibl_status ibl_mass_check_read(ibl_ctx* ctx, double* m0, double* m_last, int64_t* checks);
+
 /* Same total as ibl_mass, for callers that must not allocate device memory
  * after start-up: a solver embedded in a real-time control loop, where a
  * cudaMalloc can block for an unbounded time, or code whose device memory is
@@ -272,13 +291,26 @@ ibl_status ibl_solver_config(ibl_ctx* ctx, int32_t refresh_every, double tol, in
  * same count are bitwise reproducible. */
 ibl_status ibl_solver_blocks(ibl_ctx* ctx, int32_t blocks);
 
-/* Preconditioner of the implicit IB solve.  kind: -1 (default) automatic,
- * 0 the dense per-body approximate inverse (G_b + sigma I)^-1.
- * resident_rows: -1 (default) each solve block keeps its preconditioner rows
- * in shared memory when they fit; 0 the rows are always read from L2/HBM
- * (the path every solve takes when they do not fit).  Both paths multiply
- * the same FP32 rows in the same order, so they give bitwise the same
- * results.  IBL_EINVAL for other values. */
+/* Preconditioner of the implicit IB solve (Eqs. 18-19).  Both kinds
+ * approximate (G_b + sigma I)^-1 per body, sigma = 1e-6 times G_b's largest
+ * absolute row sum, rebuilt every refresh_every steps (ibl_solver_config):
+ *   kind 0: the dense inverse, FP32, m_b^2 numbers per body;
+ *   kind 1: separable factors, for bodies whose markers form a chord x span
+ *           product mesh (a planform grid, possibly clipped) turning about
+ *           the z axis: G_b is then a principal submatrix of a Kronecker
+ *           product C (x) Z, and its shifted inverse follows from the
+ *           factors' inverses and one Schur block over the mesh's bounding
+ *           rectangle (n_k^2 + n_k n_i^2 + n_c^2 numbers; 3D only);
+ *   kind -1 (default): kind 1 when every body qualifies and the largest has
+ *           at least 4096 markers, else kind 0.
+ * A change of kind takes effect at the next step and restarts the solver's
+ * warm start.  IBL_EINVAL at the next step if kind 1 is asked for bodies
+ * that do not qualify.
+ * resident_rows (kind 0): -1 (default) each solve block keeps its
+ * preconditioner rows in shared memory when they fit; 0 the rows are always
+ * read from L2/HBM (the path every solve takes when they do not fit).  Both
+ * paths multiply the same FP32 rows in the same order, so they give bitwise
+ * the same results.  IBL_EINVAL for other values. */
 ibl_status ibl_solver_preconditioner(ibl_ctx* ctx, int32_t kind, int32_t resident_rows);
 
 /* How a step with markers schedules its collision: 0 = one kernel over all
@@ -381,8 +413,16 @@ typedef struct {
 ibl_status ibl_server_create(const ibl_server_config* cfg, ibl_server** out);
 /* Queue a run; *run_id identifies it.  IBL_EINVAL for a malformed request or
  * wings that do not fit the box, IBL_ENOMEM if its footprint exceeds the
- * whole budget.  Thread-safe. */
+ * whole budget, IBL_EUNSTABLE if it lies outside the BGK collision's
+ * stability range (tau = 3 nu + 1/2 below 0.505, a free stream J U_tip above
+ * 0.05 or a tip speed above 0.15 lattice units), instead of diverging on the
+ * GPU.  The submission time is taken on entry.  Thread-safe. */
 ibl_status ibl_server_submit(ibl_server* s, const ibl_run_request* req, int64_t* run_id);
+/* Cancel a run: a queued run never starts; a running one stops after the
+ * chunk of steps in flight and its memory returns to the budget.  Its result
+ * then reports IBL_ECANCELED with the steps done.  No effect on a finished
+ * run; IBL_EINVAL for an unknown id.  Thread-safe. */
+ibl_status ibl_server_cancel(ibl_server* s, int64_t run_id);
 /* Snapshot of a run's progress and, once done, its result.  Thread-safe. */
 ibl_status ibl_server_poll(ibl_server* s, int64_t run_id, ibl_run_result* out);
 /* Block until no run is queued or active; IBL_ETIMEOUT after timeout_s. */

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libibl.so")
-SOURCES = ["api.cu", "lbm.cu", "ib.cu", "server.cu", "points.cu"]
+SOURCES = ["api.cu", "lbm.cu", "ib.cu", "server.cu", "points.cu", "sep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

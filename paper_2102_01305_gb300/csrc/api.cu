@@ -128,6 +128,9 @@ ibl_status ibl_create(const ibl_grid* grid, double tau, int32_t lattice, ibl_ctx
   if (e == cudaSuccess) e = cudaMalloc(&c->f[1], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_mass_parts, sizeof(double) * MASS_PARTS);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_mass_ref, sizeof(double) * 3);
+  if (e == cudaSuccess) e = cudaMemset(c->d_mass_ref, 0, sizeof(double) * 3);
   if (e != cudaSuccess) {
     ibl_status s = cuda_check(nullptr, e, "ibl_create");
     ibl_destroy(c);
@@ -150,6 +153,8 @@ ibl_status ibl_destroy(ibl_ctx* c) {
   if (c->f[0]) cudaFree(c->f[0]);
   if (c->f[1]) cudaFree(c->f[1]);
   if (c->d_status) cudaFree(c->d_status);
+  if (c->d_mass_parts) cudaFree(c->d_mass_parts);
+  if (c->d_mass_ref) cudaFree(c->d_mass_ref);
   if (c->d_pt_perm) cudaFree(c->d_pt_perm);
   if (c->d_pt_bins) cudaFree(c->d_pt_bins);
   for (auto& ev : c->stage_ev)
@@ -176,6 +181,8 @@ ibl_status ibl_init_fluid(ibl_ctx* c, const double* rho, const double* u) {
   if (e == cudaSuccess && u)
     e = cudaMemcpyAsync(d_u, u, sizeof(double) * n1 * c->D, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = launch_init_eq(c, d_rho, d_u);
+  c->poststream = true;
+  if (e == cudaSuccess) e = launch_mass_check(c, 0);   // reference total of the mass check
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   st = cuda_check(c, e, "init_fluid");
   if (d) cudaFree(d);
@@ -195,6 +202,8 @@ ibl_status ibl_set_populations(ibl_ctx* c, const double* f) {
   CK(cudaMalloc(&d, sizeof(double) * n), "set_populations alloc");
   cudaError_t e = cudaMemcpyAsync(d, f, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = launch_set_pop(c, d);
+  c->poststream = true;
+  if (e == cudaSuccess) e = launch_mass_check(c, 0);   // reference total of the mass check
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(d);
   ibl_status st = cuda_check(c, e, "set_populations");
@@ -290,6 +299,10 @@ static ibl_status ensure_split(ibl_ctx* c) {
 
 static ibl_status ensure_ib(ibl_ctx* c) {
   if (c->ib_ready || c->m_total == 0) return IBL_OK;
+  if (c->precond_kind == 1 && !sep_all_separable(c, nullptr))
+    return fail(c, IBL_EINVAL,
+                "separable preconditioner: every body needs its markers on a chord x span product mesh "
+                "rotating about the z axis (3D)");
   CK(cudaStreamSynchronize(c->stream), "sync");
   CK(ib_alloc(c), "IB buffers");
   const size_t m = c->m_total;
@@ -403,8 +416,30 @@ ibl_status ibl_step(ibl_ctx* c, int64_t n) {
     c->cur ^= 1;
     c->poststream = false;
     c->step++;
+    if (c->mass_every > 0 && c->step % c->mass_every == 0) CK(launch_mass_check(c, 1), "mass check");
   }
   return IBL_OK;
+}
+
+ibl_status ibl_set_mass_check(ibl_ctx* c, int32_t every, double rel_tol) {
+  if (!c) return IBL_EINVAL;
+  if (every < 0 || !(rel_tol >= 0.0) || !std::isfinite(rel_tol))
+    return fail(c, IBL_EINVAL, "mass check: every >= 0 and a finite rel_tol >= 0");
+  c->mass_every = every;
+  c->mass_tol = rel_tol;
+  return IBL_OK;
+}
+
+ibl_status ibl_mass_check_read(ibl_ctx* c, double* m0, double* m_last, int64_t* checks) {
+  if (!c) return IBL_EINVAL;
+  ibl_status s = sync_and_collect(c);
+  if (s != IBL_OK && s != IBL_ENOTCONV && s != IBL_EDIVERGED) return s;
+  double r[3];
+  CK(cudaMemcpy(r, c->d_mass_ref, sizeof(r), cudaMemcpyDeviceToHost), "mass check read");
+  if (m0) *m0 = r[0];
+  if (m_last) *m_last = r[1];
+  if (checks) *checks = (int64_t)r[2];
+  return s;
 }
 
 ibl_status ibl_solver_blocks(ibl_ctx* c, int32_t blocks) {
@@ -416,8 +451,13 @@ ibl_status ibl_solver_blocks(ibl_ctx* c, int32_t blocks) {
 
 ibl_status ibl_solver_preconditioner(ibl_ctx* c, int32_t kind, int32_t resident_rows) {
   if (!c) return IBL_EINVAL;
-  if (kind < -1 || kind > 0) return fail(c, IBL_EINVAL, "preconditioner kind must be -1 or 0");
+  if (kind < -1 || kind > 1) return fail(c, IBL_EINVAL, "preconditioner kind must be -1, 0 or 1");
   if (resident_rows < -1 || resident_rows > 0) return fail(c, IBL_EINVAL, "resident_rows must be -1 or 0");
+  if (kind != c->precond_kind && c->ib_ready) {
+    // the preconditioner's buffers are sized at the next step
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    c->ib_ready = false;
+  }
   c->precond_kind = kind;
   c->resident_rows = resident_rows;
   return IBL_OK;

@@ -126,6 +126,14 @@ __device__ __forceinline__ void acc_fma(dfacc& a, df x, df y) {
   a.s = t.hi;
   a.c = __fadd_rn(a.c, __fadd_rn(t.lo, e));
 }
+// a += x * y, both float: the product's rounding error enters c exactly.
+__device__ __forceinline__ void acc_fma_ff(dfacc& a, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  const float e = fmaf(x, y, -p);
+  const df t = two_sum(a.s, p);
+  a.s = t.hi;
+  a.c = __fadd_rn(a.c, __fadd_rn(t.lo, e));
+}
 __device__ __forceinline__ df acc_value(dfacc a) { return fast_two_sum(a.s, a.c); }
 
 // Butterfly sum over groups of `width` lanes in a fixed order (every lane of

@@ -30,6 +30,7 @@
 
 #include "df.cuh"
 #include "ib_stencil.cuh"
+#include "sep.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -555,6 +556,9 @@ struct PcgArgs {
   double* mforce;
   double* hist;
   long long step;
+  // separable preconditioner (all bodies) instead of the dense inverses
+  const SepBody* sep;
+  int sep_on;
 };
 
 __device__ __forceinline__ void trace_mark(const PcgArgs& A, int slot) {
@@ -1082,6 +1086,23 @@ __device__ __noinline__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, f
   }
 }
 
+// Stages A-F of the separable preconditioner (sep.cuh) for all bodies and
+// components, a grid barrier after each; stage G is done by the caller.
+__device__ void sep_front(const PcgArgs& A, cg::grid_group& grid, const SepIn& in, float* sm) {
+  sep_rowpass(A.sep, A.nbodies, 0, in, A.voff, sm);
+  grid.sync();
+  sep_colpass(A.sep, A.nbodies, false);
+  grid.sync();
+  sep_complement_values(A.sep, A.nbodies);
+  grid.sync();
+  sep_schur(A.sep, A.nbodies);
+  grid.sync();
+  sep_rowpass(A.sep, A.nbodies, 1, in, A.voff, sm);
+  grid.sync();
+  sep_colpass(A.sep, A.nbodies, true);
+  grid.sync();
+}
+
 // Preconditioned CG on G w = B, three right-hand sides (velocity components)
 // at once, two grid barriers per iteration, vectors and scalars in
 // double-float.  A p is updated by the recurrence A p = G z + beta A p_old,
@@ -1104,8 +1125,10 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
 
   // ---- optional preconditioner rebuild: M_b <- (G_b + sigma_b I)^-1 in FP32
   trace_mark(A, 0);
-  const bool rebuild = A.refresh || A.info[1];
-  if (rebuild) {
+  // the separable factors are rebuilt by their own kernel on the host's
+  // schedule only (sep_launch), so early requests apply to the dense path
+  const bool rebuild = A.refresh || (!A.sep_on && A.info[1]);
+  if (rebuild && !A.sep_on) {
     if (gtid == 0 && !A.refresh) A.info[3] += 1;   // early rebuilds (a slow previous solve)
     for (int b = 0; b < A.nbodies; ++b) {
       const int mb = A.boff[b + 1] - A.boff[b];
@@ -1196,7 +1219,38 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   grid.sync();
   // z = M r and the stopping scale B.(M B): lane c of each warp accumulates
   // component c; partials r.z (slots 3..5) and B.MB (0..2)
-  {
+  const int gwarp = blockIdx.x * PCG_WARPS + wib, nwarp_all = gridDim.x * PCG_WARPS;
+  if (A.sep_on) {
+    df rz = dzero, bb = dzero;
+    SepIn in;
+    in.a = A.rf;
+    in.b = nullptr;
+    in.s[0] = in.s[1] = in.s[2] = 0.f;
+    sep_front(A, grid, in, sm);
+    for (int l = gwarp; l < m; l += nwarp_all) {
+      const int bd = A.body_of[l];
+      float z[3];
+      sep_marker_z(A.sep[bd], l - A.boff[bd], z);
+      if (lane < 3) {
+        const float zc = lane == 0 ? z[0] : (lane == 1 ? z[1] : z[2]);
+        A.zf[3 * l + lane] = zc;
+        rz = df_add(rz, df_mul_f(A.rd[3 * l + lane], zc));
+      }
+    }
+    in.a = A.Bf;
+    sep_front(A, grid, in, sm);
+    for (int l = gwarp; l < m; l += nwarp_all) {
+      const int bd = A.body_of[l];
+      float z[3];
+      sep_marker_z(A.sep[bd], l - A.boff[bd], z);
+      if (lane < 3) {
+        const float zc = lane == 0 ? z[0] : (lane == 1 ? z[1] : z[2]);
+        bb = df_add(bb, df_mul_f(df_from_double(A.B[3 * l + lane]), zc));
+      }
+    }
+    block_partial3(bb, shdf, A.red + blockIdx.x * 8);
+    block_partial3(rz, shdf, A.red + blockIdx.x * 8 + 3);
+  } else {
     df rz = dzero, bb = dzero;
     const float zero3[3] = {0.f, 0.f, 0.f};
     const float* xs = stage_x(A, A.rf, nullptr, zero3, sm);
@@ -1345,7 +1399,37 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     __syncthreads();
     trace_mark(A, ts + 5);
     const float alphaf[3] = {s_alphaf[0], s_alphaf[1], s_alphaf[2]};
-    {
+    if (A.sep_on) {
+      // z = M (r - alpha A p) through the separable factors; then, per
+      // marker, w += alpha p, r -= alpha A p and the partial r.z
+      df rz = dzero;
+      SepIn in;
+      in.a = A.rf;
+      in.b = A.Apf;
+      in.s[0] = alphaf[0];
+      in.s[1] = alphaf[1];
+      in.s[2] = alphaf[2];
+      trace_mark(A, ts + 6);
+      sep_front(A, grid, in, sm);
+      for (int l = gwarp; l < m; l += nwarp_all) {
+        const int bd = A.body_of[l];
+        float z[3];
+        sep_marker_z(A.sep[bd], l - A.boff[bd], z);
+        if (lane < 3) {
+          const int c = lane;
+          const float zl = c == 0 ? z[0] : (c == 1 ? z[1] : z[2]);
+          const df alpha = s_alpha[c];
+          const df w0 = A.wd[3 * l + c], p0 = A.pd[3 * l + c], r0 = A.rd[3 * l + c], ap0 = A.Apd[3 * l + c];
+          A.wd[3 * l + c] = df_add(w0, df_mul(alpha, p0));
+          const df rn = df_sub(r0, df_mul(alpha, ap0));
+          A.rd[3 * l + c] = rn;
+          A.zf[3 * l + c] = zl;
+          rz = df_add(rz, df_mul_f(rn, zl));
+        }
+      }
+      trace_mark(A, ts + 7);
+      block_partial3(rz, shdf, A.red + blockIdx.x * 8 + 3);
+    } else {
       df rz = dzero;
       const float* xs = stage_x(A, A.rf, A.Apf, alphaf, sm);
       trace_mark(A, ts + 6);
@@ -1565,14 +1649,25 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   IBL_CU(cudaMalloc(&c->d_Gval, sizeof(double) * (size_t)m * G_MAXNNZ));
   IBL_CU(cudaMalloc(&c->d_Gnnz, sizeof(int) * m));
   IBL_CU(cudaMalloc(&c->d_Gdiag_max, sizeof(double) * MAX_BODIES));
+  // preconditioner: the separable factors when every body allows them and
+  // they are asked for (or, automatically, for large bodies); else the dense
+  // per-body inverses
+  int max_m = 0;
+  const bool separable = sep_all_separable(c, &max_m);
+  if (c->precond_kind == 1 && !separable) return cudaErrorInvalidValue;
+  const bool use_sep = c->precond_kind == 1 || (c->precond_kind < 0 && separable && max_m >= SEP_AUTO_MIN_MARKERS);
   size_t mf = 0;
   for (auto& b : c->bodies) {
     b.precond_offset = (int)mf;
-    mf += (size_t)b.m * (size_t)((b.m + 3) & ~3);
+    if (!use_sep) mf += (size_t)b.m * (size_t)((b.m + 3) & ~3);
   }
   c->M_floats = mf;
-  IBL_CU(cudaMalloc(&c->d_M, sizeof(float) * mf));
-  keep_in_l2(c, c->d_M, sizeof(float) * mf);
+  if (use_sep) {
+    IBL_CU(sep_alloc(c));
+  } else {
+    IBL_CU(cudaMalloc(&c->d_M, sizeof(float) * mf));
+    keep_in_l2(c, c->d_M, sizeof(float) * mf);
+  }
   IBL_CU(cudaMalloc(&c->d_red, sizeof(double) * 8 * 1024));
   IBL_CU(cudaMalloc(&c->d_cg_info, sizeof(int) * 8));
   IBL_CU(cudaMemsetAsync(c->d_cg_info, 0, sizeof(int) * 8, c->stream));
@@ -1623,6 +1718,7 @@ void ib_free(ibl_ctx* c) {
   c->d_acc = nullptr;
   c->d_slot_body = c->d_mixed = c->d_cand = c->d_ncand = nullptr;
   c->d_wprev = nullptr;
+  sep_free(c);
   c->ib_ready = false;
 }
 
@@ -1877,8 +1973,9 @@ cudaError_t ib_step_back(ibl_ctx* c) {
     for (int b = 0; b < A.nbodies; ++b) slot = std::max(slot, precond_ld(c->bodies[b].m));
     const size_t rows = 2 * (((size_t)(m + 1) / 2 + pcg_blocks - 1) / pcg_blocks);   // whole row pairs
     const size_t need = stage + rows * (size_t)slot * sizeof(float);
+    if (c->sep_on) stage = std::max(stage, sep_smem_bytes());
     A.smem_floats = (int)(stage / sizeof(float));
-    A.row_slot = (need <= PCG_SMEM_MAX && c->resident_rows != 0) ? slot : 0;
+    A.row_slot = (need <= PCG_SMEM_MAX && c->resident_rows != 0 && !c->sep_on) ? slot : 0;
     c->pcg_smem = A.row_slot ? need : stage;
   }
   A.tol = c->solver_tol > 0 ? c->solver_tol
@@ -1912,6 +2009,9 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   A.mforce = c->d_mforce;
   A.hist = c->d_hist;
   A.step = c->step;
+  A.sep = c->d_sep;
+  A.sep_on = c->sep_on ? 1 : 0;
+  if (c->sep_on && A.refresh) IBL_CU(sep_launch(c, g.n, g.per));
   static bool smem_set = false;
   if (!smem_set) {
     IBL_CU(cudaFuncSetAttribute((const void*)k_pcg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PCG_SMEM_MAX));

@@ -33,6 +33,8 @@
 
 namespace ibl {
 
+struct SepBody;   // separable preconditioner of one body (sep.cuh)
+
 // ----------------------------------------------------------------- bodies
 struct Wave {
   int kind;
@@ -83,6 +85,10 @@ struct ibl_ctx {
   long long step = 0;
   long long launches = 0;
   int* d_status = nullptr;       // [0] step status bits, [1] point-operator flag
+  double* d_mass_parts = nullptr;  // MASS_PARTS partial sums of the periodic mass check
+  double* d_mass_ref = nullptr;    // [0] total at initialisation, [1] last total, [2] checks
+  int mass_every = 500;            // steps between mass checks (0: off)
+  double mass_tol = 0.0;           // relative drift bound (0: default for the precision)
   int* d_pt_perm = nullptr;      // point operators: sorted point order (pt_cap ints)
   int* d_pt_bins = nullptr;      // point operators: per-tile counters / offsets (n_tiles ints)
   size_t pt_cap = 0;
@@ -150,7 +156,12 @@ struct ibl_ctx {
   int refresh_every = 384;       // steps between scheduled preconditioner rebuilds
   double solver_tol = 0.0;       // 0: default for the storage precision
   int pcg_blocks = 0;            // blocks of the cooperative solve (0: half the SMs)
-  int precond_kind = -1;         // -1 automatic, 0 dense per-body inverse
+  int precond_kind = -1;         // -1 automatic, 0 dense per-body inverse, 1 separable
+  bool sep_on = false;           // the separable preconditioner is in use (sep.cu)
+  ibl::SepBody* d_sep = nullptr; // per body: sizes, index maps, factors, scratch
+  std::vector<void*> sep_allocs; // device buffers behind d_sep
+  bool sep_eigen_ready = false;  // span factors decomposed
+  int sep_blocks = 0;            // blocks of the cooperative rebuild
   int resident_rows = -1;        // -1 preconditioner rows in shared memory when they fit, 0 never
   size_t pcg_smem = 0;           // dynamic shared memory of the last solve launch
   double* d_wprev = nullptr;     // m x 3 solution of the previous step
@@ -192,6 +203,8 @@ cudaError_t launch_collide_bulk(ibl_ctx* c, int blocks);   // on stream_bulk
 cudaError_t launch_collide_band(ibl_ctx* c, int blocks);
 cudaError_t launch_fields(ibl_ctx* c, double* d_rho, double* d_u, double* d_pop);
 cudaError_t launch_mass(ibl_ctx* c, double* d_partials, int nparts, double* d_out);
+constexpr int MASS_PARTS = 1024;
+cudaError_t launch_mass_check(ibl_ctx* c, int mode);   // 0: store the reference, 1: check
 
 // IB launches (ib.cu)
 cudaError_t ib_alloc(ibl_ctx* c);
@@ -207,5 +220,16 @@ int pcg_block_count(const ibl_ctx* c);
 // gets every SM.
 constexpr int SPLIT_MAX_MARKERS = 8192;
 cudaError_t launch_force_field(ibl_ctx* c, double* d_out);
+
+// separable preconditioner (sep.cu)
+// Bodies with at least this many markers (the largest body counts) use the
+// separable preconditioner automatically when every body is separable: the
+// dense inverse costs m_b^2 FP32 per iteration and m_b^3 per rebuild.
+constexpr int SEP_AUTO_MIN_MARKERS = 4096;
+bool sep_all_separable(const ibl_ctx* c, int* max_markers);
+cudaError_t sep_alloc(ibl_ctx* c);
+void sep_free(ibl_ctx* c);
+size_t sep_smem_bytes();
+cudaError_t sep_launch(ibl_ctx* c, const int geo_n[3], const int geo_per[3]);
 
 }  // namespace ibl

@@ -420,6 +420,29 @@ __global__ void k_mass(const T* __restrict__ src, FluidParams<typename Store<T>:
   if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
 }
 
+// Total of the mass partials in a fixed order (one warp) and the test of
+// the periodic mass check.  mode 0 stores the total as the reference (at
+// initialisation); mode 1 records it and flags divergence for a non-finite
+// total or, when the faces conserve mass (no Zou-He face), a relative change
+// from the reference above tol.  ref: [0] reference, [1] last total, [2] checks.
+__global__ void k_mass_check(const double* __restrict__ partials, int nparts, double* __restrict__ ref, int mode,
+                             double tol, int closed, int* status) {
+  const int lane = threadIdx.x;
+  double s = 0.0;
+  for (int k = lane; k < nparts; k += 32) s += partials[k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane != 0) return;
+  if (mode == 0) {
+    ref[0] = s;
+    ref[1] = s;
+    ref[2] = 0.0;
+    return;
+  }
+  ref[1] = s;
+  ref[2] += 1.0;
+  if (!isfinite(s) || (closed && fabs(s - ref[0]) > tol * fabs(ref[0]))) atomicOr(status, ST_DIVERGED);
+}
+
 // ----------------------------------------------------------------- host side
 template <class R>
 FluidParams<R> make_params(ibl_ctx* c, bool with_ib) {
@@ -586,6 +609,18 @@ cudaError_t launch_mass(ibl_ctx* c, double* d_partials, int nparts, double* d_ou
   (void)d_out;
   IBL_DISPATCH(mass_q, d_partials, nparts);
 }
+cudaError_t launch_mass_check(ibl_ctx* c, int mode) {
+  cudaError_t e = launch_mass(c, c->d_mass_parts, MASS_PARTS, nullptr);
+  if (e != cudaSuccess) return e;
+  const double tol = c->mass_tol > 0 ? c->mass_tol
+                                     : (c->prec == IBL_FP64 ? 1e-9 : (c->prec == IBL_FP32 ? 1e-4 : 1e-2));
+  int closed = 1;
+  for (int f = 0; f < 6; ++f) closed &= (c->bc[f] == IBL_PERIODIC || c->bc[f] == IBL_BOUNCEBACK) ? 1 : 0;
+  k_mass_check<<<1, 32, 0, c->stream>>>(c->d_mass_parts, MASS_PARTS, c->d_mass_ref, mode, tol, closed, c->d_status);
+  c->launches++;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_eq(ibl_ctx* c, const double* d_rho, const double* d_u) {
   IBL_DISPATCH(init_q, d_rho, d_u);
 }

@@ -7,7 +7,7 @@
 //   2. enqueues the next chunk of steps of every active run whose previous
 //      chunk has finished (each run has its own CUDA stream, so the chunks of
 //      different runs overlap on the device);
-//   3. retires finished runs: reads their force histories, reduces them to
+//   3. retires finished (or cancelled) runs: reads their force histories, reduces them to
 //      the per-wing maxima and means of C_L and C_T (the quantities of the
 //      paper's parametric study, Sec. 3.4-3.7 and Fig. 11), destroys the
 //      context and returns its memory to the budget.
@@ -34,16 +34,22 @@ using clock_type = std::chrono::steady_clock;
 struct Run {
   int64_t id = 0;
   ibl_run_request req{};
-  ibl_run_result res{};
-  ibl_ctx* ctx = nullptr;
-  cudaEvent_t ev = nullptr;
-  bool inflight = false;
+  ibl_run_result res{};          // shared: read by ibl_server_poll under the server's mutex
+  ibl_ctx* ctx = nullptr;        // worker-owned
+  cudaEvent_t ev = nullptr;      // worker-owned
+  bool inflight = false;         // worker-owned
+  int64_t steps_enqueued = 0;    // worker-owned
+  std::atomic<bool> cancel{false};
   size_t bytes = 0;
   int m[2] = {0, 0};
 };
 
 }  // namespace
 
+// Shared state (queue, results, budget and counters) is guarded by `mu`;
+// the worker thread owns the active runs' contexts and does the slow work
+// (building a context, enqueueing steps, reading results, destroying it)
+// without holding `mu`, so that submit and poll never wait behind it.
 struct ibl_server {
   ibl_server_config cfg{};
   int device = 0;
@@ -51,11 +57,12 @@ struct ibl_server {
   std::mutex mu;
   std::condition_variable cv;
   std::deque<std::shared_ptr<Run>> queue;
-  std::vector<std::shared_ptr<Run>> active;
   std::map<int64_t, std::shared_ptr<Run>> all;
   int64_t next_id = 1;
   size_t in_use = 0;
+  int active = 0;                                 // admitted and not yet retired
   int finished = 0;
+  std::vector<std::shared_ptr<Run>> running;      // worker-owned
   std::atomic<bool> stop{false};
   std::thread worker;
   std::string err;
@@ -101,6 +108,26 @@ size_t estimate_bytes(const ibl_run_request& r, int m_total, int m_body) {
   return b + (64u << 20);                                           // slack
 }
 
+// Relaxation time and the largest imposed velocities of a request (lattice
+// units): U_tip = 2 Phi f c with Phi = 120 degrees (Eq. 24, Sec. 3.4),
+// nu = U_tip c / Re, tau = 3 nu + 1/2 (Eq. 3), free stream U_inf = J U_tip.
+void run_parameters(const ibl_run_request& r, double& tau, double& u_tip, double& u_inf) {
+  const double pi = 3.14159265358979323846;
+  u_tip = 2.0 * (2.0 * pi / 3.0) * (1.0 / r.period) * r.chord;
+  const double nu = u_tip * r.chord / r.Re;
+  tau = 3.0 * nu + 0.5;
+  u_inf = r.J * u_tip;
+}
+
+// Stability screen at submission (BGK collision): requests outside it are
+// refused with IBL_EUNSTABLE instead of diverging after using the GPU.
+// Bounds from the 64-request sweep (Re 75-150, f 0.05 / 0.25, J 1e-3..2):
+// every run with tau below 0.505 or a uniform free stream of 0.05 lattice
+// units or more diverged; wall speeds up to 0.105 (f = 0.25) were stable.
+constexpr double SERVE_TAU_MIN = 0.505;
+constexpr double SERVE_U_FREE_MAX = 0.05;
+constexpr double SERVE_U_WALL_MAX = 0.15;
+
 // Build the context of a clap-and-fling wing pair (Sec. 3.3): trailing-edge
 // hinges c/2 apart about the mid-plane, opening angle (pi/3)|sin(2 pi t/T)|
 // per wing, Re = U_tip c / nu with U_tip = 2 Phi f c, Phi = 120 degrees
@@ -109,10 +136,8 @@ ibl_status build_run(Run& run) {
   const ibl_run_request& r = run.req;
   const double pi = 3.14159265358979323846;
   const double f = 1.0 / r.period;
-  const double u_tip = 2.0 * (2.0 * pi / 3.0) * f * r.chord;
-  const double nu = u_tip * r.chord / r.Re;
-  const double tau = 3.0 * nu + 0.5;
-  const double u_inf = r.J * u_tip;
+  double tau = 0, u_tip = 0, u_inf = 0;
+  run_parameters(r, tau, u_tip, u_inf);
   ibl_grid g{};
   g.nx = r.nx; g.ny = r.ny; g.nz = r.nz;
   const int xface0 = r.faces ? IBL_VEL_INLET : IBL_PERIODIC;
@@ -154,8 +179,9 @@ ibl_status build_run(Run& run) {
   return cudaEventCreateWithFlags(&run.ev, cudaEventDisableTiming) == cudaSuccess ? IBL_OK : IBL_ECUDA;
 }
 
-void retire(ibl_server* s, Run& run, ibl_status st) {
-  ibl_run_result& res = run.res;
+// Reduce a finished run's force histories to the per-wing statistics and
+// release its context (no lock held); the caller publishes the result.
+void collect(Run& run, ibl_status st, ibl_run_result& res) {
   res.status = st;
   if (st == IBL_OK || st == IBL_ENOTCONV) {
     std::vector<double> h(3 * (size_t)std::max<int64_t>(run.req.steps, 1));
@@ -183,77 +209,119 @@ void retire(ibl_server* s, Run& run, ibl_status st) {
   }
   if (run.ev) cudaEventDestroy(run.ev);
   run.ev = nullptr;
-  ibl_destroy(run.ctx);
+  if (run.ctx) ibl_destroy(run.ctx);
   run.ctx = nullptr;
-  res.finish_s = now_s(s);
-  res.done = 1;
-  s->in_use -= run.bytes;
+}
+
+// Publish a finished (or failed, or cancelled) run and, if it was admitted,
+// return its memory to the budget; `mu` must be held.
+void publish(ibl_server* s, Run& run, const ibl_run_result& res, bool admitted) {
+  const double submit = run.res.submit_s, start = run.res.start_s;
+  const int64_t done = run.steps_enqueued;
+  run.res = res;
+  run.res.submit_s = submit;
+  run.res.start_s = start;
+  run.res.steps_done = done;
+  run.res.finish_s = now_s(s);
+  run.res.done = 1;
+  if (admitted) {
+    s->in_use -= run.bytes;
+    s->active--;
+  }
   s->finished++;
+  s->cv.notify_all();
 }
 
 void worker_loop(ibl_server* s) {
   cudaSetDevice(s->device);
   while (!s->stop.load()) {
     bool busy = false;
+    // 1. admission by arrival order, active count and HBM budget; the
+    // contexts are built after the lock is released
+    std::vector<std::shared_ptr<Run>> admit;
     {
-      std::unique_lock<std::mutex> lock(s->mu);
-      // 1. admission by arrival order, active count and HBM budget
-      while (!s->queue.empty() && (int)s->active.size() < s->cfg.max_active) {
+      std::lock_guard<std::mutex> lock(s->mu);
+      while (!s->queue.empty() && s->active < s->cfg.max_active) {
         auto run = s->queue.front();
-        if (s->in_use + run->bytes > s->cfg.hbm_budget_bytes && !s->active.empty()) break;
+        if (run->cancel.load()) {
+          s->queue.pop_front();
+          ibl_run_result res = run->res;
+          res.status = IBL_ECANCELED;
+          publish(s, *run, res, false);
+          continue;
+        }
+        if (s->in_use + run->bytes > (size_t)s->cfg.hbm_budget_bytes && s->active > 0) break;
         s->queue.pop_front();
         s->in_use += run->bytes;
-        const ibl_status st = build_run(*run);
-        run->res.start_s = now_s(s);
-        if (st != IBL_OK) {
-          if (run->ctx) {
-            retire(s, *run, st);
-          } else {
-            run->res.status = st;
-            run->res.done = 1;
-            run->res.finish_s = now_s(s);
-            s->in_use -= run->bytes;
-            s->finished++;
-          }
-          continue;
-        }
-        s->active.push_back(run);
-        busy = true;
+        s->active++;
+        admit.push_back(run);
       }
-      // 2. next chunk of every run whose previous chunk finished; 3. retire
-      for (size_t i = 0; i < s->active.size();) {
-        Run& r = *s->active[i];
-        if (r.inflight) {
-          const cudaError_t q = cudaEventQuery(r.ev);
-          if (q == cudaErrorNotReady) {
-            ++i;
-            continue;
-          }
-          r.inflight = false;
-        }
-        if (r.res.steps_done >= r.req.steps) {
-          retire(s, r, ibl_sync(r.ctx));
-          s->active.erase(s->active.begin() + i);
-          s->cv.notify_all();
-          busy = true;
+    }
+    for (auto& run : admit) {
+      const double t_start = now_s(s);
+      const ibl_status st = build_run(*run);
+      if (st != IBL_OK) {
+        ibl_run_result res{};
+        collect(*run, st, res);
+        std::lock_guard<std::mutex> lock(s->mu);
+        run->res.start_s = t_start;
+        publish(s, *run, res, true);
+        continue;
+      }
+      {
+        std::lock_guard<std::mutex> lock(s->mu);
+        run->res.start_s = t_start;
+      }
+      s->running.push_back(run);
+      busy = true;
+    }
+    // 2. next chunk of every run whose previous chunk finished; 3. retire
+    for (size_t i = 0; i < s->running.size();) {
+      Run& r = *s->running[i];
+      ibl_status st = IBL_OK;
+      if (r.inflight) {
+        if (cudaEventQuery(r.ev) == cudaErrorNotReady) {
+          ++i;
           continue;
         }
-        const int64_t n = std::min<int64_t>(s->cfg.chunk_steps, r.req.steps - r.res.steps_done);
-        const ibl_status st = ibl_step(r.ctx, n);
-        if (st != IBL_OK) {
-          retire(s, r, st);
-          s->active.erase(s->active.begin() + i);
-          s->cv.notify_all();
-          continue;
+        r.inflight = false;
+        // the run's stream is idle: reading its status bits costs one small
+        // copy, and a divergence stops the run here instead of at its end
+        st = ibl_sync(r.ctx);
+        if (st == IBL_ENOTCONV) st = IBL_OK;   // reported, not fatal
+      }
+      const bool cancelled = r.cancel.load();
+      bool finish = cancelled || st != IBL_OK || r.steps_enqueued >= r.req.steps;
+      if (!finish) {
+        const int64_t n = std::min<int64_t>(s->cfg.chunk_steps, r.req.steps - r.steps_enqueued);
+        st = ibl_step(r.ctx, n);
+        if (st == IBL_OK) {
+          void* stream = nullptr;
+          ibl_stream(r.ctx, &stream);
+          cudaEventRecord(r.ev, (cudaStream_t)stream);
+          r.inflight = true;
+          r.steps_enqueued += n;
+          std::lock_guard<std::mutex> lock(s->mu);
+          r.res.steps_done = r.steps_enqueued;
+        } else {
+          finish = true;
         }
-        void* stream = nullptr;
-        ibl_stream(r.ctx, &stream);
-        cudaEventRecord(r.ev, (cudaStream_t)stream);
-        r.inflight = true;
-        r.res.steps_done += n;
+      }
+      if (!finish) {
         busy = true;
         ++i;
+        continue;
       }
+      if (cancelled && st == IBL_OK) st = IBL_ECANCELED;
+      else if (st == IBL_OK) st = ibl_sync(r.ctx);
+      ibl_run_result res{};
+      collect(r, st, res);
+      {
+        std::lock_guard<std::mutex> lock(s->mu);
+        publish(s, r, res, true);
+      }
+      s->running.erase(s->running.begin() + i);
+      busy = true;
     }
     if (!busy) std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
@@ -266,7 +334,7 @@ extern "C" {
 ibl_status ibl_server_create(const ibl_server_config* cfg, ibl_server** out) {
   if (!out || !cfg) return IBL_EINVAL;
   *out = nullptr;
-  if (cfg->max_active < 1 || cfg->chunk_steps < 1 || cfg->hbm_budget_bytes == 0) return IBL_EINVAL;
+  if (cfg->max_active < 1 || cfg->chunk_steps < 1 || cfg->hbm_budget_bytes <= 0) return IBL_EINVAL;
   ibl_server* s = new ibl_server();
   s->cfg = *cfg;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
@@ -281,6 +349,7 @@ ibl_status ibl_server_create(const ibl_server_config* cfg, ibl_server** out) {
 
 ibl_status ibl_server_submit(ibl_server* s, const ibl_run_request* req, int64_t* run_id) {
   if (!s || !req) return IBL_EINVAL;
+  const double submit_s = now_s(s);   // before any lock: the wait for it counts as latency
   if (req->nx < 16 || req->ny < 16 || req->nz < 16 || !(req->chord >= 4.0) || !(req->Re > 0) ||
       !(req->period > 0) || !(req->J >= 0) || req->steps < 1 || req->steps > ibl::HIST_LEN ||
       req->precision < IBL_FP64 || req->precision > IBL_BF16DEV)
@@ -289,20 +358,33 @@ ibl_status ibl_server_submit(ibl_server* s, const ibl_run_request* req, int64_t*
   if (req->chord * 5.0 + 8 > req->nz || std::round(req->nx / 3.0) - req->chord < 4 ||
       0.5 * req->ny - 0.25 * req->chord - req->chord < 4)
     return IBL_EINVAL;
+  double tau = 0, u_tip = 0, u_inf = 0;
+  run_parameters(*req, tau, u_tip, u_inf);
+  if (!(tau >= SERVE_TAU_MIN) || !(u_inf <= SERVE_U_FREE_MAX) || !(u_tip <= SERVE_U_WALL_MAX))
+    return IBL_EUNSTABLE;
   auto run = std::make_shared<Run>();
   run->req = *req;
   std::vector<double> X0, ds;
   planform(req->chord, X0, ds);
   const int m = (int)ds.size();
   run->bytes = estimate_bytes(*req, 2 * m, m);
-  std::lock_guard<std::mutex> lock(s->mu);
-  if (run->bytes > s->cfg.hbm_budget_bytes) return IBL_ENOMEM;
-  run->id = s->next_id++;
-  run->res.submit_s = now_s(s);
+  if (run->bytes > (size_t)s->cfg.hbm_budget_bytes) return IBL_ENOMEM;
+  run->res.submit_s = submit_s;
   run->res.status = IBL_OK;
+  std::lock_guard<std::mutex> lock(s->mu);
+  run->id = s->next_id++;
   s->queue.push_back(run);
   s->all[run->id] = run;
   if (run_id) *run_id = run->id;
+  return IBL_OK;
+}
+
+ibl_status ibl_server_cancel(ibl_server* s, int64_t run_id) {
+  if (!s) return IBL_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->all.find(run_id);
+  if (it == s->all.end()) return IBL_EINVAL;
+  if (!it->second->res.done) it->second->cancel.store(true);
   return IBL_OK;
 }
 
@@ -319,9 +401,8 @@ ibl_status ibl_server_wait_all(ibl_server* s, double timeout_s) {
   if (!s) return IBL_EINVAL;
   std::unique_lock<std::mutex> lock(s->mu);
   const auto deadline = clock_type::now() + std::chrono::duration<double>(timeout_s);
-  while (!(s->queue.empty() && s->active.empty())) {
-    if (s->cv.wait_until(lock, deadline) == std::cv_status::timeout &&
-        !(s->queue.empty() && s->active.empty()))
+  while (!(s->queue.empty() && s->active == 0)) {
+    if (s->cv.wait_until(lock, deadline) == std::cv_status::timeout && !(s->queue.empty() && s->active == 0))
       return IBL_ETIMEOUT;
   }
   return IBL_OK;
@@ -332,7 +413,7 @@ ibl_status ibl_server_stats(ibl_server* s, int32_t* queued, int32_t* active, int
   if (!s) return IBL_EINVAL;
   std::lock_guard<std::mutex> lock(s->mu);
   if (queued) *queued = (int32_t)s->queue.size();
-  if (active) *active = (int32_t)s->active.size();
+  if (active) *active = (int32_t)s->active;
   if (finished) *finished = s->finished;
   if (hbm_in_use) *hbm_in_use = (int64_t)s->in_use;
   return IBL_OK;
@@ -342,8 +423,10 @@ ibl_status ibl_server_destroy(ibl_server* s) {
   if (!s) return IBL_OK;
   s->stop.store(true);
   if (s->worker.joinable()) s->worker.join();
-  for (auto& r : s->active)
+  for (auto& r : s->running) {
+    if (r->ev) cudaEventDestroy(r->ev);
     if (r->ctx) ibl_destroy(r->ctx);
+  }
   delete s;
   return IBL_OK;
 }

@@ -21,14 +21,15 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 # ------------------------------------------------------------------ enums (ibl.h)
-IBL_OK, IBL_EINVAL, IBL_ENOMEM, IBL_ECUDA, IBL_EDIVERGED, IBL_ENOTCONV, IBL_ETIMEOUT, IBL_ESTATE = range(8)
+(IBL_OK, IBL_EINVAL, IBL_ENOMEM, IBL_ECUDA, IBL_EDIVERGED, IBL_ENOTCONV, IBL_ETIMEOUT, IBL_ESTATE,
+ IBL_ECANCELED, IBL_EUNSTABLE) = range(10)
 IBL_D2Q9, IBL_D3Q19 = 9, 19
 IBL_PERIODIC, IBL_BOUNCEBACK, IBL_VEL_INLET, IBL_PRESS_OUTLET = range(4)
 IBL_FP64, IBL_FP32, IBL_FP16DEV, IBL_BF16DEV = range(4)
 IBL_WAVE_CONST, IBL_WAVE_COS, IBL_WAVE_SIN, IBL_WAVE_ABS_SIN, IBL_WAVE_TABLE = range(5)
 IBL_FIELD_RHO, IBL_FIELD_U, IBL_FIELD_FORCE = range(3)
 STATUS_NAMES = ["IBL_OK", "IBL_EINVAL", "IBL_ENOMEM", "IBL_ECUDA", "IBL_EDIVERGED",
-                "IBL_ENOTCONV", "IBL_ETIMEOUT", "IBL_ESTATE"]
+                "IBL_ENOTCONV", "IBL_ETIMEOUT", "IBL_ESTATE", "IBL_ECANCELED", "IBL_EUNSTABLE"]
 PRECISIONS = {"fp64": IBL_FP64, "fp32": IBL_FP32, "fp16dev": IBL_FP16DEV, "bf16dev": IBL_BF16DEV}
 
 
@@ -85,6 +86,8 @@ _SIGS = {
     "ibl_get_markers": ([_P, C.c_int32, _D, _D, _D], C.c_int),
     "ibl_mass": ([_P, _D], C.c_int),
     "ibl_mass_noalloc": ([_P, C.c_int32, _D], C.c_int),
+    "ibl_set_mass_check": ([_P, C.c_int32, C.c_double], C.c_int),
+    "ibl_mass_check_read": ([_P, _D, _D, _I64], C.c_int),
     "ibl_set_overlap": ([_P, C.c_int32], C.c_int),
     "ibl_profile_phases": ([_P, _D, C.c_int32], C.c_int),
     "ibl_solver_blocks": ([_P, C.c_int32], C.c_int),
@@ -103,6 +106,7 @@ _SIGS = {
     "ibl_server_create": ([C.POINTER(ibl_server_config), C.POINTER(_P)], C.c_int),
     "ibl_server_submit": ([_P, C.POINTER(ibl_run_request), _I64], C.c_int),
     "ibl_server_poll": ([_P, C.c_int64, C.POINTER(ibl_run_result)], C.c_int),
+    "ibl_server_cancel": ([_P, C.c_int64], C.c_int),
     "ibl_server_wait_all": ([_P, C.c_double], C.c_int),
     "ibl_server_stats": ([_P, _I32, _I32, _I32, _I64], C.c_int),
     "ibl_server_destroy": ([_P], C.c_int),
@@ -337,6 +341,16 @@ class Context:
         _check(self.h, _lib.ibl_mass_noalloc(self.h, int(nparts), C.byref(m)), allow)
         return m.value
 
+    def ibl_set_mass_check(self, every=500, rel_tol=0.0):
+        """FP64 mass check every `every` steps (0: off); rel_tol 0: default for the precision."""
+        _check(self.h, _lib.ibl_set_mass_check(self.h, int(every), float(rel_tol)))
+
+    def ibl_mass_check_read(self, allow=()):
+        """(reference total, last checked total, checks so far)."""
+        m0, m1, n = C.c_double(), C.c_double(), C.c_int64()
+        _check(self.h, _lib.ibl_mass_check_read(self.h, C.byref(m0), C.byref(m1), C.byref(n)), allow)
+        return m0.value, m1.value, n.value
+
     def ibl_solver_blocks(self, blocks):
         """Blocks of the cooperative solve (0: half the SMs)."""
         _check(self.h, _lib.ibl_solver_blocks(self.h, int(blocks)))
@@ -393,8 +407,8 @@ class Context:
         _check(self.h, _lib.ibl_solver_config(self.h, int(refresh_every), float(tol), mode))
 
     def ibl_solver_preconditioner(self, kind=-1, resident_rows=-1):
-        """kind: -1 automatic, 0 dense per-body inverse; resident_rows: -1 when
-        they fit, 0 always read from L2/HBM."""
+        """kind: -1 automatic, 0 dense per-body inverse, 1 separable factors;
+        resident_rows: -1 when they fit, 0 always read from L2/HBM."""
         _check(self.h, _lib.ibl_solver_preconditioner(self.h, int(kind), int(resident_rows)))
 
     def ibl_solver_trace(self, allow=()):
@@ -473,6 +487,11 @@ class Server:
                 "submit_s": r.submit_s, "start_s": r.start_s, "finish_s": r.finish_s,
                 "CL_max": list(r.CL_max), "CL_mean": list(r.CL_mean), "CT_max": list(r.CT_max),
                 "CT_mean": list(r.CT_mean), "CL_last": list(r.CL_last), "CT_last": list(r.CT_last)}
+
+    def ibl_server_cancel(self, run_id):
+        st = _lib.ibl_server_cancel(self.h, int(run_id))
+        if st != IBL_OK:
+            raise IblError(st, "unknown run id")
 
     def ibl_server_wait_all(self, timeout_s=3600.0):
         st = _lib.ibl_server_wait_all(self.h, float(timeout_s))

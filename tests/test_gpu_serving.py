@@ -74,3 +74,57 @@ def test_budget_and_validation(ibl):
         srv.ibl_server_submit(**dict(REQ, nz=20))  # the span does not fit
     assert e.value.status == ibl.IBL_EINVAL
     srv.close()
+
+
+UNSTABLE = dict(nx=48, ny=40, nz=40, chord=6.0, Re=29.0, period=1200.0, J=0.1, precision="fp32", steps=400,
+                faces=1)   # tau 0.513 with Zou-He faces: diverges within ~150 steps (the oracle too)
+
+
+def test_a_diverging_run_fails_alone(ibl):
+    """A request that passes the stability screen but diverges (Zou-He
+    inlet/outlet at tau 0.513) is stopped at the chunk where its divergence
+    shows, with IBL_EDIVERGED; the run beside it gives bitwise its result
+    alone."""
+    alone = ibl.Server(hbm_budget_bytes=8 << 30, max_active=2, chunk_steps=25)
+    rid = alone.ibl_server_submit(**REQ)
+    alone.ibl_server_wait_all(600)
+    ra = alone.ibl_server_poll(rid)
+    alone.close()
+    mix = ibl.Server(hbm_budget_bytes=8 << 30, max_active=2, chunk_steps=25)
+    bad = mix.ibl_server_submit(**UNSTABLE)
+    rid = mix.ibl_server_submit(**REQ)
+    mix.ibl_server_wait_all(600)
+    rb, rm = mix.ibl_server_poll(bad), mix.ibl_server_poll(rid)
+    stats = mix.ibl_server_stats()
+    mix.close()
+    assert rb["done"] and rb["status"] == ibl.IBL_EDIVERGED and rb["steps_done"] < UNSTABLE["steps"]
+    assert rm["status"] == ibl.IBL_OK and _keys(rm) == _keys(ra)
+    assert stats["hbm_in_use"] == 0 and stats["finished"] == 2
+
+
+def test_unstable_requests_are_refused_at_submission(ibl):
+    srv = ibl.Server(hbm_budget_bytes=8 << 30, max_active=2, chunk_steps=25)
+    for bad in (dict(REQ, Re=2000.0),      # tau = 0.5013
+                dict(REQ, J=5.0)):         # free stream 5 U_tip = 0.18 lattice units
+        with pytest.raises(ibl.IblError) as e:
+            srv.ibl_server_submit(**bad)
+        assert e.value.status == ibl.IBL_EUNSTABLE
+    srv.close()
+
+
+def test_cancel_queued_and_running(ibl):
+    srv = ibl.Server(hbm_budget_bytes=8 << 30, max_active=1, chunk_steps=10)
+    running = srv.ibl_server_submit(**dict(REQ, steps=20000))
+    queued = srv.ibl_server_submit(**REQ)
+    t0 = time.time()
+    while srv.ibl_server_poll(running)["steps_done"] == 0 and time.time() - t0 < 60:
+        time.sleep(0.01)
+    srv.ibl_server_cancel(queued)
+    srv.ibl_server_cancel(running)
+    srv.ibl_server_wait_all(600)
+    rr, rq = srv.ibl_server_poll(running), srv.ibl_server_poll(queued)
+    stats = srv.ibl_server_stats()
+    srv.close()
+    assert rr["status"] == ibl.IBL_ECANCELED and 0 < rr["steps_done"] < 20000
+    assert rq["status"] == ibl.IBL_ECANCELED and rq["steps_done"] == 0 and rq["start_s"] == 0.0
+    assert stats["hbm_in_use"] == 0 and stats["active"] == 0 and stats["finished"] == 2
