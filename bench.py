@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the 256x192x160 wing pair measured after the default workload")
     ap.add_argument("--size", type=int, default=256, help="cube edge of the tgv workload")
+    ap.add_argument("--box", default=None,
+                    help="NXxNYxNZ: the wing pair of --workload in a box of this size (profiling a smaller case)")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving sweep (Poisson arrivals of clap-and-fling runs) instead")
     ap.add_argument("--requests", type=int, default=64)
@@ -87,8 +89,15 @@ def parse():
     return ap.parse_args()
 
 
-def workload(precision="fp32", scale=1.0, kind="wings", size=256):
+def workload(precision="fp32", scale=1.0, kind="wings", size=256, box=None):
     import workloads as W
+    if box:
+        # the same wings in another box (profiling): chord and flow as in the workload
+        nx, ny, nz = (int(v) for v in box.lower().split("x"))
+        if kind == "wings-large":
+            return W.clap_fling_3d(nx=nx, ny=ny, nz=nz, chord=40.0, Re=150.0, J=1e-3, period=8000.0,
+                                   precision=precision, faces="periodic")
+        return W.clap_fling_3d(nx=nx, ny=ny, nz=nz, chord=20.0, precision=precision, faces="periodic")
     if kind == "tgv":
         n = max(8, int(round(size * scale)))
         return W.taylor_green_3d(n=n, u0=0.05, tau=0.6, precision=precision)
@@ -285,6 +294,12 @@ def pcg_trace_summary(tr, iters):
     for j, name in enumerate(PCG_PHASES):
         out[name + "_us"] = med([(tr[b + j + 1] - tr[b + j]) / 1e3 for b in base])
     out["iteration_us_median"] = med([(tr[b + 8] - e) / 1e3 for b, e in zip(base, prev_end)])
+    if len(tr) > 253 and tr[250] and tr[253] and tr[250] < tr[4] < tr[253]:
+        # separable preconditioner: stages A-F of the set-up's first
+        # application and stage G with its barrier (block 0's clock)
+        marks = [tr[250], tr[4], tr[5], tr[6], tr[7], tr[251], tr[252], tr[253]]
+        out["separable_stages_us"] = dict(zip("ABCDEFG", [round((marks[k + 1] - marks[k]) / 1e3, 3)
+                                                          for k in range(7)]))
     return out
 
 
@@ -420,7 +435,7 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo",
                                 init_method="env://")
     torch.cuda.set_device(0)
-    cfg = workload(args.precision, 1.0, args.workload, args.size)
+    cfg = workload(args.precision, 1.0, args.workload, args.size, args.box)
     g = cfg["grid"]
     cells = g["nx"] * g["ny"] * g["nz"]
     elem = {"fp32": 4, "fp16dev": 2, "bf16dev": 2, "fp64": 8}[args.precision]
@@ -611,20 +626,29 @@ def run_serving(n: int, mean_gap: float, run_steps: int, mix: str, budget_frac: 
     gaps = rng.exponential(mean_gap, size=n)
     t0 = time.perf_counter()
     ids = []
+    refused = 0
+    admitted = []
     for g, r in zip(gaps, reqs):
         time.sleep(float(g))
-        ids.append(srv.ibl_server_submit(**r))
+        try:
+            ids.append(srv.ibl_server_submit(**r))
+            admitted.append(r)
+        except ibl.IblError as e:
+            if e.status != ibl.IBL_EUNSTABLE:
+                raise
+            refused += 1       # outside the collision's stability range: refused at submission
     srv.ibl_server_wait_all(24 * 3600.0)
     wall = time.perf_counter() - t0
     res = [srv.ibl_server_poll(i) for i in ids]
     srv.close()
+    reqs = admitted
     ok = [r for r in res if r["status"] == ibl.IBL_OK]
     lat = sorted(r["finish_s"] - r["submit_s"] for r in ok)
     q = lambda p: float(np.percentile(lat, p)) if lat else None
     cells = sum(rq["nx"] * rq["ny"] * rq["nz"] * rq["steps"] for rq, r in zip(reqs, res) if r["status"] == ibl.IBL_OK)
     return {"solves_per_hour": len(ok) / wall * 3600.0, "requests": n, "completed": len(ok),
-            "failed": n - len(ok), "failure_statuses": sorted({ibl.STATUS_NAMES[r["status"]] for r in res
-                                                                if r["status"] != ibl.IBL_OK}),
+            "refused_unstable": refused, "failed": len(res) - len(ok),
+            "failure_statuses": sorted({ibl.STATUS_NAMES[r["status"]] for r in res if r["status"] != ibl.IBL_OK}),
             "p50_latency_s": q(50), "p99_latency_s": q(99), "wall_s": wall, "mean_gap_s": mean_gap,
             "steps_per_run": run_steps, "precision_mix": mix,
             "aggregate_glups": cells / wall / 1e9}

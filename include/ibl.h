@@ -292,8 +292,9 @@ ibl_status ibl_solver_config(ibl_ctx* ctx, int32_t refresh_every, double tol, in
 ibl_status ibl_solver_blocks(ibl_ctx* ctx, int32_t blocks);
 
 /* Preconditioner of the implicit IB solve (Eqs. 18-19).  Both kinds
- * approximate (G_b + sigma I)^-1 per body, sigma = 1e-6 times G_b's largest
- * absolute row sum, rebuilt every refresh_every steps (ibl_solver_config):
+ * approximate (G_b + sigma I)^-1 per body, sigma = 1e-6 (kind 0) or 2e-7
+ * (kind 1) times G_b's largest absolute row sum, rebuilt every
+ * refresh_every steps (ibl_solver_config):
  *   kind 0: the dense inverse, FP32, m_b^2 numbers per body;
  *   kind 1: separable factors, for bodies whose markers form a chord x span
  *           product mesh (a planform grid, possibly clipped) turning about
@@ -328,8 +329,10 @@ ibl_status ibl_set_overlap(ibl_ctx* ctx, int32_t mode);
  * iteration k (k < 27) at 8 + 9k: recurrence
  * scalars ready, search direction input staged, SpMV rows done, block
  * reduction done, grid barrier passed, step length ready, preconditioner
- * input staged, preconditioner rows done, grid barrier passed.  Unused
- * slots are 0.  Copies min(max, 256) values into ns. */
+ * input staged, preconditioner rows done, grid barrier passed.  With the
+ * separable preconditioner, [4]-[7] and [251]-[252] mark the ends of stages
+ * A-F of the set-up's first application (from [250]) and [253] the end of
+ * its stage G.  Unused slots are 0.  Copies min(max, 256) values into ns. */
 ibl_status ibl_solver_trace(ibl_ctx* ctx, int64_t* ns, int32_t max, int32_t* n);
 
 /* Enable (1 or 2) or disable (0) CUDA-event timing of the collide-stream

@@ -1086,21 +1086,27 @@ __device__ __noinline__ void gj_invert(const PcgArgs& A, cg::grid_group& grid, f
   }
 }
 
-// Stages A-F of the separable preconditioner (sep.cuh) for all bodies and
-// components, a grid barrier after each; stage G is done by the caller.
-__device__ void sep_front(const PcgArgs& A, cg::grid_group& grid, const SepIn& in, float* sm) {
-  sep_rowpass(A.sep, A.nbodies, 0, in, A.voff, sm);
-  grid.sync();
-  sep_colpass(A.sep, A.nbodies, false);
-  grid.sync();
-  sep_complement_values(A.sep, A.nbodies);
-  grid.sync();
-  sep_schur(A.sep, A.nbodies);
-  grid.sync();
-  sep_rowpass(A.sep, A.nbodies, 1, in, A.voff, sm);
-  grid.sync();
-  sep_colpass(A.sep, A.nbodies, true);
-  grid.sync();
+// Stages A-G of the separable preconditioner (sep.cuh) for all bodies and
+// components, a grid barrier after each; the caller then reads each
+// marker's z from the R0 rectangle (sep_marker_z).  With trace set (the
+// set-up's first application) the end of each stage is time-stamped: slots
+// 4-7 (unused by this preconditioner's rebuild) and 251-253 (after the
+// iteration slots), from 250.
+__device__ void sep_apply(const PcgArgs& A, cg::grid_group& grid, const SepIn& in, float* sm, bool trace) {
+  const int marks[7] = {4, 5, 6, 7, 251, 252, 253};
+  for (int st = 0; st < 7; ++st) {
+    switch (st) {
+      case 0: sep_gemm(A.sep, A.nbodies, 0, false, in, A.voff, sm); break;    // A  Y1 = X V
+      case 1: sep_colpass(A.sep, A.nbodies, false, sm); break;                 // B  Y2 = H Y1
+      case 2: sep_gemm(A.sep, A.nbodies, 2, true, in, A.voff, sm); break;     // C  T = Y2 V^T
+      case 3: sep_schur(A.sep, A.nbodies, sm, A.smem_floats); break;          // D  u = S^-1 t
+      case 4: sep_gemm(A.sep, A.nbodies, 1, false, in, A.voff, sm); break;    // E  W1 = U V
+      case 5: sep_colpass(A.sep, A.nbodies, true, sm); break;                  // F  W2 = H W1
+      default: sep_gemm(A.sep, A.nbodies, 3, true, in, A.voff, sm); break;    // G  Z = (Y2 - W2) V^T
+    }
+    grid.sync();
+    if (trace) trace_mark(A, marks[st]);
+  }
 }
 
 // Preconditioned CG on G w = B, three right-hand sides (velocity components)
@@ -1226,7 +1232,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
     in.a = A.rf;
     in.b = nullptr;
     in.s[0] = in.s[1] = in.s[2] = 0.f;
-    sep_front(A, grid, in, sm);
+    trace_mark(A, 250);
+    sep_apply(A, grid, in, sm, true);
     for (int l = gwarp; l < m; l += nwarp_all) {
       const int bd = A.body_of[l];
       float z[3];
@@ -1237,8 +1244,9 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
         rz = df_add(rz, df_mul_f(A.rd[3 * l + lane], zc));
       }
     }
+    grid.sync();   // every block has read its z before the next application writes R0
     in.a = A.Bf;
-    sep_front(A, grid, in, sm);
+    sep_apply(A, grid, in, sm, false);
     for (int l = gwarp; l < m; l += nwarp_all) {
       const int bd = A.body_of[l];
       float z[3];
@@ -1410,7 +1418,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
       in.s[1] = alphaf[1];
       in.s[2] = alphaf[2];
       trace_mark(A, ts + 6);
-      sep_front(A, grid, in, sm);
+      sep_apply(A, grid, in, sm, false);
       for (int l = gwarp; l < m; l += nwarp_all) {
         const int bd = A.body_of[l];
         float z[3];
@@ -1973,7 +1981,7 @@ cudaError_t ib_step_back(ibl_ctx* c) {
     for (int b = 0; b < A.nbodies; ++b) slot = std::max(slot, precond_ld(c->bodies[b].m));
     const size_t rows = 2 * (((size_t)(m + 1) / 2 + pcg_blocks - 1) / pcg_blocks);   // whole row pairs
     const size_t need = stage + rows * (size_t)slot * sizeof(float);
-    if (c->sep_on) stage = std::max(stage, sep_smem_bytes());
+    if (c->sep_on) stage = std::max(stage, sep_smem_bytes(c));
     A.smem_floats = (int)(stage / sizeof(float));
     A.row_slot = (need <= PCG_SMEM_MAX && c->resident_rows != 0 && !c->sep_on) ? slot : 0;
     c->pcg_smem = A.row_slot ? need : stage;

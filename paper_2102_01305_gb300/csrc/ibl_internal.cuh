@@ -162,6 +162,7 @@ struct ibl_ctx {
   std::vector<void*> sep_allocs; // device buffers behind d_sep
   bool sep_eigen_ready = false;  // span factors decomposed
   int sep_blocks = 0;            // blocks of the cooperative rebuild
+  size_t sep_smem = 0;           // dynamic shared memory the solve's separable stages need
   int resident_rows = -1;        // -1 preconditioner rows in shared memory when they fit, 0 never
   size_t pcg_smem = 0;           // dynamic shared memory of the last solve launch
   double* d_wprev = nullptr;     // m x 3 solution of the previous step
@@ -229,7 +230,7 @@ constexpr int SEP_AUTO_MIN_MARKERS = 4096;
 bool sep_all_separable(const ibl_ctx* c, int* max_markers);
 cudaError_t sep_alloc(ibl_ctx* c);
 void sep_free(ibl_ctx* c);
-size_t sep_smem_bytes();
+size_t sep_smem_bytes(const ibl_ctx* c);
 cudaError_t sep_launch(ibl_ctx* c, const int geo_n[3], const int geo_per[3]);
 
 }  // namespace ibl

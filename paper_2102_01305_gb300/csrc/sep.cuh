@@ -23,11 +23,12 @@
 // inverse of the same matrix), held in O(n_k^2 + n_k n_i^2 + n_c^2) numbers
 // instead of O(m^2): at 2 x 6292 markers 2 x 25 MB instead of 2 x 158 MB.
 //
-// Application, per right-hand side (velocity component), in seven stages
-// separated by grid barriers; rectangles are n_i x n_k FP32 arrays:
+// Application, for the three right-hand sides (velocity components) at once,
+// in seven stages separated by grid barriers; rectangles are n_i x n_k FP32
+// arrays:
 //   A  Y1 = X V           X: the input on the markers, 0 on c (rows i)
 //   B  Y2[:,j] = H_j Y1[:,j]                                  (columns j)
-//   C  t_p = (Y2 V^T)[p] for p in c
+//   C  T = Y2 V^T         (t = T on c)
 //   D  u = S^-1 t         (S^-1 stored as double-float pairs, products
 //                          accumulated in double-float: the only stage whose
 //                          FP32 rounding the Schur subtraction does not
@@ -36,16 +37,25 @@
 //                          FP32 S^-1 makes the preconditioner indefinite)
 //   E  W1 = U V           U: u on c, 0 on the markers
 //   F  W2[:,j] = H_j W1[:,j]
-//   G  z_l = ((Y2 - W2) V^T)[l] for the markers l  (done by the caller)
+//   G  Z = (Y2 - W2) V^T  (z = Z on the markers, read by the caller after
+//                          a grid barrier)
 #pragma once
 
 #include "df.cuh"
 
 namespace ibl {
 
-constexpr int SEP_RG = 4;          // chord rows per warp item of a row pass
-constexpr int SEP_NK_MAX = 256;    // span positions per body (shared-memory rows)
+constexpr int SEP_NK_MAX = 256;    // span positions per body
 constexpr int SEP_NI_MAX = 64;     // chord positions per body
+// Rectangle products (stages A, C, E, G): a block computes SEP_GR chord rows
+// x SEP_GC columns of all three components, its 1024 threads splitting the
+// reduction into SEP_GK groups.
+constexpr int SEP_GR = 8;
+constexpr int SEP_GC = 32;
+constexpr int SEP_GK = 4;
+// Column passes: a block applies SEP_JG consecutive span modes' H_j.
+constexpr int SEP_JG = 2;
+__host__ __device__ constexpr int sep_ldv(int nk) { return (nk + 3) & ~3; }   // V row stride (16-byte rows)
 
 struct SepBody {
   int ni, nk, nc, m;      // chord positions, span positions, complement entries, markers
@@ -55,7 +65,7 @@ struct SepBody {
   const int* crect;       // n_c: rectangle index of each complement entry
   const int* rep_i;       // n_i: a marker (local index) at each chord position
   const int* rep_k;       // n_k: a marker (local index) at each span position
-  float* V;               // n_k x n_k eigenvectors of Z, V[k n_k + j]
+  float* V;               // n_k x ldv eigenvectors of Z, V[k ldv + j], ldv = sep_ldv(n_k), zero padded
   float* Ht;              // n_k x n_i x n_i: Ht[(j n_i + i2) n_i + i] = H_j[i][i2]
   float* Sinv;            // n_c x ldc double-float pairs (hi, lo), 2 ldc floats per row
   float* R0;              // 3 x n_i x n_k scratch (Y1, then W1)
@@ -80,17 +90,22 @@ struct SepIn {
   float s[3];
 };
 
-// Warp items of a stage are dealt over all bodies in order; item -> (body, local item).
-__device__ __forceinline__ int sep_item_body(const SepBody* sb, int nb, int per_body_kind, long long& item) {
+// Items of a stage are dealt over all bodies in order; item -> (body, local item).
+//   kind 0: rectangle-product tiles, one per block
+//   kind 1: column-pass groups of SEP_JG modes, one per block
+//   kind 2: groups of 32 Schur rows, one per block;  kind 3: markers
+__device__ __forceinline__ long long sep_count(const SepBody& B, int kind) {
+  switch (kind) {
+    case 0: return (long long)((B.ni + SEP_GR - 1) / SEP_GR) * ((B.nk + SEP_GC - 1) / SEP_GC);
+    case 1: return (B.nk + SEP_JG - 1) / SEP_JG;
+    case 2: return (B.nc + 31) / 32;
+    default: return B.m;
+  }
+}
+
+__device__ __forceinline__ int sep_item_body(const SepBody* sb, int nb, int kind, long long& item) {
   for (int b = 0; b < nb; ++b) {
-    const SepBody& B = sb[b];
-    long long cnt;
-    switch (per_body_kind) {
-      case 0: cnt = 3LL * ((B.ni + SEP_RG - 1) / SEP_RG) * ((B.nk + 31) / 32); break;   // row pass
-      case 1: cnt = 3LL * B.nk * ((B.ni + 31) / 32); break;                              // column pass
-      case 2: cnt = B.nc; break;                                                          // per complement entry
-      default: cnt = B.m; break;                                                          // per marker
-    }
+    const long long cnt = sep_count(sb[b], kind);
     if (item < cnt) return b;
     item -= cnt;
   }
@@ -99,45 +114,49 @@ __device__ __forceinline__ int sep_item_body(const SepBody* sb, int nb, int per_
 
 __device__ __forceinline__ long long sep_items(const SepBody* sb, int nb, int kind) {
   long long t = 0;
-  for (int b = 0; b < nb; ++b) {
-    const SepBody& B = sb[b];
-    switch (kind) {
-      case 0: t += 3LL * ((B.ni + SEP_RG - 1) / SEP_RG) * ((B.nk + 31) / 32); break;
-      case 1: t += 3LL * B.nk * ((B.ni + 31) / 32); break;
-      case 2: t += B.nc; break;
-      default: t += B.m; break;
-    }
-  }
+  for (int b = 0; b < nb; ++b) t += sep_count(sb[b], kind);
   return t;
 }
 
-// Row pass (stages A and E): out[c][i][j] = sum_k in[c][i][k] V[k][j].
-// mode 0: in = x on the markers (0 on c); mode 1: in = u on c (0 on the
-// markers).  One warp per (body, component, group of SEP_RG rows, 32
-// columns); the rows are gathered into the warp's shared-memory slice.
-static __device__ void sep_rowpass(const SepBody* sb, int nb, int mode, const SepIn& in, const int* voff,
-                            float* sm) {
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  float* xs = sm + wib * SEP_RG * SEP_NK_MAX;
+// Shared memory of the rectangle products and column passes, in floats (the
+// Schur product adds 3 n_c, see sep_smem_bytes).
+constexpr int SEP_GEMM_FLOATS = 3 * SEP_GR * SEP_NK_MAX + SEP_NK_MAX * SEP_GC + SEP_GK * 3 * SEP_GR * SEP_GC;
+constexpr int SEP_COL_FLOATS = SEP_JG * (SEP_NI_MAX * SEP_NI_MAX + 3 * SEP_NI_MAX);
+
+// Rectangle product (stages A, C, E, G), all three components:
+//   trans = false:  R0[c][i][j] = sum_k in[c][i][k] V[k][j]        (to the span modes)
+//   trans = true:   R0[c][i][k] = sum_j in[c][i][j] V[k][j]        (back to the span positions)
+// with in = mode 0: x on the markers (x = a - s b, 0 on the complement),
+// 1: u on the complement (0 on the markers), 2: R1, 3: R1 - R2.  A tile's
+// input rows and its V tile are staged in shared memory; thread (g, r, jj)
+// sums the g-th quarter of the reduction, and the quarters are added in a
+// fixed order.  Needs blockDim.x == SEP_GK * SEP_GR * SEP_GC.
+static __device__ void sep_gemm(const SepBody* sb, int nb, int mode, bool trans, const SepIn& in,
+                                const int* voff, float* sm) {
   const long long total = sep_items(sb, nb, 0);
-  for (long long it = (long long)blockIdx.x * nwarps + wib; it < total; it += (long long)gridDim.x * nwarps) {
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
     long long li = it;
     const int b = sep_item_body(sb, nb, 0, li);
     const SepBody& B = sb[b];
-    const int njc = (B.nk + 31) / 32, nig = (B.ni + SEP_RG - 1) / SEP_RG;
-    const int jc = (int)(li % njc);
-    const int ig = (int)((li / njc) % nig);
-    const int c = (int)(li / ((long long)njc * nig));
-    const int i0 = ig * SEP_RG;
-    __syncwarp();
-    for (int r = 0; r < SEP_RG; ++r) {
+    const int nk = B.nk, ldv = sep_ldv(nk);
+    const int nct = (nk + SEP_GC - 1) / SEP_GC;
+    const int i0 = (int)(li / nct) * SEP_GR, j0 = (int)(li % nct) * SEP_GC;
+    const long long plane = (long long)B.ni * nk;
+    float* xs = sm;                                  // [3][SEP_GR][nk]
+    float* ws = xs + 3 * SEP_GR * nk;                // [nk][SEP_GC]
+    float* red = ws + nk * SEP_GC;                   // [SEP_GK][3][SEP_GR][SEP_GC]
+    __syncthreads();
+    for (int e = threadIdx.x; e < 3 * SEP_GR * nk; e += blockDim.x) {
+      const int c = e / (SEP_GR * nk), r = (e / nk) % SEP_GR, k = e % nk;
       const int i = i0 + r;
-      for (int k = lane; k < B.nk; k += 32) {
-        float v = 0.f;
-        if (i < B.ni) {
-          const int slot = B.rect[i * B.nk + k];
+      float v = 0.f;
+      if (i < B.ni) {
+        if (mode >= 2) {
+          const long long o = c * plane + (long long)i * nk + k;
+          v = __ldcg(B.R1 + o);
+          if (mode == 3) v -= __ldcg(B.R2 + o);
+        } else {
+          const int slot = B.rect[i * nk + k];
           if (mode == 0) {
             if (slot >= 0) {
               const int vi = voff[b] + 3 * slot + c;
@@ -148,157 +167,163 @@ static __device__ void sep_rowpass(const SepBody* sb, int nb, int mode, const Se
             v = __ldcg(B.U + c * B.nc + (-slot - 1));
           }
         }
-        xs[r * SEP_NK_MAX + k] = v;
+      }
+      xs[e] = v;
+    }
+    if (!trans) {
+      // ws[k][jj] = V[k][j0 + jj] (float4 groups; rows are zero padded to ldv)
+      for (int e = threadIdx.x; e < nk * (SEP_GC / 4); e += blockDim.x) {
+        const int k = e / (SEP_GC / 4), jq = 4 * (e % (SEP_GC / 4)), j = j0 + jq;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < ldv) v = __ldg(reinterpret_cast<const float4*>(B.V + (long long)k * ldv + j));
+        *reinterpret_cast<float4*>(ws + k * SEP_GC + jq) = v;
+      }
+    } else {
+      // ws[j][kk] = V[j0 + kk][j]: rows j0 .. j0 + SEP_GC of V, transposed
+      for (int e = threadIdx.x; e < SEP_GC * nk; e += blockDim.x) {
+        const int kk = e / nk, j = e % nk, k = j0 + kk;
+        ws[j * SEP_GC + kk] = k < nk ? __ldg(B.V + (long long)k * ldv + j) : 0.f;
       }
     }
-    __syncwarp();
-    const int j = jc * 32 + lane;
-    if (j < B.nk) {
-      float acc[SEP_RG];
-#pragma unroll
-      for (int r = 0; r < SEP_RG; ++r) acc[r] = 0.f;
-      const float* Vj = B.V + j;
+    __syncthreads();
+    const int g = threadIdx.x / (SEP_GR * SEP_GC), r = (threadIdx.x / SEP_GC) % SEP_GR, jj = threadIdx.x % SEP_GC;
+    const int kq = (nk + SEP_GK - 1) / SEP_GK, k0 = g * kq, k1 = min(nk, k0 + kq);
+    const float* x0 = xs + r * nk;
+    const float* x1 = x0 + SEP_GR * nk;
+    const float* x2 = x1 + SEP_GR * nk;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
 #pragma unroll 4
-      for (int k = 0; k < B.nk; ++k) {
-        const float v = __ldg(Vj + (long long)k * B.nk);
+    for (int k = k0; k < k1; ++k) {
+      const float v = ws[k * SEP_GC + jj];
+      a0 = fmaf(x0[k], v, a0);
+      a1 = fmaf(x1[k], v, a1);
+      a2 = fmaf(x2[k], v, a2);
+    }
+    float* rd = red + (g * 3 * SEP_GR + r) * SEP_GC + jj;
+    rd[0] = a0;
+    rd[SEP_GR * SEP_GC] = a1;
+    rd[2 * SEP_GR * SEP_GC] = a2;
+    __syncthreads();
+    if (g == 0) {
+      const int i = i0 + r, j = j0 + jj;
+      if (i < B.ni && j < nk) {
 #pragma unroll
-        for (int r = 0; r < SEP_RG; ++r) acc[r] = fmaf(xs[r * SEP_NK_MAX + k], v, acc[r]);
+        for (int c = 0; c < 3; ++c) {
+          float t = 0.f;
+#pragma unroll
+          for (int q = 0; q < SEP_GK; ++q) t += red[((q * 3 + c) * SEP_GR + r) * SEP_GC + jj];
+          B.R0[c * plane + (long long)i * nk + j] = t;
+        }
       }
-      float* out = B.R0 + (long long)c * B.ni * B.nk;
-#pragma unroll
-      for (int r = 0; r < SEP_RG; ++r)
-        if (i0 + r < B.ni) out[(long long)(i0 + r) * B.nk + j] = acc[r];
     }
   }
 }
 
-// Column pass (stages B and F): dst[c][i][j] = sum_i2 H_j[i][i2] src[c][i2][j].
-// One warp per (body, component, span mode j, 32 chord rows).
-static __device__ void sep_colpass(const SepBody* sb, int nb, bool second) {
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
+// Column pass (stages B and F): dst[c][i][j] = sum_i2 H_j[i][i2] src[c][i2][j]
+// with src = R0.  One block per group of SEP_JG modes: their H_j and the
+// source columns are staged in shared memory, then one thread per
+// (mode, component, row) output.
+static __device__ void sep_colpass(const SepBody* sb, int nb, bool second, float* sm) {
   const long long total = sep_items(sb, nb, 1);
-  for (long long it = (long long)blockIdx.x * nwarps + wib; it < total; it += (long long)gridDim.x * nwarps) {
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
     long long li = it;
     const int b = sep_item_body(sb, nb, 1, li);
     const SepBody& B = sb[b];
-    const int nic = (B.ni + 31) / 32;
-    const int ic = (int)(li % nic);
-    const int j = (int)((li / nic) % B.nk);
-    const int c = (int)(li / ((long long)nic * B.nk));
-    const int i = ic * 32 + lane;
-    const float* src = B.R0 + (long long)c * B.ni * B.nk + j;
-    float* dst = (second ? B.R2 : B.R1) + (long long)c * B.ni * B.nk + j;
-    const float* h = B.Ht + (long long)j * B.ni * B.ni + i;
-    float acc = 0.f;
-    if (i < B.ni) {
+    const int ni = B.ni, nk = B.nk;
+    const int j0 = (int)li * SEP_JG, nj = min(SEP_JG, nk - j0);
+    const long long plane = (long long)ni * nk;
+    float* hs = sm;                                   // [SEP_JG][ni][ni] in the Ht layout
+    float* ys = sm + SEP_JG * ni * ni;                // [SEP_JG][3][ni]
+    __syncthreads();
+    const float* hsrc = B.Ht + (long long)j0 * ni * ni;
+    for (int e = threadIdx.x; e < nj * ni * ni; e += blockDim.x) hs[e] = __ldg(hsrc + e);
+    for (int e = threadIdx.x; e < nj * 3 * ni; e += blockDim.x) {
+      const int jj = e / (3 * ni), c = (e / ni) % 3, i2 = e % ni;
+      ys[e] = __ldcg(B.R0 + c * plane + (long long)i2 * nk + j0 + jj);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nj * 3 * ni; e += blockDim.x) {
+      const int jj = e / (3 * ni), c = (e / ni) % 3, i = e % ni;
+      const float* h = hs + jj * ni * ni + i;
+      const float* y = ys + (jj * 3 + c) * ni;
+      float acc = 0.f;
 #pragma unroll 4
-      for (int i2 = 0; i2 < B.ni; ++i2) acc = fmaf(__ldg(h + (long long)i2 * B.ni), __ldcg(src + (long long)i2 * B.nk), acc);
-      dst[(long long)i * B.nk] = acc;
+      for (int i2 = 0; i2 < ni; ++i2) acc = fmaf(h[i2 * ni], y[i2], acc);
+      (second ? B.R2 : B.R1)[c * plane + (long long)i * nk + j0 + jj] = acc;
     }
   }
 }
 
-// Stage C: t_p = sum_j Y2[i_p][j] V[k_p][j] for every complement entry p,
-// three components; one warp per entry.
-static __device__ void sep_complement_values(const SepBody* sb, int nb) {
+// Stage D: u = S^-1 t.  One block per 32 rows of a body: t (the complement
+// entries of R0, three components) is staged in shared memory when it fits,
+// then one warp per row; each double-float entry of S^-1 times an FP32 t
+// enters a double-float accumulator (the product's rounding error included).
+static __device__ void sep_schur(const SepBody* sb, int nb, float* sm, int smem_floats) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
   const long long total = sep_items(sb, nb, 2);
-  for (long long it = (long long)blockIdx.x * nwarps + wib; it < total; it += (long long)gridDim.x * nwarps) {
-    long long p = it;
-    const int b = sep_item_body(sb, nb, 2, p);
+  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+    long long li = it;
+    const int b = sep_item_body(sb, nb, 2, li);
     const SepBody& B = sb[b];
-    const int r = B.crect[p];
-    const int i = r / B.nk, k = r - i * B.nk;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    const int nc = B.nc;
     const long long plane = (long long)B.ni * B.nk;
-    const float* y = B.R1 + (long long)i * B.nk;
-    const float* v = B.V + (long long)k * B.nk;
-    for (int j = lane; j < B.nk; j += 32) {
-      const float vj = __ldg(v + j);
-      a0 = fmaf(__ldcg(y + j), vj, a0);
-      a1 = fmaf(__ldcg(y + plane + j), vj, a1);
-      a2 = fmaf(__ldcg(y + 2 * plane + j), vj, a2);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-    }
-    if (lane == 0) {
-      B.Tc[p] = a0;
-      B.Tc[B.nc + p] = a1;
-      B.Tc[2 * B.nc + p] = a2;
-    }
-  }
-}
-
-// Stage D: u = S^-1 t, one warp per row p, three components; each
-// double-float entry of S^-1 times an FP32 t enters a double-float
-// accumulator (the product's rounding error included).
-static __device__ void sep_schur(const SepBody* sb, int nb) {
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  const long long total = sep_items(sb, nb, 2);
-  for (long long it = (long long)blockIdx.x * nwarps + wib; it < total; it += (long long)gridDim.x * nwarps) {
-    long long p = it;
-    const int b = sep_item_body(sb, nb, 2, p);
-    const SepBody& B = sb[b];
+    const bool stage_t = 3 * nc <= smem_floats;
+    __syncthreads();
+    if (stage_t)
+      for (int e = threadIdx.x; e < 3 * nc; e += blockDim.x) {
+        const int c = e / nc, q = e % nc;
+        sm[e] = __ldcg(B.R0 + c * plane + B.crect[q]);
+      }
+    __syncthreads();
+    const int p = (int)li * 32 + wib;
+    if (p >= nc) continue;
     // two (hi, lo) entries per 128-bit load
     const float4* row = reinterpret_cast<const float4*>(B.Sinv + 2LL * p * B.ldc);
     dfacc a0 = acc_zero(), a1 = acc_zero(), a2 = acc_zero();
     const int nq = B.ldc >> 1;
+#pragma unroll 4
     for (int q = lane; q < nq; q += 32) {
-      const float4 s = __ldg(row + q);
-      const df sv[2] = {df_make(s.x, s.y), df_make(s.z, s.w)};
+      const float4 s4 = __ldg(row + q);
+      const df sv[2] = {df_make(s4.x, s4.y), df_make(s4.z, s4.w)};
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const int col = 2 * q + e;
-        if (col < B.nc) {
-          acc_fma_f(a0, sv[e], __ldcg(B.Tc + col));
-          acc_fma_f(a1, sv[e], __ldcg(B.Tc + B.nc + col));
-          acc_fma_f(a2, sv[e], __ldcg(B.Tc + 2 * B.nc + col));
+        if (col < nc) {
+          float t0, t1, t2;
+          if (stage_t) {
+            t0 = sm[col];
+            t1 = sm[nc + col];
+            t2 = sm[2 * nc + col];
+          } else {
+            const int r = B.crect[col];
+            t0 = __ldcg(B.R0 + r);
+            t1 = __ldcg(B.R0 + plane + r);
+            t2 = __ldcg(B.R0 + 2 * plane + r);
+          }
+          acc_fma_f(a0, sv[e], t0);
+          acc_fma_f(a1, sv[e], t1);
+          acc_fma_f(a2, sv[e], t2);
         }
       }
     }
     const df u0 = df_warp_sum(acc_value(a0)), u1 = df_warp_sum(acc_value(a1)), u2 = df_warp_sum(acc_value(a2));
     if (lane == 0) {
       B.U[p] = u0.hi + u0.lo;
-      B.U[B.nc + p] = u1.hi + u1.lo;
-      B.U[2 * B.nc + p] = u2.hi + u2.lo;
+      B.U[nc + p] = u1.hi + u1.lo;
+      B.U[2 * nc + p] = u2.hi + u2.lo;
     }
   }
 }
 
-// Stage G for one marker (local index l of body B), in every lane of the
-// calling warp: z[c] = sum_j (Y2 - W2)[c][i_l][j] V[k_l][j].
+// z of one marker (local index l of body B) after stage G: its entry of
+// the R0 rectangle, three components.
 __device__ __forceinline__ void sep_marker_z(const SepBody& B, int l, float z[3]) {
-  const int lane = threadIdx.x & 31;
-  const int r = B.mrect[l];
-  const int i = r / B.nk, k = r - i * B.nk;
   const long long plane = (long long)B.ni * B.nk;
-  const float* y = B.R1 + (long long)i * B.nk;
-  const float* w = B.R2 + (long long)i * B.nk;
-  const float* v = B.V + (long long)k * B.nk;
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-  for (int j = lane; j < B.nk; j += 32) {
-    const float vj = __ldg(v + j);
-    a0 = fmaf(__ldcg(y + j) - __ldcg(w + j), vj, a0);
-    a1 = fmaf(__ldcg(y + plane + j) - __ldcg(w + plane + j), vj, a1);
-    a2 = fmaf(__ldcg(y + 2 * plane + j) - __ldcg(w + 2 * plane + j), vj, a2);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-  }
-  z[0] = a0;
-  z[1] = a1;
-  z[2] = a2;
+  const int r = B.mrect[l];
+  z[0] = __ldcg(B.R0 + r);
+  z[1] = __ldcg(B.R0 + plane + r);
+  z[2] = __ldcg(B.R0 + 2 * plane + r);
 }
 
 }  // namespace ibl
