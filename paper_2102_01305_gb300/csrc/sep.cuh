@@ -118,6 +118,26 @@ __device__ __forceinline__ long long sep_items(const SepBody* sb, int nb, int ki
   return t;
 }
 
+// dst[e] = f(e) for e < n by the whole block, U elements per thread per pass:
+// the U loads (or load chains) of a thread are issued before the first store,
+// so a pass costs one round trip instead of U.
+template <int U, class F>
+__device__ __forceinline__ void sep_stage(float* dst, int n, F f) {
+  for (int base = 0; base < n; base += U * (int)blockDim.x) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * (int)blockDim.x + (int)threadIdx.x;
+      v[u] = e < n ? f(e) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * (int)blockDim.x + (int)threadIdx.x;
+      if (e < n) dst[e] = v[u];
+    }
+  }
+}
+
 // Shared memory of the rectangle products and column passes, in floats (the
 // Schur product adds 3 n_c, see sep_smem_bytes).
 constexpr int SEP_GEMM_FLOATS = 3 * SEP_GR * SEP_NK_MAX + SEP_NK_MAX * SEP_GC + SEP_GK * 3 * SEP_GR * SEP_GC;
@@ -146,44 +166,47 @@ static __device__ void sep_gemm(const SepBody* sb, int nb, int mode, bool trans,
     float* ws = xs + 3 * SEP_GR * nk;                // [nk][SEP_GC]
     float* red = ws + nk * SEP_GC;                   // [SEP_GK][3][SEP_GR][SEP_GC]
     __syncthreads();
-    for (int e = threadIdx.x; e < 3 * SEP_GR * nk; e += blockDim.x) {
+    const int ni = B.ni, nc = B.nc;
+    const int* rect = B.rect;
+    const float *R1 = B.R1, *R2 = B.R2, *Uc = B.U, *V = B.V;
+    const float *ina = in.a, *inb = in.b;
+    const int vo = voff[b];
+    sep_stage<8>(xs, 3 * SEP_GR * nk, [&](int e) {
       const int c = e / (SEP_GR * nk), r = (e / nk) % SEP_GR, k = e % nk;
       const int i = i0 + r;
       float v = 0.f;
-      if (i < B.ni) {
+      if (i < ni) {
         if (mode >= 2) {
           const long long o = c * plane + (long long)i * nk + k;
-          v = __ldcg(B.R1 + o);
-          if (mode == 3) v -= __ldcg(B.R2 + o);
+          v = __ldcg(R1 + o);
+          if (mode == 3) v -= __ldcg(R2 + o);
         } else {
-          const int slot = B.rect[i * nk + k];
+          const int slot = rect[i * nk + k];
           if (mode == 0) {
             if (slot >= 0) {
-              const int vi = voff[b] + 3 * slot + c;
-              v = __ldcg(in.a + vi);
-              if (in.b) v = fmaf(-in.s[c], __ldcg(in.b + vi), v);
+              const int vi = vo + 3 * slot + c;
+              v = __ldcg(ina + vi);
+              if (inb) v = fmaf(-in.s[c], __ldcg(inb + vi), v);
             }
           } else if (slot < 0) {
-            v = __ldcg(B.U + c * B.nc + (-slot - 1));
+            v = __ldcg(Uc + c * nc + (-slot - 1));
           }
         }
       }
-      xs[e] = v;
-    }
+      return v;
+    });
     if (!trans) {
-      // ws[k][jj] = V[k][j0 + jj] (float4 groups; rows are zero padded to ldv)
-      for (int e = threadIdx.x; e < nk * (SEP_GC / 4); e += blockDim.x) {
-        const int k = e / (SEP_GC / 4), jq = 4 * (e % (SEP_GC / 4)), j = j0 + jq;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < ldv) v = __ldg(reinterpret_cast<const float4*>(B.V + (long long)k * ldv + j));
-        *reinterpret_cast<float4*>(ws + k * SEP_GC + jq) = v;
-      }
+      // ws[k][jj] = V[k][j0 + jj] (rows are zero padded to ldv)
+      sep_stage<8>(ws, nk * SEP_GC, [&](int e) {
+        const int k = e / SEP_GC, j = j0 + e % SEP_GC;
+        return j < ldv ? __ldg(V + (long long)k * ldv + j) : 0.f;
+      });
     } else {
       // ws[j][kk] = V[j0 + kk][j]: rows j0 .. j0 + SEP_GC of V, transposed
-      for (int e = threadIdx.x; e < SEP_GC * nk; e += blockDim.x) {
-        const int kk = e / nk, j = e % nk, k = j0 + kk;
-        ws[j * SEP_GC + kk] = k < nk ? __ldg(B.V + (long long)k * ldv + j) : 0.f;
-      }
+      sep_stage<8>(ws, SEP_GC * nk, [&](int e) {
+        const int j = e / SEP_GC, kk = e % SEP_GC, k = j0 + kk;
+        return k < nk ? __ldg(V + (long long)k * ldv + j) : 0.f;
+      });
     }
     __syncthreads();
     const int g = threadIdx.x / (SEP_GR * SEP_GC), r = (threadIdx.x / SEP_GC) % SEP_GR, jj = threadIdx.x % SEP_GC;
@@ -236,11 +259,12 @@ static __device__ void sep_colpass(const SepBody* sb, int nb, bool second, float
     float* ys = sm + SEP_JG * ni * ni;                // [SEP_JG][3][ni]
     __syncthreads();
     const float* hsrc = B.Ht + (long long)j0 * ni * ni;
-    for (int e = threadIdx.x; e < nj * ni * ni; e += blockDim.x) hs[e] = __ldg(hsrc + e);
-    for (int e = threadIdx.x; e < nj * 3 * ni; e += blockDim.x) {
+    const float* R0 = B.R0;
+    sep_stage<8>(hs, nj * ni * ni, [&](int e) { return __ldg(hsrc + e); });
+    sep_stage<1>(ys, nj * 3 * ni, [&](int e) {
       const int jj = e / (3 * ni), c = (e / ni) % 3, i2 = e % ni;
-      ys[e] = __ldcg(B.R0 + c * plane + (long long)i2 * nk + j0 + jj);
-    }
+      return __ldcg(R0 + c * plane + (long long)i2 * nk + j0 + jj);
+    });
     __syncthreads();
     for (int e = threadIdx.x; e < nj * 3 * ni; e += blockDim.x) {
       const int jj = e / (3 * ni), c = (e / ni) % 3, i = e % ni;
@@ -270,11 +294,14 @@ static __device__ void sep_schur(const SepBody* sb, int nb, float* sm, int smem_
     const long long plane = (long long)B.ni * B.nk;
     const bool stage_t = 3 * nc <= smem_floats;
     __syncthreads();
-    if (stage_t)
-      for (int e = threadIdx.x; e < 3 * nc; e += blockDim.x) {
+    if (stage_t) {
+      const float* R0 = B.R0;
+      const int* crect = B.crect;
+      sep_stage<8>(sm, 3 * nc, [&](int e) {
         const int c = e / nc, q = e % nc;
-        sm[e] = __ldcg(B.R0 + c * plane + B.crect[q]);
-      }
+        return __ldcg(R0 + c * plane + crect[q]);
+      });
+    }
     __syncthreads();
     const int p = (int)li * 32 + wib;
     if (p >= nc) continue;
