@@ -222,6 +222,61 @@ __device__ __forceinline__ void gather_pair(const DirPtrs<Q, T>& P, int x, int y
   }
 }
 
+// As gather_pair, with every load an aligned 32-bit word: per direction each
+// thread loads the word (x, x + 1) of its source row; for c_x = +1 the value
+// at x - 1 is the high half of the previous lane's word, for c_x = -1 the
+// value at x + 2 the low half of the next lane's word (lanes hold x, x + 2,
+// ... of one row: the block is 64 threads wide in x).  The first lane, the
+// last lane and lanes at the row's ends load that value directly.  Every
+// lane of the warp must call it (shuffles); lanes outside the grid pass
+// clamped coordinates and discard the result.  The values are those of
+// gather_pair, bit for bit.
+template <int Q, class T, class R>
+__device__ __forceinline__ void gather_pair_words(const DirPtrs<Q, T>& P, int x, int y, int z,
+                                                  const FluidParams<R>& p, R ga[Q], R gb[Q]) {
+  const int lane = threadIdx.x & 31;
+  int xm = x - 1, xp = x + 2;
+  if (xm < 0) xm += p.nx;
+  if (xp >= p.nx) xp -= p.nx;
+  const bool own_left = lane == 0 || x == 0;              // x - 1 not in the previous lane
+  const bool own_right = lane == 31 || x + 2 >= p.nx;     // x + 2 not in the next lane
+  int ys[3] = {y - 1, y, y + 1};
+  if (ys[0] < 0) ys[0] += p.ny;
+  if (ys[2] >= p.ny) ys[2] -= p.ny;
+  int zs[3] = {z - 1, z, z + 1};
+  if (Lat<Q>::D == 3) {
+    if (zs[0] < 0) zs[0] += p.nz;
+    if (zs[2] >= p.nz) zs[2] -= p.nz;
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int dy = 1 - Lat<Q>::cy(i), dz = 1 - Lat<Q>::cz(i);
+    const int row = (zs[dz] * p.ny + ys[dy]) * p.nx;
+    const Pair16<T> w = *reinterpret_cast<const Pair16<T>*>(P.s[i] + row + x);
+    const unsigned bits = *reinterpret_cast<const unsigned*>(&w);
+    if (Lat<Q>::cx(i) == 0) {
+      ga[i] = Store<T>::ld(w.a);
+      gb[i] = Store<T>::ld(w.b);
+    } else if (Lat<Q>::cx(i) > 0) {
+      // sources x - 1, x
+      const unsigned prev = __shfl_up_sync(0xffffffffu, bits, 1);
+      Pair16<T> pw;
+      *reinterpret_cast<unsigned*>(&pw) = prev;
+      const T left = own_left ? P.s[i][row + xm] : pw.b;
+      ga[i] = Store<T>::ld(left);
+      gb[i] = Store<T>::ld(w.a);
+    } else {
+      // sources x + 1, x + 2
+      const unsigned next = __shfl_down_sync(0xffffffffu, bits, 1);
+      Pair16<T> nw;
+      *reinterpret_cast<unsigned*>(&nw) = next;
+      const T right = own_right ? P.s[i][row + xp] : nw.a;
+      ga[i] = Store<T>::ld(w.b);
+      gb[i] = Store<T>::ld(right);
+    }
+  }
+}
+
 // Band correction, collision and divergence check of one cell (the part of
 // collide_cell between the pull and the store).
 template <int Q, bool IB, class R>
@@ -241,21 +296,24 @@ __device__ __forceinline__ void collide_only(R g[Q], const FluidParams<R>& p, in
 
 // Every cell of a grid with even nx: 128 x 4 cells per 256-thread block;
 // four blocks per SM (64 registers) where that does not spill, three with
-// the band lookup.
+// the band lookup.  The pulls are aligned 32-bit words (gather_pair_words).
 template <int Q, class T, bool IB>
 __global__ void __launch_bounds__(256, IB ? 3 : 4) k_collide_pairs(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p) {
   using R = typename Store<T>::R;
   const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x >= p.nx || y >= p.ny) return;
+  // every lane takes part in the word loads and shuffles; lanes outside the
+  // grid read a clamped row and store nothing
+  const bool inside = x < p.nx && y < p.ny;
+  R ga[Q], gb[Q];
+  gather_pair_words<Q, T, R>(P, inside ? x : p.nx - 2, inside ? y : p.ny - 1, z, p, ga, gb);
+  if (!inside) return;
   if (on_special_face<R>(x, y, z, Lat<Q>::D, p) || on_special_face<R>(x + 1, y, z, Lat<Q>::D, p)) {
     collide_cell<Q, T, true, IB>(P, p, x, y, z);
     collide_cell<Q, T, true, IB>(P, p, x + 1, y, z);
     return;
   }
-  R ga[Q], gb[Q];
-  gather_pair<Q, T, R>(P, x, y, z, p, ga, gb);
   collide_only<Q, IB, R>(ga, p, x, y, z);
   collide_only<Q, IB, R>(gb, p, x + 1, y, z);
   const int cell = (z * p.ny + y) * p.nx + x;
