@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--mean-gap", type=float, default=2.0, help="mean Poisson inter-arrival gap, s")
     ap.add_argument("--run-steps", type=int, default=10000)
     ap.add_argument("--mix", default="mixed", choices=["mixed", "fp32", "fp16dev", "bf16dev"])
+    ap.add_argument("--serve-tune", type=int, default=1, choices=[0, 1],
+                    help="serving: 1 per-request launch tuning, 0 library defaults")
     ap.add_argument("--serving-sample", type=int, default=12,
                     help="requests of the short serving sample in the default line (0: none)")
     ap.add_argument("--e2e-steps", type=int, default=300)
@@ -614,13 +616,13 @@ def sweep_requests(n: int, run_steps: int, mix: str, seed: int = 20210203):
     return out
 
 
-def run_serving(n: int, mean_gap: float, run_steps: int, mix: str, budget_frac: float = 0.8):
+def run_serving(n: int, mean_gap: float, run_steps: int, mix: str, budget_frac: float = 0.8, tune: int = 1):
     """Submit a Poisson stream of sweep requests, wait, report solves/h and latency."""
     import numpy as np
     import torch
     from paper_2102_01305_gb300 import ibl
     free, total = torch.cuda.mem_get_info()
-    srv = ibl.Server(hbm_budget_bytes=int(free * budget_frac), max_active=16, chunk_steps=50)
+    srv = ibl.Server(hbm_budget_bytes=int(free * budget_frac), max_active=16, chunk_steps=50, tune=tune)
     reqs = sweep_requests(n, run_steps, mix)
     rng = np.random.default_rng(7)
     gaps = rng.exponential(mean_gap, size=n)
@@ -640,6 +642,7 @@ def run_serving(n: int, mean_gap: float, run_steps: int, mix: str, budget_frac: 
     srv.ibl_server_wait_all(24 * 3600.0)
     wall = time.perf_counter() - t0
     res = [srv.ibl_server_poll(i) for i in ids]
+    load = srv.ibl_server_load()
     srv.close()
     reqs = admitted
     ok = [r for r in res if r["status"] == ibl.IBL_OK]
@@ -650,8 +653,15 @@ def run_serving(n: int, mean_gap: float, run_steps: int, mix: str, budget_frac: 
             "refused_unstable": refused, "failed": len(res) - len(ok),
             "failure_statuses": sorted({ibl.STATUS_NAMES[r["status"]] for r in res if r["status"] != ibl.IBL_OK}),
             "p50_latency_s": q(50), "p99_latency_s": q(99), "wall_s": wall, "mean_gap_s": mean_gap,
-            "steps_per_run": run_steps, "precision_mix": mix,
-            "aggregate_glups": cells / wall / 1e9}
+            "steps_per_run": run_steps, "precision_mix": mix, "tune": tune,
+            "aggregate_glups": cells / wall / 1e9,
+            "scheduler": {"busy_frac": load["busy_s"] / max(load["wall_s"], 1e-9),
+                          "enqueue_s": load["enqueue_s"], "build_s": load["build_s"],
+                          "retire_s": load["retire_s"], "wall_s": load["wall_s"]},
+            "launches": sorted({(r["solve_blocks"], r["overlap"], tuple(r["collide_shape"]))
+                                for r in res if r["tuned"]}),
+            "runs": [[rq["nx"], rq["chord"], rq["Re"], rq["period"], rq["J"], rq["precision"],
+                      ibl.STATUS_NAMES[r["status"]], r["steps_done"]] for rq, r in zip(reqs, res)]}
 
 
 def run_ib_sweep(args):
@@ -774,7 +784,7 @@ def main():
     elif args.ib_sweep:
         run_ib_sweep(args)
     elif args.serving:
-        r = run_serving(args.requests, args.mean_gap, args.run_steps, args.mix)
+        r = run_serving(args.requests, args.mean_gap, args.run_steps, args.mix, tune=args.serve_tune)
         print(json.dumps({"metric": METRIC, "value": round(r["solves_per_hour"], 2), "unit": "solves/h",
                           "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                           "data": "synthetic (seeded sweep of the paper's Re, f, J grid)",

@@ -322,6 +322,16 @@ ibl_status ibl_solver_preconditioner(ibl_ctx* ctx, int32_t kind, int32_t residen
  * populations and forces (every cell runs the same arithmetic). */
 ibl_status ibl_set_overlap(ibl_ctx* ctx, int32_t mode);
 
+/* Launch shape of the one-kernel collide (the kernel of steps without the
+ * split, see ibl_set_overlap): thread blocks of bx x by threads, bx in
+ * {32, 64, 128, 256}, bx * by <= 256 (default 64 x 4); pairs = 1 (default)
+ * gives each thread the two x-adjacent cells (x, x + 1) when the storage is
+ * 16-bit and nx even, their collisions run as packed FP32 pairs; pairs = 0
+ * one cell per thread.  Every cell runs the same rounded operations whatever
+ * the shape, so all shapes give bitwise the same populations (a tuning knob,
+ * not a numerical one).  IBL_EINVAL for other values. */
+ibl_status ibl_set_collide_shape(ibl_ctx* ctx, int32_t bx, int32_t by, int32_t pairs);
+
 /* Phase timestamps (GPU global timer, ns, taken by block 0) of the last
  * implicit solve: [0] start, [1] after the optional preconditioner rebuild,
  * [2] after set-up, [3] end; [4]-[7] the four phases of the rebuild's first
@@ -383,6 +393,7 @@ typedef struct {
   int64_t hbm_budget_bytes;  /* device memory the active runs may use together */
   int32_t max_active;        /* runs advanced concurrently */
   int32_t chunk_steps;       /* steps enqueued per run between scheduling passes */
+  int32_t tune;              /* 1: per-request launch tuning (see below); 0: library defaults */
 } ibl_server_config;
 
 /* One clap-and-fling run: D3Q19 box nx x ny x nz, two flat elliptic wings of
@@ -410,8 +421,23 @@ typedef struct {
   double submit_s, start_s, finish_s;   /* server clock, seconds since creation */
   double CL_max[2], CL_mean[2], CT_max[2], CT_mean[2];   /* per wing over the run */
   double CL_last[2], CT_last[2];
+  /* launch configuration the run used (tune = 1): solve blocks, overlap
+   * mode and collide shape after its tuning chunk (0 where not set) */
+  int32_t solve_blocks, overlap, collide_bx, collide_by, collide_pairs, tuned;
 } ibl_run_result;
 
+/* Per-request tuning (tune = 1).  The solve's block count changes its
+ * reduction order, so it is a function of the request alone: one block per
+ * 64 markers, between 4 and half the SMs (small runs then leave SMs to the
+ * others' kernels).  The overlap mode and the collide shape give bitwise the
+ * same results whatever their values (ibl_set_overlap,
+ * ibl_set_collide_shape), so they are measured: the first chunk of a run
+ * whose shape (grid, chord, precision, faces) has not been seen is split
+ * between the candidates (split step; one kernel with 64 x 4, 128 x 2,
+ * 32 x 8 and 256 x 1 blocks), each timed with CUDA events on the run's
+ * stream, and the fastest is kept for that run and every later run of the
+ * same shape.  A run's numbers therefore depend on its request only, alone
+ * or in any mix. */
 /* Create a server on the current device (starts its scheduling thread). */
 ibl_status ibl_server_create(const ibl_server_config* cfg, ibl_server** out);
 /* Queue a run; *run_id identifies it.  IBL_EINVAL for a malformed request or
@@ -432,6 +458,14 @@ ibl_status ibl_server_poll(ibl_server* s, int64_t run_id, ibl_run_result* out);
 ibl_status ibl_server_wait_all(ibl_server* s, double timeout_s);
 ibl_status ibl_server_stats(ibl_server* s, int32_t* queued, int32_t* active, int32_t* finished,
                             int64_t* hbm_in_use);
+/* Where the scheduling thread's time went since the server was created:
+ * wall_s in total, busy_s in scheduling passes that did work (the rest it
+ * slept), and of busy_s: enqueue_s enqueueing steps (ibl_step), build_s
+ * creating run contexts, retire_s reading results and destroying contexts.
+ * busy_s close to wall_s with the GPU not saturated means the host thread
+ * bounds the throughput.  Any pointer may be NULL. */
+ibl_status ibl_server_load(ibl_server* s, double* wall_s, double* busy_s, double* enqueue_s, double* build_s,
+                           double* retire_s);
 /* Stop the scheduler and release every run. */
 ibl_status ibl_server_destroy(ibl_server* s);
 

@@ -77,6 +77,8 @@ struct ibl_ctx {
   cudaEvent_t ev_tiles = nullptr;   // band tiles of the step assigned (stream)
   cudaEvent_t ev_bulk = nullptr;    // bulk collide done (stream_bulk)
   int overlap = -1;                 // -1 automatic, 0 off, 1 on
+  int collide_bx = 64, collide_by = 4;   // thread block of the one-kernel collide
+  bool collide_pairs = true;         // two cells per thread where the storage and nx allow
   size_t elem = 4;               // bytes per stored population
   void* f[2] = {nullptr, nullptr};
   int cur = 0;

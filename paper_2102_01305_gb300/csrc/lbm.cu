@@ -47,62 +47,202 @@ __device__ __forceinline__ int band_du(int x, int y, int z, const FluidParams<R>
   return slot * 3 * TILE_CELLS + local;
 }
 
+// ------------------------------------------------------------------ collision arithmetic
+// Every operation of the collision is an explicit IEEE operation rounded on
+// its own, so the result is fixed by the source.  Sc<R> runs it on one cell;
+// Pk runs it on two cells at once with Blackwell's packed FP32 instructions
+// (add/sub/mul/fma .rn.f32x2 round each lane exactly as the scalar
+// instruction does), so the two-cell kernel and the one-cell kernels give
+// bitwise the same populations.  One rule keeps that true: no product feeds
+// an addition or subtraction.  The assembler fuses a packed multiply and a
+// packed add that follows it into one FMA even with .rn on both (measured
+// on sm_103a; the scalar .rn forms are left alone), so wherever a product
+// meets a sum the collision uses an explicit FMA instead.
+template <class R> struct Sc;
+template <> struct Sc<float> {
+  using R = float;
+  using V = float;
+  static __device__ __forceinline__ V splat(R s) { return s; }
+  static __device__ __forceinline__ V add(V a, V b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ V mul(V a, V b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ V div(V a, V b) { return __fdiv_rn(a, b); }
+};
+template <> struct Sc<double> {
+  using R = double;
+  using V = double;
+  static __device__ __forceinline__ V splat(R s) { return s; }
+  static __device__ __forceinline__ V add(V a, V b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ V mul(V a, V b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ V div(V a, V b) { return __ddiv_rn(a, b); }
+};
+
+// Uniform coefficients (one rounded product, the same in every lane).
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+
+// Two FP32 lanes in one 64-bit register pair: lo = cell x, hi = cell x + 1.
+struct F2 {
+  unsigned long long v;
+};
+struct Pk {
+  using R = float;
+  using V = F2;
+  static __device__ __forceinline__ V make(float lo, float hi) {
+    V r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+  }
+  static __device__ __forceinline__ float lo(V a) {
+    float l, h;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(a.v));
+    return l;
+  }
+  static __device__ __forceinline__ float hi(V a) {
+    float l, h;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(a.v));
+    return h;
+  }
+  static __device__ __forceinline__ V splat(R s) { return make(s, s); }
+  static __device__ __forceinline__ V add(V a, V b) {
+    V r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+  }
+  static __device__ __forceinline__ V sub(V a, V b) {
+    V r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+  }
+  static __device__ __forceinline__ V mul(V a, V b) {
+    V r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+  }
+  static __device__ __forceinline__ V fma(V a, V b, V c) {
+    V r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+  }
+  // no packed division: one IEEE division per lane
+  static __device__ __forceinline__ V div(V a, V b) {
+    return make(__fdiv_rn(lo(a), lo(b)), __fdiv_rn(hi(a), hi(b)));
+  }
+};
+
+// c_a u_a + c_b u_b of the first member of a direction pair.  In both
+// lattices the first member's first nonzero component is +1, so the sum is
+// u_a, u_a + u_b or u_a - u_b: no negation.
+template <int Q, class O>
+__device__ __forceinline__ typename O::V dir_dot(int i, const typename O::V v[3]) {
+  const int c[3] = {Lat<Q>::cx(i), Lat<Q>::cy(i), Lat<Q>::cz(i)};
+  typename O::V s{};
+  bool have = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (c[a] == 0) continue;
+    if (!have) s = v[a];
+    else s = c[a] > 0 ? O::add(s, v[a]) : O::sub(s, v[a]);
+    have = true;
+  }
+  return s;
+}
+
 // BGK collision with the Guo source (Eqs. 7-8) in deviation form g = f - w.
 // Pairs (c, -c) share |c.u| and |c.F|: the even part of f_eq and of the
 // source is computed once per pair, the odd part flips sign.  rho = 1 + drho
 // is never formed in the storage precision where it would drop drho's low
 // bits: rho X = X + drho X and u = m - m drho/(1 + drho).  Returns drho.
-// F is the uniform body force G plus the IB force density 2 rho du (Eq. 26),
-// formed here from this cell's own density; F is returned in F.
-template <int Q, class R>
-__device__ __forceinline__ R collide(R g[Q], R F[3], const R du[3], const FluidParams<R>& p) {
-  R drho = g[0], m0 = R(0), m1 = R(0), m2 = R(0);
+// F is the uniform body force G plus, with IB, the IB force density
+// 2 rho du (Eq. 26) formed here from this cell's own density; F is returned
+// in F.  Without IB, du = 0 and F = G exactly (G carries no negative zero).
+template <int Q, bool IB, class O>
+__device__ __forceinline__ typename O::V collide_v(typename O::V g[Q], typename O::V F[3],
+                                                   const typename O::V du[3],
+                                                   const FluidParams<typename O::R>& p) {
+  using V = typename O::V;
+  using R = typename O::R;
+  V drho = g[0];
+  V m[3];
+  bool have[3] = {false, false, false};
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
-    drho += g[i] + g[i + 1];
-    const R d = g[i] - g[i + 1];
-    if (Lat<Q>::cx(i)) m0 += R(Lat<Q>::cx(i)) * d;
-    if (Lat<Q>::cy(i)) m1 += R(Lat<Q>::cy(i)) * d;
-    if (Lat<Q>::cz(i)) m2 += R(Lat<Q>::cz(i)) * d;
-  }
-  // 2 rho du = 2 du + 2 drho du (rho = 1 + drho is not formed in low precision)
+    drho = O::add(drho, O::add(g[i], g[i + 1]));
+    const V d = O::sub(g[i], g[i + 1]);
+    const int c[3] = {Lat<Q>::cx(i), Lat<Q>::cy(i), Lat<Q>::cz(i)};
 #pragma unroll
-  for (int c = 0; c < 3; ++c) F[c] = p.G[c] + (R(2) * du[c] + R(2) * drho * du[c]);
-  // Eq. 9: rho u = sum c_i f_i + F/2
-  const R q = drho / (R(1) + drho);
-  R u0 = m0 + R(0.5) * F[0], u1 = m1 + R(0.5) * F[1], u2 = m2 + R(0.5) * F[2];
-  u0 -= u0 * q;
-  u1 -= u1 * q;
-  u2 -= u2 * q;
-  const R usq = u0 * u0 + u1 * u1 + u2 * u2;
-  const R uF = u0 * F[0] + u1 * F[1] + u2 * F[2];
-  const R om = p.omega;
+    for (int a = 0; a < 3; ++a) {
+      if (c[a] == 0) continue;
+      if (!have[a]) m[a] = c[a] > 0 ? d : O::sub(O::splat(R(0)), d);
+      else m[a] = c[a] > 0 ? O::add(m[a], d) : O::sub(m[a], d);
+      have[a] = true;
+    }
+  }
+  if (Lat<Q>::D == 2) m[2] = O::splat(R(0));
+  // 2 rho du = 2 du + drho (2 du) (rho = 1 + drho is not formed in low precision)
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (IB) {
+      const V t = O::mul(O::splat(R(2)), du[a]);
+      F[a] = O::add(O::splat(p.G[a]), O::fma(drho, t, t));
+    } else {
+      F[a] = O::splat(p.G[a]);
+    }
+  }
+  // Eq. 9: rho u = sum c_i f_i + F/2, u = (m + F/2) - (m + F/2) drho/(1 + drho)
+  const V nq = O::div(drho, O::sub(O::splat(R(-1)), drho));   // -drho/(1 + drho), exactly
+  V u[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    u[a] = O::fma(O::splat(R(0.5)), F[a], m[a]);
+    u[a] = O::fma(u[a], nq, u[a]);
+  }
+  const V usq = O::fma(u[2], u[2], O::fma(u[1], u[1], O::mul(u[0], u[0])));
+  const V uF = O::fma(u[2], F[2], O::fma(u[1], F[1], O::mul(u[0], F[0])));
+  const V X = O::mul(O::splat(R(-1.5)), usq);       // -1.5 u.u
+  const V m3uF = O::mul(O::splat(R(-3)), uF);       // -3 u.F
+  const V nom = O::splat(-p.omega);
+  const R pref = p.pref;
   {
-    // rest population: f_eq - w = w (drho - 1.5 rho u.u)
+    // rest population: f_eq - w = w (drho - 1.5 rho u.u); source -3 pref w u.F
+    //   g0 - omega (g0 - w E0) + (pref w) (-3 u.F)
     const R w = R(Lat<Q>::w(0));
-    const R X = R(-1.5) * usq;
-    const R geq = w * (drho + X + drho * X);
-    const R S = p.pref * w * (R(-3) * uF);
-    g[0] = g[0] - om * (g[0] - geq) + S;
+    const V E0 = O::add(drho, O::fma(drho, X, X));
+    const V t = O::fma(O::splat(-w), E0, g[0]);                        // g0 - w E0
+    g[0] = O::fma(O::splat(rn_mul(pref, w)), m3uF, O::fma(nom, t, g[0]));
   }
 #pragma unroll
   for (int i = 1; i < Q; i += 2) {
-    const R cu = R(Lat<Q>::cx(i)) * u0 + R(Lat<Q>::cy(i)) * u1 + R(Lat<Q>::cz(i)) * u2;
-    const R cF = R(Lat<Q>::cx(i)) * F[0] + R(Lat<Q>::cy(i)) * F[1] + R(Lat<Q>::cz(i)) * F[2];
+    const V cu = dir_dot<Q, O>(i, u);
+    const V cF = dir_dot<Q, O>(i, F);
     const R w = R(Lat<Q>::w(i));
     const R wo = w3<Q, R>(i);
-    // Eq. 4 (second-order expansion): even part rho(4.5 cu^2 - 1.5 u.u), odd part 3 rho cu
-    const R Xe = R(4.5) * cu * cu - R(1.5) * usq;
-    const R ge = w * (drho + Xe + drho * Xe);
-    const R go = wo * (cu + drho * cu);
-    // Eq. 8: pref w [3 (c - u).F + 9 (c.u)(c.F)]: even 9 cu cF - 3 uF, odd 3 cF
-    const R Se = p.pref * w * (R(9) * cu * cF - R(3) * uF);
-    const R So = p.pref * wo * cF;
-    const R a = g[i], b = g[i + 1];
-    g[i] = a - om * (a - (ge + go)) + (Se + So);
-    g[i + 1] = b - om * (b - (ge - go)) + (Se - So);
+    const R pwo = rn_mul(pref, wo);
+    // Eq. 4 (second-order expansion): even part rho w (4.5 cu^2 - 1.5 u.u),
+    // odd part 3 w rho cu; f_eq - w = ge +/- wo (cu + drho cu)
+    const V Xe = O::fma(O::mul(O::splat(R(4.5)), cu), cu, X);
+    const V ge = O::mul(O::splat(w), O::add(drho, O::fma(drho, Xe, Xe)));
+    const V Oc = O::fma(drho, cu, cu);
+    const V eq_p = O::fma(O::splat(wo), Oc, ge);
+    const V eq_m = O::fma(O::splat(-wo), Oc, ge);
+    // Eq. 8: pref w [3 (c - u).F + 9 (c.u)(c.F)]: even pref w (9 cu cF - 3 uF),
+    // odd +/- pref wo cF
+    const V Se = O::mul(O::splat(rn_mul(pref, w)), O::fma(O::mul(O::splat(R(9)), cu), cF, m3uF));
+    const V S_p = O::fma(O::splat(pwo), cF, Se);
+    const V S_m = O::fma(O::splat(-pwo), cF, Se);
+    const V a = g[i], b = g[i + 1];
+    g[i] = O::add(O::fma(nom, O::sub(a, eq_p), a), S_p);
+    g[i + 1] = O::add(O::fma(nom, O::sub(b, eq_m), b), S_m);
   }
   return drho;
+}
+
+template <int Q, bool IB, class R>
+__device__ __forceinline__ R collide(R g[Q], R F[3], const R du[3], const FluidParams<R>& p) {
+  return collide_v<Q, IB, Sc<R>>(g, F, du, p);
 }
 
 // Per-direction base pointers of the two population buffers (kernel
@@ -166,7 +306,7 @@ __device__ __forceinline__ void collide_cell(const DirPtrs<Q, T>& P, const Fluid
   R du[3] = {R(0), R(0), R(0)};
   int band = -1;
   if (IB) band = band_du<Q, R>(x, y, z, p, du);
-  const R drho = collide<Q, R>(g, F, du, p);
+  const R drho = collide<Q, IB, R>(g, F, du, p);
   if (!(drho > R(-1) && drho < R(99))) atomicOr(p.status, ST_DIVERGED);
 #pragma unroll
   for (int i = 0; i < Q; ++i) P.d[i][cell] = Store<T>::st(g[i]);
@@ -182,58 +322,50 @@ __device__ __forceinline__ void collide_cell(const DirPtrs<Q, T>& P, const Fluid
 // With 2-byte populations one cell per thread keeps too few bytes in flight
 // to cover HBM latency (the kernel then runs at ~0.56 of the bandwidth
 // bound).  Here a thread takes the x-adjacent cells (x, x + 1), x even and nx
-// even.  Directions with c_x = 0 read both sources as one aligned 32-bit
-// pair, the others as two 16-bit loads.  All 2Q loads are issued before the
-// first collision, and the stores go out as 32-bit pairs.  Each cell still
-// runs collide() on the same values, so the populations are bitwise those of
-// the one-cell kernels.
+// even: every pull is an aligned 32-bit word, every store one 32-bit pair,
+// and the two cells' collisions run as one stream of packed FP32 operations
+// (Pk), which halves the instructions of the arithmetic that otherwise
+// limits this kernel's issue rate.  Each lane computes exactly what the
+// one-cell kernels compute, so the populations are bitwise theirs.
 template <class T> struct __align__(4) Pair16 {
   T a, b;
 };
 
-template <int Q, class T, class R>
-__device__ __forceinline__ void gather_pair(const DirPtrs<Q, T>& P, int x, int y, int z, const FluidParams<R>& p,
-                                            R ga[Q], R gb[Q]) {
-  // sources x - 1 .. x + 2 (x + 1 < nx since x is even and nx even)
-  int xs[4] = {x - 1, x, x + 1, x + 2};
-  if (xs[0] < 0) xs[0] += p.nx;
-  if (xs[3] >= p.nx) xs[3] -= p.nx;
-  int ys[3] = {y - 1, y, y + 1};
-  if (ys[0] < 0) ys[0] += p.ny;
-  if (ys[2] >= p.ny) ys[2] -= p.ny;
-  int zs[3] = {z - 1, z, z + 1};
-  if (Lat<Q>::D == 3) {
-    if (zs[0] < 0) zs[0] += p.nz;
-    if (zs[2] >= p.nz) zs[2] -= p.nz;
+// Two 16-bit values as one packed FP32 pair and back, with the scaling and
+// rounding of Store<T>::ld and Store<T>::st (the scale is a power of two).
+template <class T> struct Pack16;
+template <> struct Pack16<__half> {
+  static __device__ __forceinline__ F2 ld(__half a, __half b) {
+    return Pk::mul(Pk::make(__half2float(a), __half2float(b)), Pk::splat(1.0f / 256.0f));
   }
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int dy = 1 - Lat<Q>::cy(i), dz = 1 - Lat<Q>::cz(i);
-    const int row = (zs[dz] * p.ny + ys[dy]) * p.nx;
-    if (Lat<Q>::cx(i) == 0) {
-      const Pair16<T> v = *reinterpret_cast<const Pair16<T>*>(P.s[i] + row + x);
-      ga[i] = Store<T>::ld(v.a);
-      gb[i] = Store<T>::ld(v.b);
-    } else {
-      const int dx = 1 - Lat<Q>::cx(i);
-      ga[i] = Store<T>::ld(P.s[i][row + xs[dx]]);
-      gb[i] = Store<T>::ld(P.s[i][row + xs[dx + 1]]);
-    }
+  static __device__ __forceinline__ unsigned st(F2 v) {
+    const F2 s = Pk::mul(v, Pk::splat(256.0f));
+    const __half2 h = __floats2half2_rn(Pk::lo(s), Pk::hi(s));
+    return *reinterpret_cast<const unsigned*>(&h);
   }
-}
+};
+template <> struct Pack16<__nv_bfloat16> {
+  static __device__ __forceinline__ F2 ld(__nv_bfloat16 a, __nv_bfloat16 b) {
+    return Pk::make(__bfloat162float(a), __bfloat162float(b));
+  }
+  static __device__ __forceinline__ unsigned st(F2 v) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(Pk::lo(v), Pk::hi(v));
+    return *reinterpret_cast<const unsigned*>(&h);
+  }
+};
 
-// As gather_pair, with every load an aligned 32-bit word: per direction each
-// thread loads the word (x, x + 1) of its source row; for c_x = +1 the value
-// at x - 1 is the high half of the previous lane's word, for c_x = -1 the
-// value at x + 2 the low half of the next lane's word (lanes hold x, x + 2,
-// ... of one row: the block is 64 threads wide in x).  The first lane, the
-// last lane and lanes at the row's ends load that value directly.  Every
-// lane of the warp must call it (shuffles); lanes outside the grid pass
-// clamped coordinates and discard the result.  The values are those of
-// gather_pair, bit for bit.
-template <int Q, class T, class R>
+// Pull of the cells (x, x + 1) with every load an aligned 32-bit word: per
+// direction each thread loads the word (x, x + 1) of its source row; for
+// c_x = +1 the value at x - 1 is the high half of the previous lane's word,
+// for c_x = -1 the value at x + 2 the low half of the next lane's word (the
+// lanes of a warp hold x, x + 2, ... of one row: blocks are a multiple of 32
+// threads wide in x).  The first lane, the last lane and lanes at the row's
+// ends load that value directly.  Every lane of the warp must call it
+// (shuffles); lanes outside the grid pass clamped coordinates and discard
+// the result.  g[i] holds the two cells' values of direction i, lo = x.
+template <int Q, class T>
 __device__ __forceinline__ void gather_pair_words(const DirPtrs<Q, T>& P, int x, int y, int z,
-                                                  const FluidParams<R>& p, R ga[Q], R gb[Q]) {
+                                                  const FluidParams<float>& p, F2 g[Q]) {
   const int lane = threadIdx.x & 31;
   int xm = x - 1, xp = x + 2;
   if (xm < 0) xm += p.nx;
@@ -255,75 +387,78 @@ __device__ __forceinline__ void gather_pair_words(const DirPtrs<Q, T>& P, int x,
     const Pair16<T> w = *reinterpret_cast<const Pair16<T>*>(P.s[i] + row + x);
     const unsigned bits = *reinterpret_cast<const unsigned*>(&w);
     if (Lat<Q>::cx(i) == 0) {
-      ga[i] = Store<T>::ld(w.a);
-      gb[i] = Store<T>::ld(w.b);
+      g[i] = Pack16<T>::ld(w.a, w.b);
     } else if (Lat<Q>::cx(i) > 0) {
       // sources x - 1, x
       const unsigned prev = __shfl_up_sync(0xffffffffu, bits, 1);
       Pair16<T> pw;
       *reinterpret_cast<unsigned*>(&pw) = prev;
       const T left = own_left ? P.s[i][row + xm] : pw.b;
-      ga[i] = Store<T>::ld(left);
-      gb[i] = Store<T>::ld(w.a);
+      g[i] = Pack16<T>::ld(left, w.a);
     } else {
       // sources x + 1, x + 2
       const unsigned next = __shfl_down_sync(0xffffffffu, bits, 1);
       Pair16<T> nw;
       *reinterpret_cast<unsigned*>(&nw) = next;
       const T right = own_right ? P.s[i][row + xp] : nw.a;
-      ga[i] = Store<T>::ld(w.b);
-      gb[i] = Store<T>::ld(right);
+      g[i] = Pack16<T>::ld(w.b, right);
     }
   }
 }
 
-// Band correction, collision and divergence check of one cell (the part of
-// collide_cell between the pull and the store).
-template <int Q, bool IB, class R>
-__device__ __forceinline__ void collide_only(R g[Q], const FluidParams<R>& p, int x, int y, int z) {
-  R F[3];
-  R du[3] = {R(0), R(0), R(0)};
+// Band correction, collision and divergence check of the cells (x, x + 1)
+// (the part of collide_cell between the pull and the store, on both lanes).
+// x is even and tiles are 16 cells wide, so both cells lie in one tile.
+template <int Q, bool IB>
+__device__ __forceinline__ void collide_pair(F2 g[Q], const FluidParams<float>& p, int x, int y, int z) {
+  F2 F[3], du[3];
   int band = -1;
-  if (IB) band = band_du<Q, R>(x, y, z, p, du);
-  const R drho = collide<Q, R>(g, F, du, p);
-  if (!(drho > R(-1) && drho < R(99))) atomicOr(p.status, ST_DIVERGED);
+  if (IB) {
+    float da[3] = {0.0f, 0.0f, 0.0f}, db[3] = {0.0f, 0.0f, 0.0f};
+    band = band_du<Q, float>(x, y, z, p, da);
+    if (band >= 0) band_du<Q, float>(x + 1, y, z, p, db);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) du[a] = Pk::make(da[a], db[a]);
+  }
+  const F2 drho = collide_v<Q, IB, Pk>(g, F, du, p);
+  const float d0 = Pk::lo(drho), d1 = Pk::hi(drho);
+  if (!(d0 > -1.0f && d0 < 99.0f) || !(d1 > -1.0f && d1 < 99.0f)) atomicOr(p.status, ST_DIVERGED);
   if (IB && band >= 0) {
-    p.band_F[band] = F[0] - p.G[0];
-    p.band_F[band + TILE_CELLS] = F[1] - p.G[1];
-    p.band_F[band + 2 * TILE_CELLS] = F[2] - p.G[2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const F2 f = Pk::sub(F[a], Pk::splat(p.G[a]));
+      p.band_F[band + a * TILE_CELLS] = Pk::lo(f);
+      p.band_F[band + 1 + a * TILE_CELLS] = Pk::hi(f);
+    }
   }
 }
 
-// Every cell of a grid with even nx: 128 x 4 cells per 256-thread block;
-// four blocks per SM (64 registers) where that does not spill, three with
-// the band lookup.  The pulls are aligned 32-bit words (gather_pair_words).
+// Every cell of a grid with even nx: 2 x-adjacent cells per thread,
+// 256-thread blocks (64 x 4 threads by default); IBL_PAIRS_MIN_BLOCKS blocks
+// per SM without the band lookup, three with it.
+#ifndef IBL_PAIRS_MIN_BLOCKS
+#define IBL_PAIRS_MIN_BLOCKS 4
+#endif
 template <int Q, class T, bool IB>
-__global__ void __launch_bounds__(256, IB ? 3 : 4) k_collide_pairs(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p) {
-  using R = typename Store<T>::R;
+__global__ void __launch_bounds__(256, IB ? 3 : IBL_PAIRS_MIN_BLOCKS) k_collide_pairs(DirPtrs<Q, T> P, FluidParams<float> p) {
   const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
   // every lane takes part in the word loads and shuffles; lanes outside the
   // grid read a clamped row and store nothing
   const bool inside = x < p.nx && y < p.ny;
-  R ga[Q], gb[Q];
-  gather_pair_words<Q, T, R>(P, inside ? x : p.nx - 2, inside ? y : p.ny - 1, z, p, ga, gb);
+  F2 g[Q];
+  gather_pair_words<Q, T>(P, inside ? x : p.nx - 2, inside ? y : p.ny - 1, z, p, g);
   if (!inside) return;
-  if (on_special_face<R>(x, y, z, Lat<Q>::D, p) || on_special_face<R>(x + 1, y, z, Lat<Q>::D, p)) {
+  if (on_special_face<float>(x, y, z, Lat<Q>::D, p) || on_special_face<float>(x + 1, y, z, Lat<Q>::D, p)) {
     collide_cell<Q, T, true, IB>(P, p, x, y, z);
     collide_cell<Q, T, true, IB>(P, p, x + 1, y, z);
     return;
   }
-  collide_only<Q, IB, R>(ga, p, x, y, z);
-  collide_only<Q, IB, R>(gb, p, x + 1, y, z);
+  collide_pair<Q, IB>(g, p, x, y, z);
   const int cell = (z * p.ny + y) * p.nx + x;
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    Pair16<T> v;
-    v.a = Store<T>::st(ga[i]);
-    v.b = Store<T>::st(gb[i]);
-    *reinterpret_cast<Pair16<T>*>(P.d[i] + cell) = v;
-  }
+  for (int i = 0; i < Q; ++i) *reinterpret_cast<unsigned*>(P.d[i] + cell) = Pack16<T>::st(g[i]);
 }
 
 // Every cell, 64 x 4 cells per block; IB selects the band lookup.
@@ -509,7 +644,7 @@ FluidParams<R> make_params(ibl_ctx* c, bool with_ib) {
   for (int i = 0; i < 6; ++i) p.bc[i] = c->bc[i];
   for (int a = 0; a < 3; ++a) {
     p.u_in[a] = (R)c->u_in[a];
-    p.G[a] = (R)c->G[a];
+    p.G[a] = (R)c->G[a] + R(0);   // no negative zero: F = G exactly off the band
   }
   p.rho_out = (R)c->rho_out;
   p.omega = (R)(1.0 / c->tau);
@@ -523,8 +658,7 @@ FluidParams<R> make_params(ibl_ctx* c, bool with_ib) {
 }
 
 static dim3 cell_block(ibl_ctx* c) {
-  (void)c;
-  return dim3(64, 4, 1);
+  return dim3(c->collide_bx, c->collide_by, 1);
 }
 static dim3 cell_grid(ibl_ctx* c, dim3 b) {
   return dim3((c->nx + b.x - 1) / b.x, (c->ny + b.y - 1) / b.y, c->nz);
@@ -549,7 +683,7 @@ cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
   const DirPtrs<Q, T> P = dir_ptrs<Q, T>(c);
   dim3 b = cell_block(c), g = cell_grid(c, b);
   if constexpr (sizeof(T) == 2) {
-    if (!c->poststream && c->nx % 2 == 0) {
+    if (!c->poststream && c->nx % 2 == 0 && c->collide_pairs) {
       // 16-bit storage: two x-adjacent cells per thread
       g.x = (c->nx / 2 + b.x - 1) / b.x;
       if (with_ib) k_collide_pairs<Q, T, true><<<g, b, 0, c->stream>>>(P, p);
@@ -600,7 +734,7 @@ cudaError_t fields_q(ibl_ctx* c, double* d_rho, double* d_u, double* d_pop) {
   using R = typename Store<T>::R;
   auto p = make_params<R>(c, false);
   const T* src = (const T*)c->f[c->cur];
-  dim3 b = cell_block(c), g = cell_grid(c, b);
+  dim3 b(64, 4, 1), g = cell_grid(c, b);
   if (c->poststream) k_fields<Q, T, false><<<g, b, 0, c->stream>>>(src, p, d_rho, d_u, d_pop);
   else k_fields<Q, T, true><<<g, b, 0, c->stream>>>(src, p, d_rho, d_u, d_pop);
   c->launches++;

@@ -12,7 +12,10 @@
 //      paper's parametric study, Sec. 3.4-3.7 and Fig. 11), destroys the
 //      context and returns its memory to the budget.
 // Every run advances through exactly the same kernel sequence as it would
-// alone, so its result does not depend on what else is running.
+// alone, so its result does not depend on what else is running.  With
+// tuning on, a run's solve block count follows from its marker count, and
+// its overlap mode and collide shape (which never change results) from a
+// timed first chunk, cached per run shape.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -23,6 +26,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "ibl_internal.cuh"
@@ -30,6 +34,17 @@
 namespace {
 
 using clock_type = std::chrono::steady_clock;
+
+// Launch candidates of the tuning chunk: overlap mode, collide block, pairs.
+struct Launch {
+  int overlap, bx, by, pairs;
+};
+constexpr Launch CANDIDATES[] = {{1, 64, 4, 1}, {0, 64, 4, 1}, {0, 128, 2, 1}, {0, 32, 8, 1}, {0, 256, 1, 1}};
+constexpr int NCAND = sizeof(CANDIDATES) / sizeof(CANDIDATES[0]);
+constexpr int TUNE_MIN_STEPS = 2;          // timed steps per candidate
+constexpr int MARKERS_PER_SOLVE_BLOCK = 64;
+
+using ShapeKey = std::tuple<int, int, int, double, int, int>;   // nx, ny, nz, chord, precision, faces
 
 struct Run {
   int64_t id = 0;
@@ -42,7 +57,19 @@ struct Run {
   std::atomic<bool> cancel{false};
   size_t bytes = 0;
   int m[2] = {0, 0};
+  // tuning (worker-owned)
+  bool tune_pending = false;     // the next chunk is the tuning chunk
+  bool tune_inflight = false;    // the tuning chunk is on the stream
+  int tune_steps = 0;            // timed steps per candidate
+  cudaEvent_t tev[2 * NCAND] = {};
+  Launch launch{-1, 64, 4, 1};
+  int solve_blocks = 0;
+  bool tuned = false;
 };
+
+ShapeKey shape_key(const ibl_run_request& r) {
+  return ShapeKey(r.nx, r.ny, r.nz, r.chord, r.precision, r.faces);
+}
 
 }  // namespace
 
@@ -63,6 +90,10 @@ struct ibl_server {
   int active = 0;                                 // admitted and not yet retired
   int finished = 0;
   std::vector<std::shared_ptr<Run>> running;      // worker-owned
+  std::map<ShapeKey, Launch> tuned;                // worker-owned: fastest launch per run shape
+  int num_sms = 0;
+  // scheduling thread's time, ns (written by the worker, read by ibl_server_load)
+  std::atomic<int64_t> busy_ns{0}, enqueue_ns{0}, build_ns{0}, retire_ns{0};
   std::atomic<bool> stop{false};
   std::thread worker;
   std::string err;
@@ -72,6 +103,15 @@ namespace {
 
 double now_s(const ibl_server* s) {
   return std::chrono::duration<double>(clock_type::now() - s->t0).count();
+}
+
+int64_t ns_since(clock_type::time_point t) {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(clock_type::now() - t).count();
+}
+
+ibl_status apply_launch(ibl_ctx* ctx, const Launch& l) {
+  const ibl_status st = ibl_set_overlap(ctx, l.overlap);
+  return st != IBL_OK ? st : ibl_set_collide_shape(ctx, l.bx, l.by, l.pairs);
 }
 
 // Flat elliptic planform (chord c, span 5c), unit-spaced cell-centred marker
@@ -132,7 +172,7 @@ constexpr double SERVE_U_WALL_MAX = 0.15;
 // hinges c/2 apart about the mid-plane, opening angle (pi/3)|sin(2 pi t/T)|
 // per wing, Re = U_tip c / nu with U_tip = 2 Phi f c, Phi = 120 degrees
 // (Eq. 24), tau = 3 nu + 1/2 (Eq. 3), free stream U_inf = J U_tip.
-ibl_status build_run(Run& run) {
+ibl_status build_run(ibl_server* s, Run& run) {
   const ibl_run_request& r = run.req;
   const double pi = 3.14159265358979323846;
   const double f = 1.0 / r.period;
@@ -172,6 +212,27 @@ ibl_status build_run(Run& run) {
   }
   st = ibl_set_reference(run.ctx, u_tip, (double)m, 1.0);
   if (st != IBL_OK) return st;
+  if (s->cfg.tune) {
+    // solve blocks from the marker count alone (they fix the reduction order)
+    const int half = std::max(4, s->num_sms / 2);
+    run.solve_blocks = std::min(half, std::max(4, (2 * m + MARKERS_PER_SOLVE_BLOCK - 1) / MARKERS_PER_SOLVE_BLOCK));
+    st = ibl_solver_blocks(run.ctx, run.solve_blocks);
+    if (st != IBL_OK) return st;
+    const auto it = s->tuned.find(shape_key(r));
+    if (it != s->tuned.end()) {
+      run.launch = it->second;
+      run.tuned = true;
+      st = apply_launch(run.ctx, run.launch);
+      if (st != IBL_OK) return st;
+    } else if (r.steps >= 1 + NCAND * TUNE_MIN_STEPS) {
+      int per = std::max(TUNE_MIN_STEPS, (s->cfg.chunk_steps - 1) / NCAND);
+      while (1 + (int64_t)NCAND * per > r.steps) --per;
+      run.tune_steps = per;
+      for (auto& e : run.tev)
+        if (cudaEventCreate(&e) != cudaSuccess) return IBL_ECUDA;
+      run.tune_pending = true;
+    }
+  }
   std::vector<double> u(3 * (size_t)g.nx * g.ny * g.nz, 0.0);
   std::fill(u.begin(), u.begin() + (size_t)g.nx * g.ny * g.nz, u_inf);
   st = ibl_init_fluid(run.ctx, nullptr, u.data());
@@ -209,6 +270,16 @@ void collect(Run& run, ibl_status st, ibl_run_result& res) {
   }
   if (run.ev) cudaEventDestroy(run.ev);
   run.ev = nullptr;
+  for (auto& e : run.tev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  res.solve_blocks = run.solve_blocks;
+  res.overlap = run.launch.overlap;
+  res.collide_bx = run.launch.bx;
+  res.collide_by = run.launch.by;
+  res.collide_pairs = run.launch.pairs;
+  res.tuned = run.tuned ? 1 : 0;
   if (run.ctx) ibl_destroy(run.ctx);
   run.ctx = nullptr;
 }
@@ -232,9 +303,52 @@ void publish(ibl_server* s, Run& run, const ibl_run_result& res, bool admitted) 
   s->cv.notify_all();
 }
 
+// The tuning chunk: one untimed step (the first solve builds the
+// preconditioner), then tune_steps steps under each candidate launch between
+// a pair of timing events on the run's stream.  Every candidate computes the
+// same populations, so the run advances exactly as it would untuned.
+ibl_status enqueue_tuning(Run& r, int64_t& steps) {
+  void* stream = nullptr;
+  ibl_stream(r.ctx, &stream);
+  steps = 0;
+  ibl_status st = ibl_step(r.ctx, 1);
+  if (st != IBL_OK) return st;
+  steps = 1;
+  for (int k = 0; k < NCAND; ++k) {
+    st = apply_launch(r.ctx, CANDIDATES[k]);
+    if (st != IBL_OK) return st;
+    cudaEventRecord(r.tev[2 * k], (cudaStream_t)stream);
+    st = ibl_step(r.ctx, r.tune_steps);
+    if (st != IBL_OK) return st;
+    cudaEventRecord(r.tev[2 * k + 1], (cudaStream_t)stream);
+    steps += r.tune_steps;
+  }
+  return IBL_OK;
+}
+
+// After the tuning chunk: keep the fastest candidate for this run and for
+// every later run of the same shape.
+ibl_status finish_tuning(ibl_server* s, Run& r) {
+  int best = 0;
+  float best_ms = 0.0f;
+  for (int k = 0; k < NCAND; ++k) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, r.tev[2 * k], r.tev[2 * k + 1]) != cudaSuccess) return IBL_ECUDA;
+    if (k == 0 || ms < best_ms) {
+      best = k;
+      best_ms = ms;
+    }
+  }
+  r.launch = CANDIDATES[best];
+  r.tuned = true;
+  s->tuned.emplace(shape_key(r.req), r.launch);
+  return apply_launch(r.ctx, r.launch);
+}
+
 void worker_loop(ibl_server* s) {
   cudaSetDevice(s->device);
   while (!s->stop.load()) {
+    const auto t_pass = clock_type::now();
     bool busy = false;
     // 1. admission by arrival order, active count and HBM budget; the
     // contexts are built after the lock is released
@@ -259,7 +373,10 @@ void worker_loop(ibl_server* s) {
     }
     for (auto& run : admit) {
       const double t_start = now_s(s);
-      const ibl_status st = build_run(*run);
+      const auto t0 = clock_type::now();
+      const ibl_status st = build_run(s, *run);
+      s->build_ns += ns_since(t0);
+      busy = true;
       if (st != IBL_OK) {
         ibl_run_result res{};
         collect(*run, st, res);
@@ -273,7 +390,6 @@ void worker_loop(ibl_server* s) {
         run->res.start_s = t_start;
       }
       s->running.push_back(run);
-      busy = true;
     }
     // 2. next chunk of every run whose previous chunk finished; 3. retire
     for (size_t i = 0; i < s->running.size();) {
@@ -285,22 +401,38 @@ void worker_loop(ibl_server* s) {
           continue;
         }
         r.inflight = false;
+        busy = true;
         // the run's stream is idle: reading its status bits costs one small
         // copy, and a divergence stops the run here instead of at its end
         st = ibl_sync(r.ctx);
         if (st == IBL_ENOTCONV) st = IBL_OK;   // reported, not fatal
+        if (st == IBL_OK && r.tune_inflight) {
+          r.tune_inflight = false;
+          st = finish_tuning(s, r);
+        }
       }
       const bool cancelled = r.cancel.load();
       bool finish = cancelled || st != IBL_OK || r.steps_enqueued >= r.req.steps;
       if (!finish) {
-        const int64_t n = std::min<int64_t>(s->cfg.chunk_steps, r.req.steps - r.steps_enqueued);
-        st = ibl_step(r.ctx, n);
+        const auto t0 = clock_type::now();
+        int64_t n = 0;
+        if (r.tune_pending) {
+          r.tune_pending = false;
+          st = enqueue_tuning(r, n);
+          r.tune_inflight = st == IBL_OK;
+        } else {
+          n = std::min<int64_t>(s->cfg.chunk_steps, r.req.steps - r.steps_enqueued);
+          st = ibl_step(r.ctx, n);
+        }
         if (st == IBL_OK) {
           void* stream = nullptr;
           ibl_stream(r.ctx, &stream);
           cudaEventRecord(r.ev, (cudaStream_t)stream);
           r.inflight = true;
           r.steps_enqueued += n;
+        }
+        s->enqueue_ns += ns_since(t0);
+        if (st == IBL_OK) {
           std::lock_guard<std::mutex> lock(s->mu);
           r.res.steps_done = r.steps_enqueued;
         } else {
@@ -312,10 +444,12 @@ void worker_loop(ibl_server* s) {
         ++i;
         continue;
       }
+      const auto t0 = clock_type::now();
       if (cancelled && st == IBL_OK) st = IBL_ECANCELED;
       else if (st == IBL_OK) st = ibl_sync(r.ctx);
       ibl_run_result res{};
       collect(r, st, res);
+      s->retire_ns += ns_since(t0);
       {
         std::lock_guard<std::mutex> lock(s->mu);
         publish(s, r, res, true);
@@ -323,7 +457,8 @@ void worker_loop(ibl_server* s) {
       s->running.erase(s->running.begin() + i);
       busy = true;
     }
-    if (!busy) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    if (busy) s->busy_ns += ns_since(t_pass);
+    else std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
 }
 
@@ -334,13 +469,15 @@ extern "C" {
 ibl_status ibl_server_create(const ibl_server_config* cfg, ibl_server** out) {
   if (!out || !cfg) return IBL_EINVAL;
   *out = nullptr;
-  if (cfg->max_active < 1 || cfg->chunk_steps < 1 || cfg->hbm_budget_bytes <= 0) return IBL_EINVAL;
+  if (cfg->max_active < 1 || cfg->chunk_steps < 1 || cfg->hbm_budget_bytes <= 0 || cfg->tune < 0 || cfg->tune > 1)
+    return IBL_EINVAL;
   ibl_server* s = new ibl_server();
   s->cfg = *cfg;
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     delete s;
     return IBL_ECUDA;
   }
+  cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
   s->t0 = clock_type::now();
   s->worker = std::thread(worker_loop, s);
   *out = s;
@@ -405,6 +542,17 @@ ibl_status ibl_server_wait_all(ibl_server* s, double timeout_s) {
     if (s->cv.wait_until(lock, deadline) == std::cv_status::timeout && !(s->queue.empty() && s->active == 0))
       return IBL_ETIMEOUT;
   }
+  return IBL_OK;
+}
+
+ibl_status ibl_server_load(ibl_server* s, double* wall_s, double* busy_s, double* enqueue_s, double* build_s,
+                           double* retire_s) {
+  if (!s) return IBL_EINVAL;
+  if (wall_s) *wall_s = now_s(s);
+  if (busy_s) *busy_s = 1e-9 * (double)s->busy_ns.load();
+  if (enqueue_s) *enqueue_s = 1e-9 * (double)s->enqueue_ns.load();
+  if (build_s) *build_s = 1e-9 * (double)s->build_ns.load();
+  if (retire_s) *retire_s = 1e-9 * (double)s->retire_ns.load();
   return IBL_OK;
 }
 

@@ -45,7 +45,8 @@ class ibl_wave(C.Structure):
 
 
 class ibl_server_config(C.Structure):
-    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_active", C.c_int32), ("chunk_steps", C.c_int32)]
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_active", C.c_int32), ("chunk_steps", C.c_int32),
+                ("tune", C.c_int32)]
 
 
 class ibl_run_request(C.Structure):
@@ -58,7 +59,9 @@ class ibl_run_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("done", C.c_int32), ("steps_done", C.c_int64),
                 ("submit_s", C.c_double), ("start_s", C.c_double), ("finish_s", C.c_double),
                 ("CL_max", C.c_double * 2), ("CL_mean", C.c_double * 2), ("CT_max", C.c_double * 2),
-                ("CT_mean", C.c_double * 2), ("CL_last", C.c_double * 2), ("CT_last", C.c_double * 2)]
+                ("CT_mean", C.c_double * 2), ("CL_last", C.c_double * 2), ("CT_last", C.c_double * 2),
+                ("solve_blocks", C.c_int32), ("overlap", C.c_int32), ("collide_bx", C.c_int32),
+                ("collide_by", C.c_int32), ("collide_pairs", C.c_int32), ("tuned", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -89,6 +92,7 @@ _SIGS = {
     "ibl_set_mass_check": ([_P, C.c_int32, C.c_double], C.c_int),
     "ibl_mass_check_read": ([_P, _D, _D, _I64], C.c_int),
     "ibl_set_overlap": ([_P, C.c_int32], C.c_int),
+    "ibl_set_collide_shape": ([_P, C.c_int32, C.c_int32, C.c_int32], C.c_int),
     "ibl_profile_phases": ([_P, _D, C.c_int32], C.c_int),
     "ibl_solver_blocks": ([_P, C.c_int32], C.c_int),
     "ibl_interpolate_points": ([_P, C.c_int32, _P, _P, _P], C.c_int),
@@ -106,6 +110,7 @@ _SIGS = {
     "ibl_server_create": ([C.POINTER(ibl_server_config), C.POINTER(_P)], C.c_int),
     "ibl_server_submit": ([_P, C.POINTER(ibl_run_request), _I64], C.c_int),
     "ibl_server_poll": ([_P, C.c_int64, C.POINTER(ibl_run_result)], C.c_int),
+    "ibl_server_load": ([_P, _D, _D, _D, _D, _D], C.c_int),
     "ibl_server_cancel": ([_P, C.c_int64], C.c_int),
     "ibl_server_wait_all": ([_P, C.c_double], C.c_int),
     "ibl_server_stats": ([_P, _I32, _I32, _I32, _I64], C.c_int),
@@ -365,6 +370,10 @@ class Context:
         """-1 automatic, 0 one collide kernel after the IB chain, 1 split step."""
         _check(self.h, _lib.ibl_set_overlap(self.h, int(mode)))
 
+    def ibl_set_collide_shape(self, bx=64, by=4, pairs=1):
+        """Thread block (bx x by) of the one-kernel collide; pairs 1: two cells per thread (16-bit storage)."""
+        _check(self.h, _lib.ibl_set_collide_shape(self.h, int(bx), int(by), int(pairs)))
+
     def ibl_interpolate_points(self, X, U=None, rho=None):
         """rho and u* of the current populations at points X (Eq. 17).
 
@@ -460,8 +469,8 @@ def from_workload(cfg: dict, init: bool = True) -> Context:
 class Server:
     """Continuous-batching server of clap-and-fling runs (ibl_server_* calls)."""
 
-    def __init__(self, hbm_budget_bytes: int, max_active: int = 8, chunk_steps: int = 50):
-        cfg = ibl_server_config(int(hbm_budget_bytes), int(max_active), int(chunk_steps))
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 8, chunk_steps: int = 50, tune: int = 1):
+        cfg = ibl_server_config(int(hbm_budget_bytes), int(max_active), int(chunk_steps), int(tune))
         h = _P()
         st = _lib.ibl_server_create(C.byref(cfg), C.byref(h))
         if st != IBL_OK:
@@ -486,7 +495,9 @@ class Server:
         return {"status": r.status, "done": bool(r.done), "steps_done": r.steps_done,
                 "submit_s": r.submit_s, "start_s": r.start_s, "finish_s": r.finish_s,
                 "CL_max": list(r.CL_max), "CL_mean": list(r.CL_mean), "CT_max": list(r.CT_max),
-                "CT_mean": list(r.CT_mean), "CL_last": list(r.CL_last), "CT_last": list(r.CT_last)}
+                "CT_mean": list(r.CT_mean), "CL_last": list(r.CL_last), "CT_last": list(r.CT_last),
+                "solve_blocks": r.solve_blocks, "overlap": r.overlap, "collide_shape": (r.collide_bx, r.collide_by),
+                "collide_pairs": r.collide_pairs, "tuned": bool(r.tuned)}
 
     def ibl_server_cancel(self, run_id):
         st = _lib.ibl_server_cancel(self.h, int(run_id))
@@ -502,6 +513,11 @@ class Server:
         q, a, f, b = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
         _lib.ibl_server_stats(self.h, C.byref(q), C.byref(a), C.byref(f), C.byref(b))
         return {"queued": q.value, "active": a.value, "finished": f.value, "hbm_in_use": b.value}
+
+    def ibl_server_load(self):
+        v = [C.c_double() for _ in range(5)]
+        _check(None, _lib.ibl_server_load(self.h, *[C.byref(x) for x in v]))
+        return dict(zip(("wall_s", "busy_s", "enqueue_s", "build_s", "retire_s"), (x.value for x in v)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -58,6 +58,7 @@ def test_server_run_matches_a_direct_run(ibl):
     cfg = W.clap_fling_3d(nx=REQ["nx"], ny=REQ["ny"], nz=REQ["nz"], chord=REQ["chord"], Re=REQ["Re"],
                           J=REQ["J"], period=REQ["period"], faces="periodic")
     ctx = ibl.from_workload(cfg)
+    ctx.ibl_solver_blocks(r["solve_blocks"])       # the tuner's block count (it fixes the reduction order)
     ctx.ibl_step(REQ["steps"])
     for w in range(2):
         h = ctx.ibl_force_history(w, REQ["steps"])
@@ -128,3 +129,49 @@ def test_cancel_queued_and_running(ibl):
     assert rr["status"] == ibl.IBL_ECANCELED and 0 < rr["steps_done"] < 20000
     assert rq["status"] == ibl.IBL_ECANCELED and rq["steps_done"] == 0 and rq["start_s"] == 0.0
     assert stats["hbm_in_use"] == 0 and stats["active"] == 0 and stats["finished"] == 2
+
+
+def _sms():
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def test_tuning_is_per_request_and_cached_per_shape(ibl):
+    """The solve block count follows from the marker count (one block per 64
+    markers, 4 .. half the SMs); the overlap mode and collide shape come from
+    the first run's timed tuning chunk and are reused by a later run of the
+    same shape, which then gives bitwise the same result."""
+    srv = ibl.Server(hbm_budget_bytes=8 << 30, max_active=2, chunk_steps=30)
+    ra_id = srv.ibl_server_submit(**REQ)
+    srv.ibl_server_wait_all(600)
+    rb_id = srv.ibl_server_submit(**REQ)
+    srv.ibl_server_wait_all(600)
+    ra, rb = srv.ibl_server_poll(ra_id), srv.ibl_server_poll(rb_id)
+    load = srv.ibl_server_load()
+    srv.close()
+    _, ds = W.elliptic_planform_markers(REQ["chord"], 5 * REQ["chord"], 1.0)
+    want = min(max(4, _sms() // 2), max(4, -(-2 * len(ds) // 64)))
+    for r in (ra, rb):
+        assert r["status"] == ibl.IBL_OK and r["tuned"] and r["solve_blocks"] == want
+    assert (ra["overlap"], ra["collide_shape"], ra["collide_pairs"]) == \
+        (rb["overlap"], rb["collide_shape"], rb["collide_pairs"])
+    assert ra["overlap"] in (0, 1) and ra["collide_shape"] in [(64, 4), (128, 2), (32, 8), (256, 1)]
+    assert _keys(ra) == _keys(rb)
+    assert 0 < load["busy_s"] <= load["wall_s"]
+    assert load["enqueue_s"] + load["build_s"] + load["retire_s"] <= load["busy_s"] * 1.01 + 1e-3
+    print(f"tuned: {want} solve blocks, overlap {ra['overlap']}, collide {ra['collide_shape']}; load {load}")
+
+
+def test_untuned_server_keeps_library_defaults(ibl):
+    srv = ibl.Server(hbm_budget_bytes=8 << 30, max_active=2, chunk_steps=30, tune=0)
+    rid = srv.ibl_server_submit(**REQ)
+    srv.ibl_server_wait_all(600)
+    r = srv.ibl_server_poll(rid)
+    srv.close()
+    assert r["status"] == ibl.IBL_OK and not r["tuned"] and r["solve_blocks"] == 0 and r["overlap"] == -1
+    cfg = W.clap_fling_3d(nx=REQ["nx"], ny=REQ["ny"], nz=REQ["nz"], chord=REQ["chord"], Re=REQ["Re"],
+                          J=REQ["J"], period=REQ["period"], faces="periodic")
+    ctx = ibl.from_workload(cfg)
+    ctx.ibl_step(REQ["steps"])
+    h = ctx.ibl_force_history(0, REQ["steps"])
+    assert h[:, 0].max() == r["CL_max"][0]
