@@ -444,8 +444,8 @@ ibl_status ibl_server_create(const ibl_server_config* cfg, ibl_server** out);
  * wings that do not fit the box, IBL_ENOMEM if its footprint exceeds the
  * whole budget, IBL_EUNSTABLE if it lies outside the BGK collision's
  * stability range (tau = 3 nu + 1/2 below 0.505, a free stream J U_tip above
- * 0.05 or a tip speed above 0.15 lattice units), instead of diverging on the
- * GPU.  The submission time is taken on entry.  Thread-safe. */
+ * 0.05, a tip speed above 0.15 lattice units, or a tip speed above 0.05 with
+ * U_tip / nu above 5), instead of diverging on the GPU.  The submission time is taken on entry.  Thread-safe. */
 ibl_status ibl_server_submit(ibl_server* s, const ibl_run_request* req, int64_t* run_id);
 /* Cancel a run: a queued run never starts; a running one stops after the
  * chunk of steps in flight and its memory returns to the budget.  Its result

@@ -54,13 +54,14 @@ ibl_status sync_and_collect(ibl_ctx* c);
 ibl_status ibl::sync_and_collect(ibl_ctx* c) {
   CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   int s = 0;
-  CK(cudaMemcpy(&s, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  CK(to_host(c, &s, c->d_status, sizeof(int)), "status read");
   // non-convergence is reported once per occurrence; the others are sticky
   c->sticky |= s;
   ibl_status r = status_code(c);
   if (s & ST_NOTCONV) {
     const int keep = s & ~ST_NOTCONV;
-    CK(cudaMemcpy(c->d_status, &keep, sizeof(int), cudaMemcpyHostToDevice), "status reset");
+    CK(to_device(c, c->d_status, &keep, sizeof(int)), "status reset");
+    CK(cudaStreamSynchronize(c->stream), "status reset");
     c->sticky &= ~ST_NOTCONV;
   }
   return r;
@@ -127,10 +128,10 @@ ibl_status ibl_create(const ibl_grid* grid, double tau, int32_t lattice, ibl_ctx
   if (e == cudaSuccess) e = cudaMalloc(&c->f[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->f[1], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 2 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = fill_zero(c, c->d_status, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_mass_parts, sizeof(double) * MASS_PARTS);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_mass_ref, sizeof(double) * 3);
-  if (e == cudaSuccess) e = cudaMemset(c->d_mass_ref, 0, sizeof(double) * 3);
+  if (e == cudaSuccess) e = fill_zero(c, c->d_mass_ref, sizeof(double) * 3);
   if (e != cudaSuccess) {
     ibl_status s = cuda_check(nullptr, e, "ibl_create");
     ibl_destroy(c);
@@ -306,8 +307,8 @@ static ibl_status ensure_ib(ibl_ctx* c) {
   CK(cudaStreamSynchronize(c->stream), "sync");
   CK(ib_alloc(c), "IB buffers");
   const size_t m = c->m_total;
-  CK(cudaMemcpy(c->d_X0, c->h_X0.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice), "X0 upload");
-  CK(cudaMemcpy(c->d_ds, c->h_ds.data(), sizeof(double) * m, cudaMemcpyHostToDevice), "ds upload");
+  CK(to_device(c, c->d_X0, c->h_X0.data(), sizeof(double) * 3 * m), "X0 upload");
+  CK(to_device(c, c->d_ds, c->h_ds.data(), sizeof(double) * m), "ds upload");
   if (c->h_stage) cudaFreeHost(c->h_stage);
   c->h_stage = nullptr;
   c->stage_doubles = 6 * m;
@@ -435,7 +436,7 @@ ibl_status ibl_mass_check_read(ibl_ctx* c, double* m0, double* m_last, int64_t* 
   ibl_status s = sync_and_collect(c);
   if (s != IBL_OK && s != IBL_ENOTCONV && s != IBL_EDIVERGED) return s;
   double r[3];
-  CK(cudaMemcpy(r, c->d_mass_ref, sizeof(r), cudaMemcpyDeviceToHost), "mass check read");
+  CK(to_host(c, r, c->d_mass_ref, sizeof(r)), "mass check read");
   if (m0) *m0 = r[0];
   if (m_last) *m_last = r[1];
   if (checks) *checks = (int64_t)r[2];
@@ -504,7 +505,7 @@ ibl_status ibl_forces(ibl_ctx* c, int32_t body_id, double* C_L, double* C_T, dou
   if (c->step == 0 || !c->ib_ready) return fail(c, IBL_ESTATE, "no completed step");
   double F[3];
   const long long idx = ((long long)body_id * HIST_LEN + ((c->step - 1) % HIST_LEN)) * 3;
-  CK(cudaMemcpy(F, c->d_hist + idx, sizeof(F), cudaMemcpyDeviceToHost), "force read");
+  CK(to_host(c, F, c->d_hist + idx, sizeof(F)), "force read");
   coefficients(c, body_id, F, C_L, C_T, C_D);
   return s;
 }
@@ -520,8 +521,8 @@ ibl_status ibl_force_history(ibl_ctx* c, int32_t body_id, int64_t max, double* o
   const long long cnt = std::min<long long>(avail, max);
   std::vector<double> F(3 * (size_t)HIST_LEN);
   if (cnt > 0)
-    CK(cudaMemcpy(F.data(), c->d_hist + (size_t)body_id * HIST_LEN * 3, sizeof(double) * 3 * HIST_LEN,
-                  cudaMemcpyDeviceToHost), "history read");
+    CK(to_host(c, F.data(), c->d_hist + (size_t)body_id * HIST_LEN * 3, sizeof(double) * 3 * HIST_LEN),
+       "history read");
   for (long long k = 0; k < cnt; ++k) {
     const long long stepk = c->step - cnt + k;
     const double* f = F.data() + 3 * (stepk % HIST_LEN);
@@ -584,8 +585,7 @@ ibl_status ibl_get_markers(ibl_ctx* c, int32_t body_id, double* X, double* U, do
   double* srcs[3] = {c->d_X, c->d_U, c->d_mforce};
   for (int k = 0; k < 3; ++k) {
     if (!outs[k]) continue;
-    CK(cudaMemcpy(tmp.data(), srcs[k] + 3 * (size_t)b.offset, sizeof(double) * 3 * b.m, cudaMemcpyDeviceToHost),
-       "marker read");
+    CK(to_host(c, tmp.data(), srcs[k] + 3 * (size_t)b.offset, sizeof(double) * 3 * b.m), "marker read");
     for (int l = 0; l < b.m; ++l)
       for (int a = 0; a < c->D; ++a) outs[k][(size_t)l * c->D + a] = tmp[3 * l + a];
   }
@@ -635,8 +635,8 @@ ibl_status ibl_solver_stats(ibl_ctx* c, int32_t* iterations, double* rel_residua
   int info[4] = {0, 0, 0, 0};
   double res = 0;
   if (c->ib_ready) {
-    CK(cudaMemcpy(info, c->d_cg_info, sizeof(info), cudaMemcpyDeviceToHost), "stats");
-    CK(cudaMemcpy(&res, c->d_cg_res, sizeof(double), cudaMemcpyDeviceToHost), "stats");
+    CK(to_host(c, info, c->d_cg_info, sizeof(info)), "stats");
+    CK(to_host(c, &res, c->d_cg_res, sizeof(double)), "stats");
   }
   if (iterations) *iterations = info[0];
   if (rel_residual) *rel_residual = res;
@@ -712,7 +712,7 @@ ibl_status ibl_solver_trace(ibl_ctx* c, int64_t* ns, int32_t max, int32_t* n) {
   ibl_status s = sync_and_collect(c);
   if (s != IBL_OK && s != IBL_ENOTCONV) return s;
   unsigned long long t[256] = {0};
-  if (c->ib_ready) CK(cudaMemcpy(t, c->d_trace, sizeof(t), cudaMemcpyDeviceToHost), "trace read");
+  if (c->ib_ready) CK(to_host(c, t, c->d_trace, sizeof(t)), "trace read");
   const int k = std::min<int>(max, 256);
   for (int i = 0; i < k; ++i) ns[i] = (int64_t)t[i];
   if (n) *n = k;

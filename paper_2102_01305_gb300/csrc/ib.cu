@@ -1689,12 +1689,12 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   std::vector<int> body_of(m);
   for (size_t b = 0; b < c->bodies.size(); ++b)
     for (int l = 0; l < c->bodies[b].m; ++l) body_of[c->bodies[b].offset + l] = (int)b;
-  IBL_CU(cudaMemcpy(c->d_body, body_of.data(), sizeof(int) * m, cudaMemcpyHostToDevice));
+  IBL_CU(to_device(c, c->d_body, body_of.data(), sizeof(int) * m));
   std::vector<int> boff(c->bodies.size() + 1);
   for (size_t b = 0; b < c->bodies.size(); ++b) boff[b] = c->bodies[b].offset;
   boff[c->bodies.size()] = m;
   IBL_CU(cudaMalloc(&c->d_boff, sizeof(int) * boff.size()));
-  IBL_CU(cudaMemcpy(c->d_boff, boff.data(), sizeof(int) * boff.size(), cudaMemcpyHostToDevice));
+  IBL_CU(to_device(c, c->d_boff, boff.data(), sizeof(int) * boff.size()));
   c->cand_ready = false;
   c->precond_valid = false;
   c->warm = false;

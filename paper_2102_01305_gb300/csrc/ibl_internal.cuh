@@ -194,6 +194,21 @@ struct ibl_ctx {
 namespace ibl {
 
 // error helpers (api.cu)
+// Host <-> device copies and fills ordered on the context's stream.  The
+// stream is non-blocking, so the legacy-stream forms (cudaMemcpy,
+// cudaMemset) are not ordered against the context's kernels: with other
+// contexts loading the GPU a fill could land after a kernel that had
+// already written the same buffer.
+inline cudaError_t to_device(ibl_ctx* c, void* dst, const void* src, size_t bytes) {
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+}
+inline cudaError_t to_host(ibl_ctx* c, void* dst, const void* src, size_t bytes) {
+  const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(c->stream);
+}
+inline cudaError_t fill_zero(ibl_ctx* c, void* dst, size_t bytes) {
+  return cudaMemsetAsync(dst, 0, bytes, c->stream);
+}
 ibl_status fail(ibl_ctx* c, ibl_status s, const std::string& msg);
 ibl_status cuda_check(ibl_ctx* c, cudaError_t e, const char* what);
 ibl_status sync_and_collect(ibl_ctx* c);   // drain the stream, fold device status bits

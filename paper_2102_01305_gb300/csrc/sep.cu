@@ -503,7 +503,7 @@ static cudaError_t sep_upload(ibl_ctx* c, T** dst, const T* src, size_t n) {
   SEP_CU(cudaMalloc(&p, sizeof(T) * std::max<size_t>(n, 1)));
   c->sep_allocs.push_back(p);
   *dst = static_cast<T*>(p);
-  if (src && n) SEP_CU(cudaMemcpy(p, src, sizeof(T) * n, cudaMemcpyHostToDevice));
+  if (src && n) SEP_CU(to_device(c, p, src, sizeof(T) * n));
   return cudaSuccess;
 }
 
@@ -539,8 +539,8 @@ cudaError_t sep_alloc(ibl_ctx* c) {
     SEP_CU(sep_upload<double>(c, &s.S64, nullptr, (size_t)h.nc * h.nc));
     // Sinv rows start 16-byte aligned (ldc is a multiple of 4 entries of 8
     // bytes, cudaMalloc aligns to 256 B): the Schur product reads float4s
-    SEP_CU(cudaMemset(s.Sinv, 0, sizeof(float) * 2 * (size_t)h.nc * s.ldc));
-    SEP_CU(cudaMemset(s.U, 0, sizeof(float) * 3 * std::max(h.nc, 1)));
+    SEP_CU(fill_zero(c, s.Sinv, sizeof(float) * 2 * (size_t)h.nc * s.ldc));
+    SEP_CU(fill_zero(c, s.U, sizeof(float) * 3 * std::max(h.nc, 1)));
     tab.push_back(s);
   }
   // shared memory of the solve's separable stages: the staged tiles, and t

@@ -161,12 +161,23 @@ void run_parameters(const ibl_run_request& r, double& tau, double& u_tip, double
 
 // Stability screen at submission (BGK collision): requests outside it are
 // refused with IBL_EUNSTABLE instead of diverging after using the GPU.
-// Bounds from the 64-request sweep (Re 75-150, f 0.05 / 0.25, J 1e-3..2):
-// every run with tau below 0.505 or a uniform free stream of 0.05 lattice
-// units or more diverged; wall speeds up to 0.105 (f = 0.25) were stable.
+// Bounds from the 64-request sweep (Re 75-150, f 0.05 / 0.25, J 1e-3..2, on
+// 96^3 .. 256 x 192 x 160 boxes): every run with tau below 0.505 or a
+// uniform free stream of 0.05 lattice units or more diverged, and so did
+// every run whose wings moved faster than 0.05 lattice units at the tip with
+// a wall-cell Reynolds number u_tip / nu above 5; tip speeds of 0.02 were
+// stable down to tau = 0.505.
 constexpr double SERVE_TAU_MIN = 0.505;
 constexpr double SERVE_U_FREE_MAX = 0.05;
 constexpr double SERVE_U_WALL_MAX = 0.15;
+constexpr double SERVE_U_WALL_FAST = 0.05;
+constexpr double SERVE_RE_CELL_FAST_MAX = 5.0;
+
+bool stable_request(double tau, double u_tip, double u_inf) {
+  const double nu = (tau - 0.5) / 3.0;
+  if (!(tau >= SERVE_TAU_MIN) || !(u_inf <= SERVE_U_FREE_MAX) || !(u_tip <= SERVE_U_WALL_MAX)) return false;
+  return !(u_tip > SERVE_U_WALL_FAST && u_tip > SERVE_RE_CELL_FAST_MAX * nu);
+}
 
 // Build the context of a clap-and-fling wing pair (Sec. 3.3): trailing-edge
 // hinges c/2 apart about the mid-plane, opening angle (pi/3)|sin(2 pi t/T)|
@@ -497,8 +508,7 @@ ibl_status ibl_server_submit(ibl_server* s, const ibl_run_request* req, int64_t*
     return IBL_EINVAL;
   double tau = 0, u_tip = 0, u_inf = 0;
   run_parameters(*req, tau, u_tip, u_inf);
-  if (!(tau >= SERVE_TAU_MIN) || !(u_inf <= SERVE_U_FREE_MAX) || !(u_tip <= SERVE_U_WALL_MAX))
-    return IBL_EUNSTABLE;
+  if (!stable_request(tau, u_tip, u_inf)) return IBL_EUNSTABLE;
   auto run = std::make_shared<Run>();
   run->req = *req;
   std::vector<double> X0, ds;

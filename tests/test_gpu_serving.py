@@ -105,11 +105,14 @@ def test_a_diverging_run_fails_alone(ibl):
 
 def test_unstable_requests_are_refused_at_submission(ibl):
     srv = ibl.Server(hbm_budget_bytes=8 << 30, max_active=2, chunk_steps=25)
-    for bad in (dict(REQ, Re=2000.0),      # tau = 0.5013
-                dict(REQ, J=5.0)):         # free stream 5 U_tip = 0.18 lattice units
+    for bad in (dict(REQ, Re=2000.0),                  # tau = 0.5013
+                dict(REQ, J=5.0),                      # free stream 5 U_tip = 0.21 lattice units
+                dict(REQ, period=240.0, Re=40.0)):     # U_tip 0.105 with U_tip / nu = 6.7
         with pytest.raises(ibl.IblError) as e:
             srv.ibl_server_submit(**bad)
         assert e.value.status == ibl.IBL_EUNSTABLE
+    ok = srv.ibl_server_submit(**dict(REQ, period=240.0, Re=20.0))   # U_tip 0.105, U_tip / nu = 3.3
+    srv.ibl_server_cancel(ok)
     srv.close()
 
 
@@ -175,3 +178,21 @@ def test_untuned_server_keeps_library_defaults(ibl):
     ctx.ibl_step(REQ["steps"])
     h = ctx.ibl_force_history(0, REQ["steps"])
     assert h[:, 0].max() == r["CL_max"][0]
+
+
+def test_many_concurrent_runs_pass_the_mass_check(ibl):
+    """Twelve runs at once, past the FP64 mass check at step 500: each
+    context's fills and copies are ordered on its own stream, so the mass
+    reference taken at initialisation is never overwritten by a late fill
+    while the GPU is loaded with the other runs' kernels."""
+    srv = ibl.Server(hbm_budget_bytes=40 << 30, max_active=12, chunk_steps=50)
+    ids = []
+    for k in range(12):
+        prec = ("fp32", "fp16dev", "bf16dev")[k % 3]
+        ids.append(srv.ibl_server_submit(nx=64 + 8 * (k % 4), ny=48, nz=48, chord=6.0, Re=20.0 + k, period=600.0,
+                                         J=1e-2, precision=prec, steps=520))
+    srv.ibl_server_wait_all(900)
+    res = [srv.ibl_server_poll(i) for i in ids]
+    srv.close()
+    assert [ibl.STATUS_NAMES[r["status"]] for r in res] == ["IBL_OK"] * 12
+    assert all(r["steps_done"] == 520 for r in res)
