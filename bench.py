@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--overlap", type=int, default=-1, choices=[-1, 0, 1],
                     help="collide scheduling: -1 automatic, 0 one kernel after the IB chain, 1 split")
     ap.add_argument("--solver-blocks", type=int, default=0, help="blocks of the implicit solve (0: default)")
+    ap.add_argument("--collide-shape", default=None,
+                    help="BXxBYxPAIRS: thread block and two-cells-per-thread flag of the one-kernel collide")
     ap.add_argument("--phases", action="store_true", help="also time every phase of the step (events)")
     ap.add_argument("--initial-guess", choices=("extrapolated", "previous", "zero"), default="extrapolated",
                     help="initial guess of each implicit solve")
@@ -351,6 +353,9 @@ def measure(ibl, cfg, args, steps, warmup, dist=None, clocks=None, extras=True):
     ctx = ibl.from_workload(cfg)
     ctx.ibl_set_overlap(args.overlap)
     ctx.ibl_solver_blocks(args.solver_blocks)
+    if args.collide_shape:
+        bx, by, pairs = (int(v) for v in args.collide_shape.lower().split("x"))
+        ctx.ibl_set_collide_shape(bx, by, pairs)
     guess = {"extrapolated": True, "previous": False, "zero": None}[args.initial_guess]
     refresh = args.refresh_every or 384
     if args.refresh_every or args.initial_guess != "extrapolated":

@@ -78,7 +78,7 @@ struct ibl_ctx {
   cudaEvent_t ev_bulk = nullptr;    // bulk collide done (stream_bulk)
   int overlap = -1;                 // -1 automatic, 0 off, 1 on
   int collide_bx = 64, collide_by = 4;   // thread block of the one-kernel collide
-  bool collide_pairs = true;         // two cells per thread where the storage and nx allow
+  int collide_pairs = 1;             // 16-bit storage: 1 two cells per thread, 2 staged planes, 0 one
   size_t elem = 4;               // bytes per stored population
   void* f[2] = {nullptr, nullptr};
   int cur = 0;

@@ -433,6 +433,16 @@ __device__ __forceinline__ void collide_pair(F2 g[Q], const FluidParams<float>& 
   }
 }
 
+// The pair (x, x + 1) when either cell lies on a non-periodic face: the
+// one-cell path with its face gathers, out of line so that its registers
+// do not count against the two-cell kernels' hot path.
+template <int Q, class T, bool IB>
+__device__ __noinline__ void collide_face_pair(const DirPtrs<Q, T>& P, const FluidParams<float>& p, int x, int y,
+                                               int z) {
+  collide_cell<Q, T, true, IB>(P, p, x, y, z);
+  collide_cell<Q, T, true, IB>(P, p, x + 1, y, z);
+}
+
 // Every cell of a grid with even nx: 2 x-adjacent cells per thread,
 // 256-thread blocks (64 x 4 threads by default); IBL_PAIRS_MIN_BLOCKS blocks
 // per SM without the band lookup, three with it.
@@ -451,14 +461,172 @@ __global__ void __launch_bounds__(256, IB ? 3 : IBL_PAIRS_MIN_BLOCKS) k_collide_
   gather_pair_words<Q, T>(P, inside ? x : p.nx - 2, inside ? y : p.ny - 1, z, p, g);
   if (!inside) return;
   if (on_special_face<float>(x, y, z, Lat<Q>::D, p) || on_special_face<float>(x + 1, y, z, Lat<Q>::D, p)) {
-    collide_cell<Q, T, true, IB>(P, p, x, y, z);
-    collide_cell<Q, T, true, IB>(P, p, x + 1, y, z);
+    collide_face_pair<Q, T, IB>(P, p, x, y, z);
     return;
   }
   collide_pair<Q, IB>(g, p, x, y, z);
   const int cell = (z * p.ny + y) * p.nx + x;
 #pragma unroll
   for (int i = 0; i < Q; ++i) *reinterpret_cast<unsigned*>(P.d[i] + cell) = Pack16<T>::st(g[i]);
+}
+
+// ---------------------------------------------------------------- 16-bit storage: staged planes
+// The two-cell kernel above keeps 19 words per thread in flight and then
+// computes; at 4 blocks per SM the HBM then idles while most warps compute
+// (long-scoreboard stalls lead, DRAM ~64 % busy).  Here a block of 64 x 4
+// threads owns 128 x 4 cells of a column of SZ planes and walks it in z.
+// While it collides plane z from shared memory, the source rows of plane
+// z + 1 (for each direction i: the 4 rows y - c_y,i of plane z - c_z,i,
+// cells x0 - 8 .. x0 + 135, one 288-byte segment each) arrive by bulk
+// asynchronous copies (cp.async.bulk, completion counted in bytes on an
+// mbarrier), so the loads of the next plane overlap the arithmetic of this
+// one without holding registers.  Rows and planes wrap periodically; cells
+// on non-periodic faces take the one-cell path (global pulls).  Every
+// segment starts on a 16-byte boundary and is a multiple of 16 bytes long
+// because nx is a multiple of 8.  The populations are bitwise those of the
+// other kernels: the same values reach the same packed collision.
+constexpr int SX = 128;                    // cells per block in x
+constexpr int SY = 4;                      // rows per block
+constexpr int SZ = 16;                     // planes per block
+constexpr int SPAD = 8;                    // halo cells on each side (one 16-byte chunk)
+constexpr int SROW = SX + 2 * SPAD;        // staged cells per row
+constexpr long long STAGE_WAIT_LIMIT = 1LL << 26;   // mbarrier polls before giving up
+
+__host__ __device__ constexpr size_t staged_smem_bytes(int Q) {
+  return 2 * (size_t)Q * SY * SROW * 2 + 2 * sizeof(unsigned long long);
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// One poll of the barrier's phase with the given parity; true once it completed.
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait: false if the phase did not complete within the poll limit.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (long long k = 0; k < STAGE_WAIT_LIMIT; ++k)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+
+// Order this thread's earlier shared-memory accesses before the async
+// proxy's writes into the same buffer.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Thread t < Q * SY stages row t % SY of direction t / SY for plane z into
+// buf: cells x0 - SPAD .. x0 + SX + SPAD - 1 of source row y0 + r - c_y of
+// source plane z - c_z, both wrapped, as contiguous pieces split where the
+// row wraps in x.
+template <int Q, class T>
+__device__ __forceinline__ void stage_plane(const DirPtrs<Q, T>& P, const FluidParams<float>& p, T* buf,
+                                            unsigned long long* bar, int x0, int y0, int z, int tid) {
+  if (tid >= Q * SY) return;
+  const int i = tid / SY, r = tid % SY;
+  int ys = y0 + r - Lat<Q>::cy(i);
+  ys = ((ys % p.ny) + p.ny) % p.ny;
+  int zs = z - Lat<Q>::cz(i);
+  zs = ((zs % p.nz) + p.nz) % p.nz;
+  // the direction's base P.s[i] is P.s[0] + i N (dir_ptrs), formed here so
+  // that the parameter array is not indexed by a run-time value
+  const T* row = P.s[0] + (long long)i * p.N + ((long long)zs * p.ny + ys) * p.nx;
+  T* dst = buf + (i * SY + r) * SROW;
+  fence_proxy_async();
+  mbar_arrive_expect_tx(bar, SROW * (unsigned)sizeof(T));
+  int done = 0;
+  int xs = ((x0 - SPAD) % p.nx + p.nx) % p.nx;
+  while (done < SROW) {
+    const int len = min(SROW - done, p.nx - xs);
+    bulk_copy_g2s(dst + done, row + xs, (unsigned)(len * sizeof(T)), bar);
+    done += len;
+    xs = 0;
+  }
+}
+
+// One thread per cell pair (x, x + 1), 64 x 4 threads, SZ planes per block.
+template <int Q, class T, bool IB>
+__global__ void __launch_bounds__(256, IB ? 3 : 4) k_collide_pairs_staged(DirPtrs<Q, T> P, FluidParams<float> p) {
+  extern __shared__ __align__(128) unsigned char stage_smem[];
+  T* bufs = reinterpret_cast<T*>(stage_smem);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(stage_smem + 2 * (size_t)Q * SY * SROW * sizeof(T));
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * blockDim.x + tx;
+  const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, z0 = blockIdx.z * SZ;
+  const int planes = min(SZ, p.nz - z0);
+  const int x = x0 + 2 * tx, y = y0 + ty;
+  const bool inside = x < p.nx && y < p.ny;
+  if (tid == 0) {
+    mbar_init(&bar[0], Q * SY);
+    mbar_init(&bar[1], Q * SY);
+  }
+  __syncthreads();
+  stage_plane<Q, T>(P, p, bufs, &bar[0], x0, y0, z0, tid);
+  for (int k = 0; k < planes; ++k) {
+    const int b = k & 1;
+    T* buf = bufs + (size_t)b * Q * SY * SROW;
+    if (k + 1 < planes) stage_plane<Q, T>(P, p, bufs + (size_t)(b ^ 1) * Q * SY * SROW, &bar[b ^ 1], x0, y0,
+                                          z0 + k + 1, tid);
+    const bool ok = mbar_wait(&bar[b], (unsigned)((k >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      // a copy did not land within the limit: report it, give the copies in
+      // flight one more bounded wait, and leave this block's cells undone
+      if (tid == 0) atomicOr(p.status, ST_TIMEOUT);
+      mbar_wait(&bar[b], (unsigned)((k >> 1) & 1));
+      if (k + 1 < planes) mbar_wait(&bar[b ^ 1], (unsigned)(((k + 1) >> 1) & 1));
+      return;
+    }
+    const int z = z0 + k;
+    if (inside) {
+      if (on_special_face<float>(x, y, z, Lat<Q>::D, p) || on_special_face<float>(x + 1, y, z, Lat<Q>::D, p)) {
+        collide_face_pair<Q, T, IB>(P, p, x, y, z);
+      } else {
+        F2 g[Q];
+        const T* base = buf + ty * SROW + SPAD + 2 * tx;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          const T* s = base + i * SY * SROW;
+          if (Lat<Q>::cx(i) == 0) {
+            const Pair16<T> w = *reinterpret_cast<const Pair16<T>*>(s);
+            g[i] = Pack16<T>::ld(w.a, w.b);
+          } else {
+            const int d = -Lat<Q>::cx(i);   // sources x - c_x, x + 1 - c_x
+            g[i] = Pack16<T>::ld(s[d], s[d + 1]);
+          }
+        }
+        collide_pair<Q, IB>(g, p, x, y, z);
+        const int cell = (z * p.ny + y) * p.nx + x;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) *reinterpret_cast<unsigned*>(P.d[i] + cell) = Pack16<T>::st(g[i]);
+      }
+    }
+    __syncthreads();   // every thread is done with buf before it is staged again
+  }
 }
 
 // Every cell, 64 x 4 cells per block; IB selects the band lookup.
@@ -683,7 +851,19 @@ cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
   const DirPtrs<Q, T> P = dir_ptrs<Q, T>(c);
   dim3 b = cell_block(c), g = cell_grid(c, b);
   if constexpr (sizeof(T) == 2) {
-    if (!c->poststream && c->nx % 2 == 0 && c->collide_pairs) {
+    if constexpr (Q == 19) {
+      if (!c->poststream && c->nx % 8 == 0 && c->collide_pairs == 2) {
+        // 16-bit storage, nx a multiple of 8: staged planes (see k_collide_pairs_staged)
+        const dim3 sb(SX / 2, SY, 1);
+        const dim3 sg((c->nx + SX - 1) / SX, (c->ny + SY - 1) / SY, (c->nz + SZ - 1) / SZ);
+        const size_t smem = staged_smem_bytes(Q);
+        if (with_ib) k_collide_pairs_staged<Q, T, true><<<sg, sb, smem, c->stream>>>(P, p);
+        else k_collide_pairs_staged<Q, T, false><<<sg, sb, smem, c->stream>>>(P, p);
+        c->launches++;
+        return cudaGetLastError();
+      }
+    }
+    if (!c->poststream && c->nx % 2 == 0 && c->collide_pairs >= 1) {
       // 16-bit storage: two x-adjacent cells per thread
       g.x = (c->nx / 2 + b.x - 1) / b.x;
       if (with_ib) k_collide_pairs<Q, T, true><<<g, b, 0, c->stream>>>(P, p);

@@ -39,7 +39,7 @@ using clock_type = std::chrono::steady_clock;
 struct Launch {
   int overlap, bx, by, pairs;
 };
-constexpr Launch CANDIDATES[] = {{1, 64, 4, 1}, {0, 64, 4, 1}, {0, 128, 2, 1}, {0, 32, 8, 1}, {0, 256, 1, 1}};
+constexpr Launch CANDIDATES[] = {{1, 64, 4, 1}, {0, 64, 4, 1}, {0, 64, 2, 1}, {0, 128, 2, 1}, {0, 64, 4, 2}};
 constexpr int NCAND = sizeof(CANDIDATES) / sizeof(CANDIDATES[0]);
 constexpr int TUNE_MIN_STEPS = 2;          // timed steps per candidate
 constexpr int MARKERS_PER_SOLVE_BLOCK = 64;

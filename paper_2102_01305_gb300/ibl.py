@@ -371,7 +371,8 @@ class Context:
         _check(self.h, _lib.ibl_set_overlap(self.h, int(mode)))
 
     def ibl_set_collide_shape(self, bx=64, by=4, pairs=1):
-        """Thread block (bx x by) of the one-kernel collide; pairs 1: two cells per thread (16-bit storage)."""
+        """Thread block (bx x by) of the one-kernel collide; 16-bit storage: pairs 1 two cells per
+        thread, 2 the same on planes staged in shared memory, 0 one cell per thread."""
         _check(self.h, _lib.ibl_set_collide_shape(self.h, int(bx), int(by), int(pairs)))
 
     def ibl_interpolate_points(self, X, U=None, rho=None):
