@@ -281,11 +281,11 @@ PCG_PHASES = ["stage_z", "spmv_rows", "block_reduce", "barrier1", "alpha", "stag
 
 def pcg_trace_summary(tr, iters):
     """Median phase durations (us) of one solve from its timestamps: slots 0-3
-    are start / after rebuild / after set-up / end; iteration k (k < 27) has 9
+    are start / after rebuild / after set-up / end; iteration k (k < 26) has 9
     marks from slot 8 + 9k: scalars ready, then the end of each phase."""
     if not (tr[0] and tr[3]):
         return None
-    n = min(iters, 27)
+    n = min(iters, 26)
     base = [8 + 9 * k for k in range(n)]
     med = lambda v: round(statistics.median(v), 3) if v else None
     out = {"total_us": (tr[3] - tr[0]) / 1e3, "rebuild_us": (tr[1] - tr[0]) / 1e3,

@@ -341,7 +341,7 @@ ibl_status ibl_set_collide_shape(ibl_ctx* ctx, int32_t bx, int32_t by, int32_t p
  * implicit solve: [0] start, [1] after the optional preconditioner rebuild,
  * [2] after set-up, [3] end; [4]-[7] the four phases of the rebuild's first
  * pivot block (pivot inverse, row panel, trailing update, column panel);
- * iteration k (k < 27) at 8 + 9k: recurrence
+ * iteration k (k < 26) at 8 + 9k: recurrence
  * scalars ready, search direction input staged, SpMV rows done, block
  * reduction done, grid barrier passed, step length ready, preconditioner
  * input staged, preconditioner rows done, grid barrier passed.  With the

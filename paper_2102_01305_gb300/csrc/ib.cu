@@ -1323,7 +1323,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   const bool stage_z = 3 * m <= A.smem_floats;
   while (!done && it < PCG_MAX_ITERS) {
     // ---- P1: p = z + beta p;  A p = G z + beta A p;  partial p.Ap;  FP32 copies of r and A p
-    const int ts = 8 + TRACE_PER_IT * it;
+    // iterations 0..25 use slots 8..241; later ones are not traced (250-253 hold the set-up's marks)
+    const int ts = it < 26 ? 8 + TRACE_PER_IT * it : TRACE_SLOTS;
     trace_mark(A, ts);
     {
       df pAp = dzero;

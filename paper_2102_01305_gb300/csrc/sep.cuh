@@ -278,19 +278,30 @@ static __device__ void sep_colpass(const SepBody* sb, int nb, bool second, float
   }
 }
 
-// Stage D: u = S^-1 t.  One block per 32 rows of a body: t (the complement
-// entries of R0, three components) is staged in shared memory when it fits,
-// then one warp per row; each double-float entry of S^-1 times an FP32 t
-// enters a double-float accumulator (the product's rounding error included).
+// Stage D: u = S^-1 t.  The complement rows of all bodies are split into
+// equal contiguous ranges, one per block, so that every SM takes part; per
+// body in its range a block stages t (the complement entries of R0, three
+// components) in shared memory when it fits, then one warp per row; each
+// double-float entry of S^-1 times an FP32 t enters a double-float
+// accumulator (the product's rounding error included).  A row's sum does not
+// depend on the block that forms it.
 static __device__ void sep_schur(const SepBody* sb, int nb, float* sm, int smem_floats) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const long long total = sep_items(sb, nb, 2);
-  for (long long it = blockIdx.x; it < total; it += gridDim.x) {
-    long long li = it;
-    const int b = sep_item_body(sb, nb, 2, li);
+  const int warps = blockDim.x >> 5;
+  // the complement rows of all bodies, split into equal contiguous ranges,
+  // one per block (every SM takes part), one warp per row
+  long long rows = 0;
+  for (int b = 0; b < nb; ++b) rows += sb[b].nc;
+  const long long r0 = (long long)blockIdx.x * rows / gridDim.x;
+  const long long r1 = (long long)(blockIdx.x + 1) * rows / gridDim.x;
+  long long base = 0;
+  for (int b = 0; b < nb; ++b) {
     const SepBody& B = sb[b];
     const int nc = B.nc;
+    const long long lo = r0 > base ? r0 : base, hi = r1 < base + nc ? r1 : base + nc;
+    base += nc;
+    if (lo >= hi) continue;
     const long long plane = (long long)B.ni * B.nk;
     const bool stage_t = 3 * nc <= smem_floats;
     __syncthreads();
@@ -303,42 +314,43 @@ static __device__ void sep_schur(const SepBody* sb, int nb, float* sm, int smem_
       });
     }
     __syncthreads();
-    const int p = (int)li * 32 + wib;
-    if (p >= nc) continue;
-    // two (hi, lo) entries per 128-bit load
-    const float4* row = reinterpret_cast<const float4*>(B.Sinv + 2LL * p * B.ldc);
-    dfacc a0 = acc_zero(), a1 = acc_zero(), a2 = acc_zero();
-    const int nq = B.ldc >> 1;
+    for (long long pr = lo + wib; pr < hi; pr += warps) {
+      const int p = (int)(pr - (base - nc));
+      // two (hi, lo) entries per 128-bit load
+      const float4* row = reinterpret_cast<const float4*>(B.Sinv + 2LL * p * B.ldc);
+      dfacc a0 = acc_zero(), a1 = acc_zero(), a2 = acc_zero();
+      const int nq = B.ldc >> 1;
 #pragma unroll 4
-    for (int q = lane; q < nq; q += 32) {
-      const float4 s4 = __ldg(row + q);
-      const df sv[2] = {df_make(s4.x, s4.y), df_make(s4.z, s4.w)};
+      for (int q = lane; q < nq; q += 32) {
+        const float4 s4 = __ldg(row + q);
+        const df sv[2] = {df_make(s4.x, s4.y), df_make(s4.z, s4.w)};
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int col = 2 * q + e;
-        if (col < nc) {
-          float t0, t1, t2;
-          if (stage_t) {
-            t0 = sm[col];
-            t1 = sm[nc + col];
-            t2 = sm[2 * nc + col];
-          } else {
-            const int r = B.crect[col];
-            t0 = __ldcg(B.R0 + r);
-            t1 = __ldcg(B.R0 + plane + r);
-            t2 = __ldcg(B.R0 + 2 * plane + r);
+        for (int e = 0; e < 2; ++e) {
+          const int col = 2 * q + e;
+          if (col < nc) {
+            float t0, t1, t2;
+            if (stage_t) {
+              t0 = sm[col];
+              t1 = sm[nc + col];
+              t2 = sm[2 * nc + col];
+            } else {
+              const int r = B.crect[col];
+              t0 = __ldcg(B.R0 + r);
+              t1 = __ldcg(B.R0 + plane + r);
+              t2 = __ldcg(B.R0 + 2 * plane + r);
+            }
+            acc_fma_f(a0, sv[e], t0);
+            acc_fma_f(a1, sv[e], t1);
+            acc_fma_f(a2, sv[e], t2);
           }
-          acc_fma_f(a0, sv[e], t0);
-          acc_fma_f(a1, sv[e], t1);
-          acc_fma_f(a2, sv[e], t2);
         }
       }
-    }
-    const df u0 = df_warp_sum(acc_value(a0)), u1 = df_warp_sum(acc_value(a1)), u2 = df_warp_sum(acc_value(a2));
-    if (lane == 0) {
-      B.U[p] = u0.hi + u0.lo;
-      B.U[nc + p] = u1.hi + u1.lo;
-      B.U[2 * nc + p] = u2.hi + u2.lo;
+      const df u0 = df_warp_sum(acc_value(a0)), u1 = df_warp_sum(acc_value(a1)), u2 = df_warp_sum(acc_value(a2));
+      if (lane == 0) {
+        B.U[p] = u0.hi + u0.lo;
+        B.U[nc + p] = u1.hi + u1.lo;
+        B.U[2 * nc + p] = u2.hi + u2.lo;
+      }
     }
   }
 }
