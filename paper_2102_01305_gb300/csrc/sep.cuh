@@ -285,6 +285,10 @@ static __device__ void sep_colpass(const SepBody* sb, int nb, bool second, float
 // double-float entry of S^-1 times an FP32 t enters a double-float
 // accumulator (the product's rounding error included).  A row's sum does not
 // depend on the block that forms it.
+#ifndef IBL_SCHUR_BATCH
+#define IBL_SCHUR_BATCH 2
+#endif
+constexpr int SCHUR_BATCH = IBL_SCHUR_BATCH;   // 128-bit loads per lane in flight in stage D
 static __device__ void sep_schur(const SepBody* sb, int nb, float* sm, int smem_floats) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -320,14 +324,23 @@ static __device__ void sep_schur(const SepBody* sb, int nb, float* sm, int smem_
       const float4* row = reinterpret_cast<const float4*>(B.Sinv + 2LL * p * B.ldc);
       dfacc a0 = acc_zero(), a1 = acc_zero(), a2 = acc_zero();
       const int nq = B.ldc >> 1;
-#pragma unroll 4
-      for (int q = lane; q < nq; q += 32) {
-        const float4 s4 = __ldg(row + q);
+      // SCHUR_BATCH loads of a lane are issued before their products (2:
+      // 26 us for the stage at 2 x 1708 complement rows, 29 us with one at a
+      // time, 34 us with 8, which spills); the accumulation order is unchanged
+      for (int q0 = lane; q0 < nq; q0 += 32 * SCHUR_BATCH) {
+        float4 s4b[SCHUR_BATCH];
+#pragma unroll
+        for (int u = 0; u < SCHUR_BATCH; ++u)
+          s4b[u] = q0 + 32 * u < nq ? __ldg(row + q0 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < SCHUR_BATCH; ++u) {
+        const int q = q0 + 32 * u;
+        const float4 s4 = s4b[u];
         const df sv[2] = {df_make(s4.x, s4.y), df_make(s4.z, s4.w)};
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const int col = 2 * q + e;
-          if (col < nc) {
+          if (q < nq && col < nc) {
             float t0, t1, t2;
             if (stage_t) {
               t0 = sm[col];
@@ -343,6 +356,7 @@ static __device__ void sep_schur(const SepBody* sb, int nb, float* sm, int smem_
             acc_fma_f(a1, sv[e], t1);
             acc_fma_f(a2, sv[e], t2);
           }
+        }
         }
       }
       const df u0 = df_warp_sum(acc_value(a0)), u1 = df_warp_sum(acc_value(a1)), u2 = df_warp_sum(acc_value(a2));
