@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--collide-shape", default=None,
                     help="BXxBYxPAIRS: thread block and two-cells-per-thread flag of the one-kernel collide")
     ap.add_argument("--phases", action="store_true", help="also time every phase of the step (events)")
-    ap.add_argument("--initial-guess", choices=("extrapolated", "previous", "zero"), default="extrapolated",
+    ap.add_argument("--initial-guess", choices=("extrapolated", "quadratic", "previous", "zero"), default="extrapolated",
                     help="initial guess of each implicit solve")
     ap.add_argument("--refresh-every", type=int, default=0,
                     help="steps between preconditioner rebuilds (0: the library default)")
@@ -356,7 +356,7 @@ def measure(ibl, cfg, args, steps, warmup, dist=None, clocks=None, extras=True):
     if args.collide_shape:
         bx, by, pairs = (int(v) for v in args.collide_shape.lower().split("x"))
         ctx.ibl_set_collide_shape(bx, by, pairs)
-    guess = {"extrapolated": True, "previous": False, "zero": None}[args.initial_guess]
+    guess = {"extrapolated": 1, "quadratic": 2, "previous": 0, "zero": -1}[args.initial_guess]
     refresh = args.refresh_every or 384
     if args.refresh_every or args.initial_guess != "extrapolated":
         ctx.ibl_solver_config(refresh, 0.0, guess)

@@ -280,8 +280,8 @@ ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_resid
  * iterations (sum 2 m_b^3 / sum 6 m_b^2, at least 64).  tol is the relative
  * residual in the preconditioner's norm (0 = default: 1e-10 for FP64
  * storage, 1e-7 for FP32, 1e-6 for FP16/BF16).  extrapolate chooses each
- * solve's initial guess: > 0 (default 1) 2 w_{n-1} - w_{n-2}, 0 w_{n-1},
- * < 0 zero.  Changing these changes the iterates, not the system being
+ * solve's initial guess: 2 (or more) 3 w_{n-1} - 3 w_{n-2} + w_{n-3},
+ * 1 (default) 2 w_{n-1} - w_{n-2}, 0 w_{n-1}, < 0 zero.  Changing these changes the iterates, not the system being
  * solved. */
 ibl_status ibl_solver_config(ibl_ctx* ctx, int32_t refresh_every, double tol, int32_t extrapolate);
 

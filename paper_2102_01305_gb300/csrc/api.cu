@@ -649,7 +649,7 @@ ibl_status ibl_solver_config(ibl_ctx* c, int32_t refresh_every, double tol, int3
   if (refresh_every < 1 || !(tol >= 0.0) || tol >= 1.0) return fail(c, IBL_EINVAL, "refresh_every >= 1, 0 <= tol < 1");
   c->refresh_every = refresh_every;
   c->solver_tol = tol;
-  c->extrapolate = extrapolate > 0 ? 1 : (extrapolate == 0 ? 0 : -1);
+  c->extrapolate = extrapolate >= 2 ? 2 : (extrapolate == 1 ? 1 : (extrapolate == 0 ? 0 : -1));
   return IBL_OK;
 }
 

@@ -46,10 +46,10 @@ constexpr double PCG_TOL_FP32 = 1e-7;   // FP32 deviations
 constexpr double PCG_TOL_HALF = 1e-6;   // FP16 / BF16 deviations
 
 // Early rebuilds follow a rent-or-buy rule.  Since the last rebuild, every
-// solve adds to a running excess the iterations it needed beyond both the
-// first solve after that rebuild and REBUILD_ITERS_OK (below that count,
-// the iteration count varies with the flow more than with the
-// preconditioner's age).  When the excess passes the rebuild's cost in
+// solve adds to a running excess the iterations it needed beyond the first
+// solve after that rebuild (on the 256 x 192 x 160 wings the count climbs
+// from 11 to 20 within 380 steps as the markers move away from the
+// rebuild's pose, and falls back to 10 after a rebuild).  When the excess passes the rebuild's cost in
 // iterations, the next solve rebuilds first.  That cost is the ratio of the
 // operation counts: 2 m_b^3 for an inverse, and 6 m_b^2 for one iteration's
 // preconditioner product over three right-hand sides.  Each is summed over
@@ -57,7 +57,6 @@ constexpr double PCG_TOL_HALF = 1e-6;   // FP16 / BF16 deviations
 // iteration counts enter the rule, so runs stay reproducible bit for bit.
 // A solve that does not converge asks for a rebuild directly.
 constexpr int REBUILD_MIN_EXCESS = 64;
-constexpr int REBUILD_ITERS_OK = 40;
 
 struct BodyTable {
   int n;
@@ -527,6 +526,7 @@ struct PcgArgs {
   // double-float vectors of the recurrence (m x 3)
   df* wd;           // solution
   df* wprevd;       // solution of the step before (extrapolated warm start)
+  df* wprev2d;      // and of the step before that (quadratic extrapolation)
   df* rd;
   df* pd;
   df* Apd;
@@ -1181,19 +1181,29 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
   }
   trace_mark(A, 1);
 
-  // ---- set-up (double-float vectors): w0 = 0, the last solution, or
-  // 2 w_n-1 - w_n-2 once two exist (the solution varies smoothly in time);
-  // r = B - G w0; FP32 copies; p = A p = 0
+  // ---- set-up (double-float vectors): w0 = 0, the last solution,
+  // 2 w_n-1 - w_n-2 once two exist, or 3 w_n-1 - 3 w_n-2 + w_n-3 once three
+  // exist (the solution varies smoothly in time); r = B - G w0; FP32 copies;
+  // p = A p = 0
   const df dzero = df_make(0.f, 0.f);
   if (A.warm >= 2) {
     for (int i = gtid; i < 3 * m; i += nthreads) {
-      const df cur = A.wd[i];
-      A.wd[i] = df_sub(df_make(2.f * cur.hi, 2.f * cur.lo), A.wprevd[i]);
+      const df cur = A.wd[i], prev = A.wprevd[i];
+      if (A.warm >= 3) {
+        const df t = df_sub(cur, prev);
+        A.wd[i] = df_add(df_add(df_add(A.wprev2d[i], t), t), t);
+      } else {
+        A.wd[i] = df_sub(df_make(2.f * cur.hi, 2.f * cur.lo), prev);
+      }
+      A.wprev2d[i] = prev;
       A.wprevd[i] = cur;
     }
     grid.sync();
   } else if (A.warm == 1) {
-    for (int i = gtid; i < 3 * m; i += nthreads) A.wprevd[i] = A.wd[i];
+    for (int i = gtid; i < 3 * m; i += nthreads) {
+      A.wprev2d[i] = A.wprevd[i];
+      A.wprevd[i] = A.wd[i];
+    }
   }
   for (int l = row0; l < m; l += rstep) {
     dfacc a0 = acc_zero(), a1 = acc_zero(), a2 = acc_zero();
@@ -1525,7 +1535,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
       A.info[4] = it;
       A.info[5] = 0;
     } else {
-      A.info[5] = min(A.info[5] + max(it - max(A.info[4], REBUILD_ITERS_OK), 0), 1 << 30);
+      A.info[5] = min(A.info[5] + max(it - A.info[4], 0), 1 << 30);
     }
     A.info[1] = (A.info[5] > A.rebuild_excess || !done) ? 1 : 0;
     A.info[2] = done ? 1 : 0;
@@ -1640,6 +1650,7 @@ cudaError_t ib_alloc(ibl_ctx* c) {
   IBL_CU(cudaMalloc(&c->d_B, sizeof(double) * 3 * m));
   IBL_CU(cudaMalloc(&c->d_w, sizeof(double) * 3 * m));
   IBL_CU(cudaMalloc(&c->d_wprev, sizeof(double) * 3 * m));
+  IBL_CU(cudaMalloc(&c->d_wprev2, sizeof(double) * 3 * m));
   IBL_CU(cudaMemsetAsync(c->d_w, 0, sizeof(double) * 3 * m, c->stream));
   IBL_CU(cudaMalloc(&c->d_r, sizeof(double) * 3 * m));
   IBL_CU(cudaMalloc(&c->d_p, sizeof(double) * 6 * m));
@@ -1711,7 +1722,7 @@ void ib_free(ibl_ctx* c) {
                   c->d_Ap, c->d_z, c->d_Gcol, c->d_Gval, c->d_Gnnz, c->d_Gdiag_max, c->d_M, c->d_red,
                   c->d_cg_info, c->d_cg_res, c->d_hist, c->d_mforce, c->d_boff, c->d_xf, c->d_trace,
                   c->d_acc, c->d_slot_body, c->d_mixed, c->d_cand, c->d_ncand,
-                  c->d_wprev};
+                  c->d_wprev, c->d_wprev2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   c->d_X0 = c->d_ds = c->d_X = c->d_U = c->d_Xp = c->d_Up = nullptr;
@@ -1726,7 +1737,7 @@ void ib_free(ibl_ctx* c) {
   c->d_trace = nullptr;
   c->d_acc = nullptr;
   c->d_slot_body = c->d_mixed = c->d_cand = c->d_ncand = nullptr;
-  c->d_wprev = nullptr;
+  c->d_wprev = c->d_wprev2 = nullptr;
   sep_free(c);
   c->ib_ready = false;
 }
@@ -1960,6 +1971,7 @@ cudaError_t ib_step_back(ibl_ctx* c) {
   A.Apd = reinterpret_cast<df*>(c->d_Ap);
   A.zf = reinterpret_cast<float*>(c->d_z);
   A.wprevd = reinterpret_cast<df*>(c->d_wprev);
+  A.wprev2d = reinterpret_cast<df*>(c->d_wprev2);
   A.rf = c->d_xf;
   A.Apf = c->d_xf + c->xf_floats;
   A.Bf = c->d_xf + 2 * c->xf_floats;
@@ -1999,7 +2011,9 @@ cudaError_t ib_step_back(ibl_ctx* c) {
     }
     A.rebuild_excess = (int)std::min(std::max(cube / std::max(square, 1.0), (double)REBUILD_MIN_EXCESS), 1e8);
   }
-  A.warm = c->extrapolate < 0 ? 0 : (c->warm_steps >= 2 && c->extrapolate ? 2 : (c->warm_steps >= 1 ? 1 : 0));
+  A.warm = c->extrapolate < 0 ? 0
+         : (c->extrapolate >= 2 && c->warm_steps >= 3 ? 3
+            : (c->extrapolate >= 1 && c->warm_steps >= 2 ? 2 : (c->warm_steps >= 1 ? 1 : 0)));
   const bool sched = !c->precond_valid || (c->step - c->last_refresh_step) >= c->refresh_every;
   A.refresh = sched ? 1 : 0;
   if (sched) {

@@ -154,7 +154,7 @@ struct ibl_ctx {
   bool precond_valid = false;
   bool warm = false;             // d_w holds the previous solution
   long long warm_steps = 0;      // consecutive solves behind d_w (2+: extrapolate)
-  int extrapolate = 1;            // initial guess: 1 extrapolated, 0 last solution, -1 zero
+  int extrapolate = 1;            // initial guess: 2 quadratic, 1 linear extrapolation, 0 last solution, -1 zero
   int refresh_every = 384;       // steps between scheduled preconditioner rebuilds
   double solver_tol = 0.0;       // 0: default for the storage precision
   int pcg_blocks = 0;            // blocks of the cooperative solve (0: half the SMs)
@@ -168,6 +168,7 @@ struct ibl_ctx {
   int resident_rows = -1;        // -1 preconditioner rows in shared memory when they fit, 0 never
   size_t pcg_smem = 0;           // dynamic shared memory of the last solve launch
   double* d_wprev = nullptr;     // m x 3 solution of the previous step
+  double* d_wprev2 = nullptr;    // m x 3 solution of the step before that
   // optional per-step event timing (ibl_profile)
   bool profiling = false;
   // 6 events per step: [0] start, [1] IB chain done, [2] collide done,

@@ -412,8 +412,14 @@ class Context:
         return it.value, res.value, ref.value
 
     def ibl_solver_config(self, refresh_every=384, tol=0.0, extrapolate=True):
-        """extrapolate: True (2 w_n-1 - w_n-2), False (w_n-1) or None (zero)."""
-        mode = -1 if extrapolate is None else (1 if extrapolate else 0)
+        """extrapolate: 2 (3 w_n-1 - 3 w_n-2 + w_n-3), True or 1 (2 w_n-1 - w_n-2),
+        False or 0 (w_n-1), None or -1 (zero)."""
+        if extrapolate is None:
+            mode = -1
+        elif isinstance(extrapolate, bool):
+            mode = 1 if extrapolate else 0
+        else:
+            mode = int(extrapolate)
         _check(self.h, _lib.ibl_solver_config(self.h, int(refresh_every), float(tol), mode))
 
     def ibl_solver_preconditioner(self, kind=-1, resident_rows=-1):
