@@ -324,17 +324,17 @@ ibl_status ibl_set_overlap(ibl_ctx* ctx, int32_t mode);
 
 /* Launch shape of the one-kernel collide (the kernel of steps without the
  * split, see ibl_set_overlap): thread blocks of bx x by threads, bx in
- * {32, 64, 128, 256}, bx * by <= 256 (default 64 x 4).  With 16-bit storage:
- * pairs = 1 (default) gives each thread the cells (x, x + 1) with pulls
- * from global memory (nx even); pairs = 2 has blocks of 64 x 4 threads walk
- * 16 z-planes of 128 x 4 cells, two cells per thread, the next plane's
- * source rows arriving in shared memory by bulk asynchronous copies while
- * the current one collides (D3Q19 with nx a multiple of 8; otherwise as 1);
- * in both the two collisions run as packed FP32 pairs; pairs = 0 one cell
- * per thread.  Every cell runs the same rounded
- * operations whatever the shape, so all shapes give bitwise the same
- * populations (a tuning knob, not a numerical one).  IBL_EINVAL for other
- * values. */
+ * {32, 64, 128, 256}, bx * by <= 256 (default 64 x 2).  With 16-bit storage
+ * and nx even, each thread takes the two x-adjacent cells (x, x + 1), whose
+ * collisions run as packed FP32 pairs: pairs = 3 (default) walks 8 z-planes
+ * per thread, the next plane's loads in flight while the current one
+ * collides; pairs = 1 one plane per thread; pairs = 2 blocks of 64 x 4
+ * threads walk 16 z-planes of 128 x 4 cells, the next plane's source rows
+ * arriving in shared memory by bulk asynchronous copies (D3Q19 with nx a
+ * multiple of 8; otherwise as 1); pairs = 0 one cell per thread.  Every
+ * cell runs the same rounded operations whatever the shape, so all shapes
+ * give bitwise the same populations (a tuning knob, not a numerical one).
+ * IBL_EINVAL for other values. */
 ibl_status ibl_set_collide_shape(ibl_ctx* ctx, int32_t bx, int32_t by, int32_t pairs);
 
 /* Phase timestamps (GPU global timer, ns, taken by block 0) of the last
@@ -438,8 +438,8 @@ typedef struct {
  * same results whatever their values (ibl_set_overlap,
  * ibl_set_collide_shape), so they are measured: the first chunk of a run
  * whose shape (grid, chord, precision, faces) has not been seen is split
- * between the candidates (split step; one kernel with 64 x 4, 64 x 2 or
- * 128 x 2 blocks; staged 16-bit planes), each timed with CUDA events on the run's
+ * between the candidates (split step; one kernel with 64 x 2, 128 x 1 or
+ * 64 x 4 blocks; staged 16-bit planes), each timed with CUDA events on the run's
  * stream, and the fastest is kept for that run and every later run of the
  * same shape.  A run's numbers therefore depend on its request only, alone
  * or in any mix. */

@@ -473,8 +473,8 @@ ibl_status ibl_set_overlap(ibl_ctx* c, int32_t mode) {
 
 ibl_status ibl_set_collide_shape(ibl_ctx* c, int32_t bx, int32_t by, int32_t pairs) {
   if (!c) return IBL_EINVAL;
-  if (!(bx == 32 || bx == 64 || bx == 128 || bx == 256) || by < 1 || bx * by > 256 || pairs < 0 || pairs > 2)
-    return fail(c, IBL_EINVAL, "collide shape: bx in {32, 64, 128, 256}, by >= 1, bx * by <= 256, pairs 0, 1 or 2");
+  if (!(bx == 32 || bx == 64 || bx == 128 || bx == 256) || by < 1 || bx * by > 256 || pairs < 0 || pairs > 3)
+    return fail(c, IBL_EINVAL, "collide shape: bx in {32, 64, 128, 256}, by >= 1, bx * by <= 256, pairs 0 .. 3");
   c->collide_bx = bx;
   c->collide_by = by;
   c->collide_pairs = pairs;

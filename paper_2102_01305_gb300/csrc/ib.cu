@@ -46,10 +46,12 @@ constexpr double PCG_TOL_FP32 = 1e-7;   // FP32 deviations
 constexpr double PCG_TOL_HALF = 1e-6;   // FP16 / BF16 deviations
 
 // Early rebuilds follow a rent-or-buy rule.  Since the last rebuild, every
-// solve adds to a running excess the iterations it needed beyond the first
-// solve after that rebuild (on the 256 x 192 x 160 wings the count climbs
-// from 11 to 20 within 380 steps as the markers move away from the
-// rebuild's pose, and falls back to 10 after a rebuild).  When the excess passes the rebuild's cost in
+// solve adds to a running excess the iterations it needed beyond both the
+// first solve after that rebuild and REBUILD_ITERS_OK.  Below that count a
+// rebuild does not pay: on the 256 x 192 x 160 wings the count climbs from
+// 11 to 20 within 380 steps as the markers leave the rebuild's pose, and
+// rebuilding on that excess (every 60-100 steps) left the step time
+// unchanged.  When the excess passes the rebuild's cost in
 // iterations, the next solve rebuilds first.  That cost is the ratio of the
 // operation counts: 2 m_b^3 for an inverse, and 6 m_b^2 for one iteration's
 // preconditioner product over three right-hand sides.  Each is summed over
@@ -57,6 +59,7 @@ constexpr double PCG_TOL_HALF = 1e-6;   // FP16 / BF16 deviations
 // iteration counts enter the rule, so runs stay reproducible bit for bit.
 // A solve that does not converge asks for a rebuild directly.
 constexpr int REBUILD_MIN_EXCESS = 64;
+constexpr int REBUILD_ITERS_OK = 40;
 
 struct BodyTable {
   int n;
@@ -1535,7 +1538,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(PcgArgs A) {
       A.info[4] = it;
       A.info[5] = 0;
     } else {
-      A.info[5] = min(A.info[5] + max(it - A.info[4], 0), 1 << 30);
+      A.info[5] = min(A.info[5] + max(it - max(A.info[4], REBUILD_ITERS_OK), 0), 1 << 30);
     }
     A.info[1] = (A.info[5] > A.rebuild_excess || !done) ? 1 : 0;
     A.info[2] = done ? 1 : 0;

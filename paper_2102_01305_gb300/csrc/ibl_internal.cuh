@@ -77,8 +77,9 @@ struct ibl_ctx {
   cudaEvent_t ev_tiles = nullptr;   // band tiles of the step assigned (stream)
   cudaEvent_t ev_bulk = nullptr;    // bulk collide done (stream_bulk)
   int overlap = -1;                 // -1 automatic, 0 off, 1 on
-  int collide_bx = 64, collide_by = 4;   // thread block of the one-kernel collide
-  int collide_pairs = 1;             // 16-bit storage: 1 two cells per thread, 2 staged planes, 0 one
+  int collide_bx = 64, collide_by = 2;   // thread block of the one-kernel collide
+  int collide_pairs = 3;             // 16-bit storage: 3 two cells and ZP planes per thread, 1 two cells,
+                                     // 2 staged planes, 0 one cell per thread
   size_t elem = 4;               // bytes per stored population
   void* f[2] = {nullptr, nullptr};
   int cur = 0;

@@ -444,7 +444,7 @@ __device__ __noinline__ void collide_face_pair(const DirPtrs<Q, T>& P, const Flu
 }
 
 // Every cell of a grid with even nx: 2 x-adjacent cells per thread,
-// 256-thread blocks (64 x 4 threads by default); IBL_PAIRS_MIN_BLOCKS blocks
+// blocks of up to 256 threads (the collide shape); IBL_PAIRS_MIN_BLOCKS blocks
 // per SM without the band lookup, three with it.
 #ifndef IBL_PAIRS_MIN_BLOCKS
 #define IBL_PAIRS_MIN_BLOCKS 4
@@ -468,6 +468,108 @@ __global__ void __launch_bounds__(256, IB ? 3 : IBL_PAIRS_MIN_BLOCKS) k_collide_
   const int cell = (z * p.ny + y) * p.nx + x;
 #pragma unroll
   for (int i = 0; i < Q; ++i) *reinterpret_cast<unsigned*>(P.d[i] + cell) = Pack16<T>::st(g[i]);
+}
+
+// ---------------------------------------------------------------- 16-bit storage: planes in flight
+// The two-cell kernel with each thread walking ZP planes in z: the 19 words
+// of plane z + 1 (and the row-end halves its edge lanes need) are loaded
+// before plane z collides, so a warp's loads for the next plane are in
+// flight while it computes; the shuffles run once a plane's words have
+// landed.
+// Same pulls, same packed collision, same stores: bitwise the populations
+// of the other kernels.
+#ifndef IBL_ZP
+#define IBL_ZP 8
+#endif
+constexpr int ZP = IBL_ZP;   // planes per thread
+
+template <int Q, class T>
+struct PairWords {
+  unsigned w[Q];   // the word (x, x + 1) of each direction's source row
+  T edge[Q];       // x - 1 (c_x = +1) or x + 2 (c_x = -1) where no neighbour lane holds it
+};
+
+template <int Q, class T>
+__device__ __forceinline__ void load_pair_words(const DirPtrs<Q, T>& P, int x, int y, int z,
+                                                const FluidParams<float>& p, PairWords<Q, T>& W) {
+  const int lane = threadIdx.x & 31;
+  int xm = x - 1, xp = x + 2;
+  if (xm < 0) xm += p.nx;
+  if (xp >= p.nx) xp -= p.nx;
+  const bool own_left = lane == 0 || x == 0;
+  const bool own_right = lane == 31 || x + 2 >= p.nx;
+  int ys[3] = {y - 1, y, y + 1};
+  if (ys[0] < 0) ys[0] += p.ny;
+  if (ys[2] >= p.ny) ys[2] -= p.ny;
+  int zs[3] = {z - 1, z, z + 1};
+  if (Lat<Q>::D == 3) {
+    if (zs[0] < 0) zs[0] += p.nz;
+    if (zs[2] >= p.nz) zs[2] -= p.nz;
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int dy = 1 - Lat<Q>::cy(i), dz = 1 - Lat<Q>::cz(i);
+    const int row = (zs[dz] * p.ny + ys[dy]) * p.nx;
+    W.w[i] = *reinterpret_cast<const unsigned*>(P.s[i] + row + x);
+    if (Lat<Q>::cx(i) > 0) W.edge[i] = own_left ? P.s[i][row + xm] : T();
+    else if (Lat<Q>::cx(i) < 0) W.edge[i] = own_right ? P.s[i][row + xp] : T();
+  }
+}
+
+// The two cells' values per direction from a plane's words (every lane of
+// the warp must call it: shuffles).
+template <int Q, class T>
+__device__ __forceinline__ void unpack_pair_words(const PairWords<Q, T>& W, int x, int nx, F2 g[Q]) {
+  const int lane = threadIdx.x & 31;
+  const bool own_left = lane == 0 || x == 0;
+  const bool own_right = lane == 31 || x + 2 >= nx;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    Pair16<T> w;
+    *reinterpret_cast<unsigned*>(&w) = W.w[i];
+    if (Lat<Q>::cx(i) == 0) {
+      g[i] = Pack16<T>::ld(w.a, w.b);
+    } else if (Lat<Q>::cx(i) > 0) {
+      Pair16<T> pw;
+      *reinterpret_cast<unsigned*>(&pw) = __shfl_up_sync(0xffffffffu, W.w[i], 1);
+      g[i] = Pack16<T>::ld(own_left ? W.edge[i] : pw.b, w.a);
+    } else {
+      Pair16<T> nw;
+      *reinterpret_cast<unsigned*>(&nw) = __shfl_down_sync(0xffffffffu, W.w[i], 1);
+      g[i] = Pack16<T>::ld(w.b, own_right ? W.edge[i] : nw.a);
+    }
+  }
+}
+
+#ifndef IBL_ZP_MIN_BLOCKS
+#define IBL_ZP_MIN_BLOCKS 2
+#endif
+template <int Q, class T, bool IB>
+__global__ void __launch_bounds__(256, IBL_ZP_MIN_BLOCKS) k_collide_pairs_zp(DirPtrs<Q, T> P, FluidParams<float> p) {
+  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z0 = blockIdx.z * ZP, z1 = min(z0 + ZP, p.nz);
+  // every lane loads and shuffles; lanes outside the grid read clamped rows
+  const bool inside = x < p.nx && y < p.ny;
+  const int xc = inside ? x : p.nx - 2, yc = inside ? y : p.ny - 1;
+  PairWords<Q, T> next;
+  load_pair_words<Q, T>(P, xc, yc, z0, p, next);
+  for (int z = z0; z < z1; ++z) {
+    // unpack this plane's words (landed during the previous plane's
+    // collision), then put the next plane's loads in flight
+    F2 g[Q];
+    unpack_pair_words<Q, T>(next, xc, p.nx, g);
+    if (z + 1 < z1) load_pair_words<Q, T>(P, xc, yc, z + 1, p, next);
+    if (!inside) continue;
+    if (on_special_face<float>(x, y, z, Lat<Q>::D, p) || on_special_face<float>(x + 1, y, z, Lat<Q>::D, p)) {
+      collide_face_pair<Q, T, IB>(P, p, x, y, z);
+      continue;
+    }
+    collide_pair<Q, IB>(g, p, x, y, z);
+    const int cell = (z * p.ny + y) * p.nx + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) *reinterpret_cast<unsigned*>(P.d[i] + cell) = Pack16<T>::st(g[i]);
+  }
 }
 
 // ---------------------------------------------------------------- 16-bit storage: staged planes
@@ -629,7 +731,7 @@ __global__ void __launch_bounds__(256, IB ? 3 : 4) k_collide_pairs_staged(DirPtr
   }
 }
 
-// Every cell, 64 x 4 cells per block; IB selects the band lookup.
+// Every cell, one per thread (blocks of the collide shape); IB selects the band lookup.
 template <int Q, class T, bool PULL, bool IB>
 __global__ void __launch_bounds__(256) k_collide(DirPtrs<Q, T> P, FluidParams<typename Store<T>::R> p) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -862,6 +964,15 @@ cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
         c->launches++;
         return cudaGetLastError();
       }
+    }
+    if (!c->poststream && c->nx % 2 == 0 && c->collide_pairs == 3) {
+      // 16-bit storage: two cells per thread, ZP planes per thread
+      const dim3 zb(b.x, b.y, 1);
+      const dim3 zg((c->nx / 2 + zb.x - 1) / zb.x, (c->ny + zb.y - 1) / zb.y, (c->nz + ZP - 1) / ZP);
+      if (with_ib) k_collide_pairs_zp<Q, T, true><<<zg, zb, 0, c->stream>>>(P, p);
+      else k_collide_pairs_zp<Q, T, false><<<zg, zb, 0, c->stream>>>(P, p);
+      c->launches++;
+      return cudaGetLastError();
     }
     if (!c->poststream && c->nx % 2 == 0 && c->collide_pairs >= 1) {
       // 16-bit storage: two x-adjacent cells per thread

@@ -39,7 +39,7 @@ using clock_type = std::chrono::steady_clock;
 struct Launch {
   int overlap, bx, by, pairs;
 };
-constexpr Launch CANDIDATES[] = {{1, 64, 4, 1}, {0, 64, 4, 1}, {0, 64, 2, 1}, {0, 128, 2, 1}, {0, 64, 4, 2}};
+constexpr Launch CANDIDATES[] = {{1, 64, 2, 3}, {0, 64, 2, 3}, {0, 128, 1, 3}, {0, 64, 4, 1}, {0, 64, 4, 2}};
 constexpr int NCAND = sizeof(CANDIDATES) / sizeof(CANDIDATES[0]);
 constexpr int TUNE_MIN_STEPS = 2;          // timed steps per candidate
 constexpr int MARKERS_PER_SOLVE_BLOCK = 64;
@@ -62,7 +62,7 @@ struct Run {
   bool tune_inflight = false;    // the tuning chunk is on the stream
   int tune_steps = 0;            // timed steps per candidate
   cudaEvent_t tev[2 * NCAND] = {};
-  Launch launch{-1, 64, 4, 1};
+  Launch launch{-1, 64, 2, 3};
   int solve_blocks = 0;
   bool tuned = false;
 };

@@ -370,9 +370,10 @@ class Context:
         """-1 automatic, 0 one collide kernel after the IB chain, 1 split step."""
         _check(self.h, _lib.ibl_set_overlap(self.h, int(mode)))
 
-    def ibl_set_collide_shape(self, bx=64, by=4, pairs=1):
-        """Thread block (bx x by) of the one-kernel collide; 16-bit storage: pairs 1 two cells per
-        thread, 2 the same on planes staged in shared memory, 0 one cell per thread."""
+    def ibl_set_collide_shape(self, bx=64, by=2, pairs=3):
+        """Thread block (bx x by) of the one-kernel collide; 16-bit storage: pairs 3 two cells and
+        8 z-planes per thread, 1 two cells per thread, 2 the same on planes staged in shared memory,
+        0 one cell per thread."""
         _check(self.h, _lib.ibl_set_collide_shape(self.h, int(bx), int(by), int(pairs)))
 
     def ibl_interpolate_points(self, X, U=None, rho=None):

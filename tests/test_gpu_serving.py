@@ -158,7 +158,7 @@ def test_tuning_is_per_request_and_cached_per_shape(ibl):
         assert r["status"] == ibl.IBL_OK and r["tuned"] and r["solve_blocks"] == want
     assert (ra["overlap"], ra["collide_shape"], ra["collide_pairs"]) == \
         (rb["overlap"], rb["collide_shape"], rb["collide_pairs"])
-    assert ra["overlap"] in (0, 1) and ra["collide_shape"] in [(64, 4), (64, 2), (128, 2)]
+    assert ra["overlap"] in (0, 1) and ra["collide_shape"] in [(64, 2), (128, 1), (64, 4)]
     assert _keys(ra) == _keys(rb)
     assert 0 < load["busy_s"] <= load["wall_s"]
     assert load["enqueue_s"] + load["build_s"] + load["retire_s"] <= load["busy_s"] * 1.01 + 1e-3
