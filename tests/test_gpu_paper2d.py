@@ -68,3 +68,39 @@ def test_paper_2d_case(ibl, oracle_runs, name, prec):
         hist = np.array(ctx.ibl_force_history(0, STEPS)), np.array(ctx.ibl_force_history(1, STEPS))
         scale = np.abs(hist[0][:, 0]).max()
         assert np.abs(hist[0][:, 0] - hist[1][:, 0]).max() < (1e-9 if prec == "fp64" else 1e-4) * scale
+
+
+PERIOD = 800
+
+
+@pytest.fixture(scope="module")
+def clap_fling_period_oracle():
+    sim = oracle_from_workload(_cases()["clap_fling"]("fp64"))
+    sim.step(PERIOD)
+    return sim
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_clap_fling_full_period(ibl, clap_fling_period_oracle, prec):
+    """One whole flapping period of the paper's 2D clap and fling (Sec. 3.3,
+    the span of its force histories): two claps and two flings, 800 steps.
+    C_L / C_T of both foils at every step and the final fields against the
+    oracle; the foils' lifts stay mirror images of each other."""
+    sim = clap_fling_period_oracle
+    cfg = _cases()["clap_fling"](prec)
+    ctx = ibl.from_workload(cfg)
+    ctx.ibl_step(PERIOD)
+    tol_f, tol_c = (TOL_FIELD_FP64, 1e-7) if prec == "fp64" else (TOL_FIELD_FP32, TOL_COEF_FP32)
+    eu, er = compare_fields(ctx, sim, ibl, tol_f)
+    hist = []
+    worst = 0.0
+    for b in range(2):
+        h = np.array(ctx.ibl_force_history(b, PERIOD))
+        ref = np.array(sim.history[b][-PERIOD:])
+        worst = max(worst, *coef_err(h[:, :2], ref[:, :2]))
+        hist.append(h)
+    print(f"clap_fling {prec} one period ({PERIOD} steps): u {eu:.2e} rho {er:.2e} coef {worst:.2e}; "
+          f"mean C_T {hist[0][:, 1].mean():.4f}, max C_L {hist[0][:, 0].max():.4f}")
+    assert worst < tol_c
+    scale = np.abs(hist[0][:, 0]).max()
+    assert np.abs(hist[0][:, 0] - hist[1][:, 0]).max() < (1e-9 if prec == "fp64" else 1e-4) * scale
