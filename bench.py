@@ -506,6 +506,16 @@ def run_ours(args):
                      "collide_ms_per_step": round(r1["collide_ms"], 5), "ib_chain_ms_per_step": round(r1["ib_ms"], 5),
                      "pcg_iterations_last_step": r1["iters"], "status": r1["status"]}
 
+    ib_sweep = None
+    if RANK == 0 and WORLD == 1 and args.workload in ("wings", "wings-large") and not args.no_secondary:
+        try:
+            ib_sweep = {"grid": "256^3 periodic D3Q19 FP32, Taylor-Green state",
+                        "rows": ib_sweep_rows(256, "fp32", [10000, 100000, 1000000], 10, 3),
+                        "note": "interpolate (Eq. 17) + spread (Eq. 15) of uniform random points, "
+                                "no solve; `bench.py --ib-sweep` for other sizes"}
+        except Exception as e:
+            ib_sweep = {"error": str(e)[:300]}
+
     serving = None
     if RANK == 0 and WORLD == 1 and args.serving_sample > 0 and args.workload in ("wings", "wings-large"):
         try:
@@ -538,7 +548,7 @@ def run_ours(args):
                                                   "solver_blocks": args.solver_blocks or (
                                                       "half the SMs" if half_sms else "all SMs")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["launches"],
-                "clocks": main["clocks"], "status": main["status"], "serving_sample": serving,
+                "clocks": main["clocks"], "status": main["status"], "serving_sample": serving, "ib_sweep": ib_sweep,
                 "host_enqueue_us_per_step": main["host_us"], "solver": solver,
                 "C_L_last_step_body0": main["C_L"]}
         if secondary:
@@ -678,21 +688,20 @@ def run_serving(n: int, mean_gap: float, run_steps: int, mix: str, budget_frac: 
                       ibl.STATUS_NAMES[r["status"]], r["steps_done"]] for rq, r in zip(reqs, res)]}
 
 
-def run_ib_sweep(args):
+def ib_sweep_rows(n: int, precision: str, markers, steps: int, warmup: int):
     """Markers/s of the IB stage without the solve: per step one interpolation
-    of rho, u* (Eq. 17) and one spreading (Eq. 15) of m random points on a
-    size^3 periodic D3Q19 state (a Taylor-Green field after one step), for
-    each m of --ib-markers.  Times are CUDA events around each ABI call on
-    the context's stream, so they include the call's launch latency and, for
-    the spreading, zeroing and converting the dense 3 x N FP64 output."""
+    of rho, u* (Eq. 17) and one spreading (Eq. 15) of m random points on an
+    n^3 periodic D3Q19 state (a Taylor-Green field after one step), for each
+    m of `markers`.  Times are CUDA events around each ABI call on the
+    context's stream, so they include the call's launch latency and, for the
+    spreading, zeroing and converting the dense 3 x N FP64 output."""
     import numpy as np
     import torch
     import workloads as W
     from paper_2102_01305_gb300 import ibl
     torch.cuda.set_device(0)
-    n = args.size
     N = n ** 3
-    cfg = {"lattice": 19, "tau": 0.6, "grid": W.grid(n, n, n, [W.PERIODIC] * 6, precision=args.precision),
+    cfg = {"lattice": 19, "tau": 0.6, "grid": W.grid(n, n, n, [W.PERIODIC] * 6, precision=precision),
            "bodies": [], "u_field": W.tgv3d_velocity(n, n, n, 0.05)}
     ctx = ibl.from_workload(cfg)
     del cfg["u_field"]
@@ -701,17 +710,15 @@ def run_ib_sweep(args):
     stream = torch.cuda.ExternalStream(ctx.ibl_stream())
     dev = dict(dtype=torch.float64, device="cuda")
     out = torch.empty((3, n, n, n), **dev)
-    elem = {"fp32": 4, "fp16dev": 2, "bf16dev": 2, "fp64": 8}[args.precision]
+    elem = {"fp32": 4, "fp16dev": 2, "bf16dev": 2, "fp64": 8}[precision]
     rows = []
-    clocks = ClockSampler()
-    clocks.start()
-    for m in [int(v) for v in args.ib_markers.split(",")]:
+    for m in markers:
         X, V = W.random_markers(m, n, 2.0, n - 2.0, 0.05)
         Xd, Vd, dsd = (torch.as_tensor(a, **dev) for a in (X, V, np.ones(m)))
         U = torch.empty((m, 3), **dev)
         rho = torch.empty(m, **dev)
         ti, ts = [], []
-        for k in range(max(args.warmup, 3) + args.steps):
+        for k in range(max(warmup, 3) + steps):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             ev[0].record(stream)
             ctx.ibl_interpolate_points(Xd, U, rho)
@@ -719,7 +726,7 @@ def run_ib_sweep(args):
             ctx.ibl_spread_points(Xd, Vd, dsd, out)
             ev[2].record(stream)
             ev[2].synchronize()
-            if k >= max(args.warmup, 3):
+            if k >= max(warmup, 3):
                 ti.append(ev[0].elapsed_time(ev[1]))
                 ts.append(ev[1].elapsed_time(ev[2]))
         t_i, t_s = statistics.median(ti), statistics.median(ts)
@@ -735,15 +742,24 @@ def run_ib_sweep(args):
                      "interpolate_GBs": round(b_i / (t_i * 1e-3) / 1e9, 1),
                      "spread_GBs": round(b_s / (t_s * 1e-3) / 1e9, 1)})
         del Xd, Vd, dsd, U, rho
-    clk = clocks.stop()
     ctx.close()
+    return rows
+
+
+def run_ib_sweep(args):
+    """The IB-stage sweep of ib_sweep_rows as its own JSON line."""
+    clocks = ClockSampler()
+    clocks.start()
+    rows = ib_sweep_rows(args.size, args.precision, [int(v) for v in args.ib_markers.split(",")],
+                         args.steps, args.warmup)
+    clk = clocks.stop()
     best = max(rows, key=lambda r: r["markers_per_s"])
     print(json.dumps({"metric": "IB-stage markers/s (interpolate + spread, no solve)",
                       "value": round(best["markers_per_s"], 1), "unit": "markers/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": max(args.warmup, 3), "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
                       "data": "synthetic (uniform random points in [2, n-2)^3, velocities in [-0.05, 0.05]^3)",
-                      "config": {"workload": f"IB sweep on a {n}^3 periodic D3Q19 grid",
+                      "config": {"workload": f"IB sweep on a {args.size}^3 periodic D3Q19 grid",
                                  "l2": "no flush: the populations (2 x 19 x N) exceed L2",
                                  "timing": "CUDA events around each ABI call (median)"},
                       "sweep": rows, "clocks": clk}), flush=True)
