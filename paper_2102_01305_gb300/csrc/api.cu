@@ -158,6 +158,9 @@ ibl_status ibl_destroy(ibl_ctx* c) {
   if (c->d_mass_ref) cudaFree(c->d_mass_ref);
   if (c->d_pt_perm) cudaFree(c->d_pt_perm);
   if (c->d_pt_bins) cudaFree(c->d_pt_bins);
+  if (c->d_pt_mom) cudaFree(c->d_pt_mom);
+  if (c->d_pt_sbase) cudaFree(c->d_pt_sbase);
+  if (c->d_pt_swts) cudaFree(c->d_pt_swts);
   for (auto& ev : c->stage_ev)
     if (ev) cudaEventDestroy(ev);
   for (auto& ev : c->prof_ev) cudaEventDestroy(ev);

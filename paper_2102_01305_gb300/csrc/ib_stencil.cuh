@@ -35,6 +35,13 @@ __device__ __forceinline__ bool stencil_axis(double x, int n, bool per, int& bas
   return finite && fl - 1.0 >= 0.0 && fl + 2.0 < (double)n;
 }
 
+// Fused multiply-add rounded once, with no room for the compiler to round
+// differently in different kernels (the point operators compute a node's
+// moments either inside the interpolation or once per cell beforehand, and
+// both must give the same bits).
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // drho and u* of one node from its post-streaming deviations, in the
 // storage's compute precision (Eq. 11 with the uniform body force G:
 // u* = (m + G/2) / rho, formed as m - m drho / rho).
@@ -55,10 +62,10 @@ __device__ __forceinline__ void node_moments(const T* __restrict__ src, int x, i
     if (Lat<Q>::cz(e)) m2 += R(Lat<Q>::cz(e)) * d;
   }
   const R qd = drho / (R(1) + drho);
-  R u0 = m0 + R(0.5) * p.G[0], u1 = m1 + R(0.5) * p.G[1], u2 = m2 + R(0.5) * p.G[2];
-  u0 -= u0 * qd;
-  u1 -= u1 * qd;
-  u2 -= u2 * qd;
+  R u0 = rn_fma(R(0.5), p.G[0], m0), u1 = rn_fma(R(0.5), p.G[1], m1), u2 = rn_fma(R(0.5), p.G[2], m2);
+  u0 = rn_fma(-u0, qd, u0);
+  u1 = rn_fma(-u1, qd, u1);
+  u2 = rn_fma(-u2, qd, u2);
   drho_out = drho;
   u[0] = u0;
   u[1] = u1;

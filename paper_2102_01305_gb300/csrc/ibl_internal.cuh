@@ -95,6 +95,11 @@ struct ibl_ctx {
   int* d_pt_perm = nullptr;      // point operators: sorted point order (pt_cap ints)
   int* d_pt_bins = nullptr;      // point operators: per-tile counters / offsets (n_tiles ints)
   size_t pt_cap = 0;
+  void* d_pt_mom = nullptr;       // point operators: drho and u* of every cell (4 N values)
+  void* d_pt_sbase = nullptr;     // point operators: stencil bases (3 per point)
+  void* d_pt_swts = nullptr;      // point operators: double-float stencil weights (12 per point)
+  size_t pt_st_cap = 0;
+  size_t pt_mom_bytes = 0;
   int sticky = 0;                // host copy of status bits seen so far
   std::string err;
 

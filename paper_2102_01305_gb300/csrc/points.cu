@@ -2,7 +2,9 @@
 // interpolation of Eq. 17 and the spreading of Eq. 15 on device arrays,
 // without the implicit solve.  They run the same per-node arithmetic as the
 // IB step (stencil_axis, node_moments, double-float weights and sums), one
-// warp per point.
+// warp per point, after a pre-pass that evaluates every point's stencil.
+#include <algorithm>
+
 #include "ib_stencil.cuh"
 
 namespace ibl {
@@ -21,32 +23,6 @@ struct PtGeo {
 
 __device__ __forceinline__ int wrap_once(int v, int n) { return v >= n ? v - n : v; }
 
-// Stencil of point l, computed once per warp: lane a < D evaluates axis a
-// (Eq. 14 in FP64), the bases and double-float weights are broadcast to all
-// lanes.  False (flag set) if it leaves a bounded axis, in which case the
-// caller touches no memory.  Every lane must call it.
-__device__ __forceinline__ bool point_stencil(const PtGeo& g, const double* X, int l, int b[3],
-                                              df w[3][4], int* flag) {
-  const int lane = threadIdx.x & 31;
-  int mb = 0;
-  df mw[4] = {df_make(1.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
-  bool ok = true;
-  if (lane < g.D) {
-    double wd[4];
-    ok = stencil_axis(X[3 * l + lane], g.n[lane], g.per[lane] != 0, mb, wd);
-    for (int k = 0; k < 4; ++k) mw[k] = df_from_double(wd[k]);
-  }
-  const bool all_ok = __all_sync(0xffffffffu, ok);
-  for (int a = 0; a < 3; ++a) {
-    b[a] = __shfl_sync(0xffffffffu, mb, a);
-    for (int k = 0; k < 4; ++k)
-      w[a][k] = df_make(__shfl_sync(0xffffffffu, mw[k].hi, a), __shfl_sync(0xffffffffu, mw[k].lo, a));
-    if (a >= g.D) b[a] = 0;
-  }
-  if (!all_ok && lane == 0) atomicOr(flag, PT_BAD_STENCIL);
-  return all_ok;
-}
-
 __device__ __forceinline__ long long stencil_node(const PtGeo& g, const int b[3], int k, int node[3]) {
   const int i = k & 3, j = (k >> 2) & 3, q = k >> 4;
   node[0] = b[0] + i;
@@ -57,17 +33,56 @@ __device__ __forceinline__ long long stencil_node(const PtGeo& g, const int b[3]
   return ((long long)node[2] * g.n[1] + node[1]) * g.n[0] + node[0];
 }
 
+// The stencils of all points, computed before the transfers with one
+// thread per (point, axis): the FP64 evaluation of Eq. 14 then fills every
+// lane of the FP64 pipe, where inside the transfers (one warp per point)
+// only D lanes of a warp would use it.  base[3 l + a] is the first node on
+// axis a (-1 if the stencil leaves a bounded axis or x is not finite),
+// wts[4 (3 l + a) + k] the double-float weights; axes a >= D get base 0
+// and weights (1, 0, 0, 0).
+__global__ void k_pt_stencils(int m, const double* __restrict__ X, PtGeo g, int* __restrict__ base,
+                              df* __restrict__ wts, int* flag) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3LL * m) return;
+  const int l = (int)(t / 3), a = (int)(t % 3);
+  int mb = 0;
+  df mw[4] = {df_make(1.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f), df_make(0.f, 0.f)};
+  bool ok = true;
+  if (a < g.D) {
+    double wd[4];
+    ok = stencil_axis(X[3 * l + a], g.n[a], g.per[a] != 0, mb, wd);
+    for (int k = 0; k < 4; ++k) mw[k] = df_from_double(wd[k]);
+  }
+  base[t] = ok ? mb : -1;
+  for (int k = 0; k < 4; ++k) wts[4 * t + k] = mw[k];
+  if (!ok) atomicOr(flag, PT_BAD_STENCIL);
+}
+
+// Point l's stencil from the pre-pass; false if an axis failed (the caller
+// then touches no memory).
+__device__ __forceinline__ bool load_stencil(const int* __restrict__ base, const df* __restrict__ wts, int l,
+                                             int b[3], df w[3][4]) {
+  bool ok = true;
+  for (int a = 0; a < 3; ++a) {
+    b[a] = base[3 * l + a];
+    ok = ok && b[a] >= 0;
+    for (int k = 0; k < 4; ++k) w[a][k] = wts[4 * (3 * l + a) + k];
+  }
+  return ok;
+}
+
 template <int Q, class T, bool PULL>
-__global__ void k_points_interpolate(int m, const double* __restrict__ X, const T* __restrict__ src,
-                                     FluidParams<typename Store<T>::R> p, PtGeo g, double* __restrict__ U,
-                                     double* __restrict__ rho_out, int* flag, const int* __restrict__ perm) {
+__global__ void k_points_interpolate(int m, const int* __restrict__ sbase, const df* __restrict__ swts,
+                                     const T* __restrict__ src, FluidParams<typename Store<T>::R> p, PtGeo g,
+                                     double* __restrict__ U, double* __restrict__ rho_out,
+                                     const int* __restrict__ perm) {
   const int wl = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (wl >= m) return;
   const int l = perm ? perm[wl] : wl;
   int b[3];
   df w[3][4];
-  if (!point_stencil(g, X, l, b, w, flag)) return;
+  if (!load_stencil(sbase, swts, l, b, w)) return;
   using R = typename Store<T>::R;
   const int nn = g.D == 3 ? 64 : 16;
   dfacc acc[4] = {acc_zero(), acc_zero(), acc_zero(), acc_zero()};
@@ -90,10 +105,68 @@ __global__ void k_points_interpolate(int m, const double* __restrict__ X, const 
   }
 }
 
+// Large point clouds cover most cells several times over, so the pulls of
+// k_points_interpolate repeat: the moments of every cell are formed once
+// (k_cell_moments, the same node_moments) into a context scratch array of
+// 4 N values (drho, u*), and the interpolation reads four values per node
+// (k_points_interpolate_cached, the same weights and accumulation order).
+// Both paths give bitwise the same results.
+template <int Q, class T, bool PULL>
+__global__ void k_cell_moments(const T* __restrict__ src, FluidParams<typename Store<T>::R> p,
+                               typename Store<T>::R* __restrict__ mom) {
+  using R = typename Store<T>::R;
+  const long long N = p.N;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += stride) {
+    const int x = (int)(cell % p.nx);
+    const long long yz = cell / p.nx;
+    const int y = (int)(yz % p.ny), z = (int)(yz / p.ny);
+    R drho, u[3];
+    node_moments<Q, T, PULL>(src, x, y, z, cell, p, drho, u);
+    mom[cell] = drho;
+    mom[N + cell] = u[0];
+    mom[2 * N + cell] = u[1];
+    mom[3 * N + cell] = u[2];
+  }
+}
+
+template <class R>
+__global__ void k_points_interpolate_cached(int m, const int* __restrict__ sbase, const df* __restrict__ swts,
+                                            const R* __restrict__ mom, long long N, PtGeo g,
+                                            double* __restrict__ U, double* __restrict__ rho_out,
+                                            const int* __restrict__ perm) {
+  const int wl = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (wl >= m) return;
+  const int l = perm ? perm[wl] : wl;
+  int b[3];
+  df w[3][4];
+  if (!load_stencil(sbase, swts, l, b, w)) return;
+  const int nn = g.D == 3 ? 64 : 16;
+  dfacc acc[4] = {acc_zero(), acc_zero(), acc_zero(), acc_zero()};
+  for (int k = lane; k < nn; k += 32) {
+    int node[3];
+    const long long cell = stencil_node(g, b, k, node);
+    df wt = df_mul(w[0][k & 3], w[1][(k >> 2) & 3]);
+    if (g.D == 3) wt = df_mul(wt, w[2][k >> 4]);
+    const R drho = mom[cell];
+    const R u[3] = {mom[N + cell], mom[2 * N + cell], mom[3 * N + cell]};
+    acc_fma(acc[0], wt, df_from_float(1.f));
+    acc_fma(acc[0], wt, to_df(drho));
+    for (int c = 0; c < 3; ++c) acc_fma(acc[1 + c], wt, to_df(u[c]));
+  }
+  df v[4];
+  for (int c = 0; c < 4; ++c) v[c] = df_warp_sum(acc_value(acc[c]));
+  if (lane == 0) {
+    if (rho_out) rho_out[l] = df_to_double(v[0]);
+    for (int a = 0; a < g.D; ++a) U[(long long)g.D * l + a] = df_to_double(v[1 + a]);
+  }
+}
+
 // Fixed-point scatter into the caller's output array reinterpreted as int64
 // (the same 8 bytes per entry): integer sums do not depend on atomic order.
-__global__ void k_points_spread(int m, const double* __restrict__ X, const double* __restrict__ V,
-                                const double* __restrict__ ds, PtGeo g, long long N,
+__global__ void k_points_spread(int m, const int* __restrict__ sbase, const df* __restrict__ swts,
+                                const double* __restrict__ V, const double* __restrict__ ds, PtGeo g, long long N,
                                 unsigned long long* __restrict__ acc, int* flag, const int* __restrict__ perm) {
   const int wl = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -101,7 +174,7 @@ __global__ void k_points_spread(int m, const double* __restrict__ X, const doubl
   const int l = perm ? perm[wl] : wl;
   int b[3];
   df w[3][4];
-  if (!point_stencil(g, X, l, b, w, flag)) return;
+  if (!load_stencil(sbase, swts, l, b, w)) return;
   // V_l ds_l per component, formed by lane c and broadcast
   df vc = df_make(0.f, 0.f);
   if (lane < g.D) vc = df_from_double(V[(long long)g.D * l + lane] * ds[l]);
@@ -234,10 +307,34 @@ const int* point_order(ibl_ctx* c, int m, const double* X, cudaError_t& e) {
   return e == cudaSuccess ? c->d_pt_perm : nullptr;
 }
 
+// Stencils of the m points in the context's scratch (grown on demand).
+bool point_stencils(ibl_ctx* c, int m, const double* X, const int*& base, const df*& wts, cudaError_t& e) {
+  e = cudaSuccess;
+  if (c->pt_st_cap < (size_t)m) {
+    if (c->d_pt_sbase) cudaFree(c->d_pt_sbase);
+    if (c->d_pt_swts) cudaFree(c->d_pt_swts);
+    c->d_pt_sbase = nullptr;
+    c->d_pt_swts = nullptr;
+    c->pt_st_cap = 0;
+    e = cudaMalloc(&c->d_pt_sbase, sizeof(int) * 3 * (size_t)m);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_pt_swts, sizeof(df) * 12 * (size_t)m);
+    if (e != cudaSuccess) return false;
+    c->pt_st_cap = (size_t)m;
+  }
+  int* b = static_cast<int*>(c->d_pt_sbase);
+  df* w = static_cast<df*>(c->d_pt_swts);
+  k_pt_stencils<<<(unsigned)((3LL * m + 255) / 256), 256, 0, c->stream>>>(m, X, pt_geo(c), b, w, c->d_status + 1);
+  c->launches++;
+  e = cudaGetLastError();
+  base = b;
+  wts = w;
+  return e == cudaSuccess;
+}
+
 unsigned point_blocks(int m) { return (unsigned)(((long long)m * 32 + 255) / 256); }
 
 template <int Q, class T>
-void launch_interpolate(ibl_ctx* c, int m, const double* X, double* U, double* rho, int* flag,
+void launch_interpolate(ibl_ctx* c, int m, const int* sbase, const df* swts, double* U, double* rho,
                         const int* perm) {
   using R = typename Store<T>::R;
   FluidParams<R> p{};
@@ -255,20 +352,42 @@ void launch_interpolate(ibl_ctx* c, int m, const double* X, double* U, double* r
   p.status = c->d_status;
   const T* src = (const T*)c->f[c->cur];
   const PtGeo g = pt_geo(c);
+  const long long nn = c->D == 3 ? 64 : 16;
+  if ((long long)m * nn >= c->N) {
+    // as many stencil nodes as cells or more: moments once per cell first
+    const size_t bytes = 4 * sizeof(R) * (size_t)c->N;
+    if (c->pt_mom_bytes < bytes) {
+      if (c->d_pt_mom) cudaFree(c->d_pt_mom);
+      c->d_pt_mom = nullptr;
+      c->pt_mom_bytes = 0;
+      if (cudaMalloc(&c->d_pt_mom, bytes) != cudaSuccess) return;   // reported by the caller's error check
+      c->pt_mom_bytes = bytes;
+    }
+    R* mom = static_cast<R*>(c->d_pt_mom);
+    const unsigned cb = (unsigned)std::min<long long>((c->N + 255) / 256, 152LL * 16);
+    if (c->poststream) k_cell_moments<Q, T, false><<<cb, 256, 0, c->stream>>>(src, p, mom);
+    else k_cell_moments<Q, T, true><<<cb, 256, 0, c->stream>>>(src, p, mom);
+    k_points_interpolate_cached<R><<<point_blocks(m), 256, 0, c->stream>>>(m, sbase, swts, mom, c->N, g, U, rho,
+                                                                           perm);
+    c->launches++;
+    return;
+  }
   if (c->poststream)
-    k_points_interpolate<Q, T, false><<<point_blocks(m), 256, 0, c->stream>>>(m, X, src, p, g, U, rho, flag, perm);
+    k_points_interpolate<Q, T, false><<<point_blocks(m), 256, 0, c->stream>>>(m, sbase, swts, src, p, g, U, rho,
+                                                                               perm);
   else
-    k_points_interpolate<Q, T, true><<<point_blocks(m), 256, 0, c->stream>>>(m, X, src, p, g, U, rho, flag, perm);
+    k_points_interpolate<Q, T, true><<<point_blocks(m), 256, 0, c->stream>>>(m, sbase, swts, src, p, g, U, rho,
+                                                                              perm);
 }
 
 template <int Q>
-void launch_interpolate_q(ibl_ctx* c, int m, const double* X, double* U, double* rho, int* flag,
+void launch_interpolate_q(ibl_ctx* c, int m, const int* sbase, const df* swts, double* U, double* rho,
                           const int* perm) {
   switch (c->prec) {
-    case IBL_FP64: launch_interpolate<Q, double>(c, m, X, U, rho, flag, perm); break;
-    case IBL_FP32: launch_interpolate<Q, float>(c, m, X, U, rho, flag, perm); break;
-    case IBL_FP16DEV: launch_interpolate<Q, __half>(c, m, X, U, rho, flag, perm); break;
-    default: launch_interpolate<Q, __nv_bfloat16>(c, m, X, U, rho, flag, perm); break;
+    case IBL_FP64: launch_interpolate<Q, double>(c, m, sbase, swts, U, rho, perm); break;
+    case IBL_FP32: launch_interpolate<Q, float>(c, m, sbase, swts, U, rho, perm); break;
+    case IBL_FP16DEV: launch_interpolate<Q, __half>(c, m, sbase, swts, U, rho, perm); break;
+    default: launch_interpolate<Q, __nv_bfloat16>(c, m, sbase, swts, U, rho, perm); break;
   }
 }
 
@@ -309,8 +428,11 @@ ibl_status ibl_interpolate_points(ibl_ctx* c, int32_t m, const double* d_X, doub
   cudaError_t pe;
   const int* perm = point_order(c, m, d_X, pe);
   if (pe != cudaSuccess) return cuda_check(c, pe, "ibl_interpolate_points: point order");
-  if (c->Q == 9) launch_interpolate_q<9>(c, m, d_X, d_U, d_rho, c->d_status + 1, perm);
-  else launch_interpolate_q<19>(c, m, d_X, d_U, d_rho, c->d_status + 1, perm);
+  const int* sbase = nullptr;
+  const df* swts = nullptr;
+  if (!point_stencils(c, m, d_X, sbase, swts, pe)) return cuda_check(c, pe, "ibl_interpolate_points: stencils");
+  if (c->Q == 9) launch_interpolate_q<9>(c, m, sbase, swts, d_U, d_rho, perm);
+  else launch_interpolate_q<19>(c, m, sbase, swts, d_U, d_rho, perm);
   c->launches++;
   const ibl_status r = finish(c, cudaGetLastError(), "ibl_interpolate_points");
   return r != IBL_OK ? r : s;
@@ -328,9 +450,12 @@ ibl_status ibl_spread_points(ibl_ctx* c, int32_t m, const double* d_X, const dou
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(d_out);
   cudaError_t e = cudaMemsetAsync(d_out, 0, sizeof(double) * tot, c->stream);
   const int* perm = nullptr;
+  const int* sbase = nullptr;
+  const df* swts = nullptr;
   if (e == cudaSuccess && m > 0) perm = point_order(c, m, d_X, e);
+  if (e == cudaSuccess && m > 0) point_stencils(c, m, d_X, sbase, swts, e);
   if (e == cudaSuccess && m > 0) {
-    k_points_spread<<<point_blocks(m), 256, 0, c->stream>>>(m, d_X, d_V, d_ds, pt_geo(c), c->N, acc,
+    k_points_spread<<<point_blocks(m), 256, 0, c->stream>>>(m, sbase, swts, d_V, d_ds, pt_geo(c), c->N, acc,
                                                             c->d_status + 1, perm);
     c->launches++;
     e = cudaGetLastError();

@@ -94,6 +94,27 @@ def test_interpolate_points_matches_oracle(ibl, q, prec, shape, bc, steps):
     assert np.abs(rho.cpu().numpy() - r_o).max() < tol
 
 
+@pytest.mark.parametrize("q,prec,shape,bc", CASES)
+@pytest.mark.parametrize("steps", [0, 2])
+def test_interpolate_cached_moments_bitwise(ibl, q, prec, shape, bc, steps):
+    """A cloud with as many stencil nodes as cells takes the moments-first
+    path (every cell's rho, u* formed once); small clouds pull at every
+    node.  Both give bitwise the same values: 300 points at once against
+    the same points 20 at a time."""
+    ctx, _ = _pair(ibl, q, prec, shape, bc, steps)
+    periodic = [bc[2 * a] == W.PERIODIC for a in range(3)]
+    if bc[0] == W.VEL_INLET:
+        periodic[0] = False
+    X = _cloud(300, shape, periodic, seed=21)
+    nodes = 64 if q == 19 else 16
+    n_cells = shape[0] * shape[1] * shape[2]
+    assert 300 * nodes >= n_cells > 20 * nodes
+    U, rho = ctx.ibl_interpolate_points(_dev(X))
+    parts = [ctx.ibl_interpolate_points(_dev(X[k:k + 20])) for k in range(0, 300, 20)]
+    assert torch.equal(U, torch.cat([p[0] for p in parts]))
+    assert torch.equal(rho, torch.cat([p[1] for p in parts]))
+
+
 @pytest.mark.parametrize("q,prec,shape,bc", CASES[:3])
 def test_spread_points_matches_oracle(ibl, q, prec, shape, bc):
     ctx, sim = _pair(ibl, q, prec, shape, bc, 0)
