@@ -73,8 +73,8 @@ def parse():
     ap.add_argument("--serving-sample", type=int, default=12,
                     help="requests of the short serving sample in the default line (0: none)")
     ap.add_argument("--e2e-steps", type=int, default=300)
-    ap.add_argument("--overlap", type=int, default=-1, choices=[-1, 0, 1],
-                    help="collide scheduling: -1 automatic, 0 one kernel after the IB chain, 1 split")
+    ap.add_argument("--overlap", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="collide scheduling: -1 automatic, 0 one kernel after the IB chain, 1 split, 2 serial split")
     ap.add_argument("--solver-blocks", type=int, default=0, help="blocks of the implicit solve (0: default)")
     ap.add_argument("--collide-shape", default=None,
                     help="BXxBYxPAIRS: thread block and two-cells-per-thread flag of the one-kernel collide")
@@ -467,12 +467,17 @@ def run_ours(args):
     achieved = alg_bytes / (main["collide_ms"] * 1e-3) / 1e9
     split = bool(cfg["bodies"]) and (args.overlap == 1 or (args.overlap == -1 and cells >= (1 << 20)
                                                            and nmark <= 8192))
+    serial = bool(cfg["bodies"]) and not split and args.overlap == 2
     half_sms = args.overlap == 1 or nmark <= 8192     # the solve's default share of the SMs
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     if split:
         pcg_blocks = min(args.solver_blocks or (sms // 2 if half_sms else sms), sms)
         kernel = (f"k_collide_bulk + k_collide_band (split step: the bulk collide runs on the "
                   f"{sms - pcg_blocks} of {sms} SMs the solve leaves free, concurrently with the IB chain)")
+        rec_key = "split"
+    elif serial:
+        kernel = ("k_collide_bulk + k_collide_band (serial split: after the IB chain, the cells outside "
+                  "the band on every SM without the band lookup, then the band tiles)")
         rec_key = "split"
     else:
         kernel = "k_collide (collide + stream + faces + IB force, D3Q19, all SMs, after the IB chain)"
@@ -543,8 +548,9 @@ def run_ours(args):
                 "data": "synthetic (seeded workload generator; no dataset)",
                 "config": describe(cfg, steps) | {"parallelism": f"replicas x{WORLD}",
                                                   "collide_schedule": {-1: "automatic", 0: "single kernel",
-                                                                       1: "split"}[args.overlap] +
-                                                  (" (split)" if split else " (single kernel)"),
+                                                                       1: "split", 2: "serial split"}[args.overlap] +
+                                                  (" (split)" if split else (" (serial split)" if serial
+                                                                             else " (single kernel)")),
                                                   "solver_blocks": args.solver_blocks or (
                                                       "half the SMs" if half_sms else "all SMs")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": main["launches"],

@@ -317,9 +317,12 @@ ibl_status ibl_solver_preconditioner(ibl_ctx* ctx, int32_t kind, int32_t residen
 /* How a step with markers schedules its collision: 0 = one kernel over all
  * cells after the IB chain; 1 = split: the cells outside the IB band collide
  * on a second stream while the IB chain (interpolation, solve, spreading)
- * runs, and the band tiles collide after the spreading; -1 (default) =
- * split on grids of at least 2^20 cells with at most 8192 markers.  Both give bitwise the same
- * populations and forces (every cell runs the same arithmetic). */
+ * runs, and the band tiles collide after the spreading; 2 = serial split:
+ * after the IB chain, the cells outside the band collide in a kernel without
+ * the band lookup on every SM, then the band tiles; -1 (default) = split on
+ * grids of at least 2^20 cells with at most 8192 markers, else 0.  All give
+ * bitwise the same populations and forces (every cell runs the same
+ * arithmetic). */
 ibl_status ibl_set_overlap(ibl_ctx* ctx, int32_t mode);
 
 /* Launch shape of the one-kernel collide (the kernel of steps without the

@@ -224,7 +224,7 @@ ibl_status sync_and_collect(ibl_ctx* c);   // drain the stream, fold device stat
 cudaError_t launch_init_eq(ibl_ctx* c, const double* d_rho, const double* d_u);
 cudaError_t launch_set_pop(ibl_ctx* c, const double* d_f);
 cudaError_t launch_collide(ibl_ctx* c, bool with_ib);
-cudaError_t launch_collide_bulk(ibl_ctx* c, int blocks);   // on stream_bulk
+cudaError_t launch_collide_bulk(ibl_ctx* c, int blocks, cudaStream_t st);
 cudaError_t launch_collide_band(ibl_ctx* c, int blocks);
 cudaError_t launch_fields(ibl_ctx* c, double* d_rho, double* d_u, double* d_pop);
 cudaError_t launch_mass(ibl_ctx* c, double* d_partials, int nparts, double* d_out);

@@ -995,12 +995,12 @@ cudaError_t collide_q(ibl_ctx* c, bool with_ib) {
 }
 
 template <int Q, class T>
-cudaError_t collide_bulk_q(ibl_ctx* c, int blocks) {
+cudaError_t collide_bulk_q(ibl_ctx* c, int blocks, cudaStream_t st) {
   using R = typename Store<T>::R;
   auto p = make_params<R>(c, true);
   const DirPtrs<Q, T> P = dir_ptrs<Q, T>(c);
-  if (c->poststream) k_collide_bulk<Q, T, false><<<blocks, BULK_THREADS, 0, c->stream_bulk>>>(P, p);
-  else k_collide_bulk<Q, T, true><<<blocks, BULK_THREADS, 0, c->stream_bulk>>>(P, p);
+  if (c->poststream) k_collide_bulk<Q, T, false><<<blocks, BULK_THREADS, 0, st>>>(P, p);
+  else k_collide_bulk<Q, T, true><<<blocks, BULK_THREADS, 0, st>>>(P, p);
   c->launches++;
   return cudaGetLastError();
 }
@@ -1083,7 +1083,7 @@ cudaError_t setpop_q(ibl_ctx* c, const double* d_f) {
   } while (0)
 
 cudaError_t launch_collide(ibl_ctx* c, bool with_ib) { IBL_DISPATCH(collide_q, with_ib); }
-cudaError_t launch_collide_bulk(ibl_ctx* c, int blocks) { IBL_DISPATCH(collide_bulk_q, blocks); }
+cudaError_t launch_collide_bulk(ibl_ctx* c, int blocks, cudaStream_t st) { IBL_DISPATCH(collide_bulk_q, blocks, st); }
 cudaError_t launch_collide_band(ibl_ctx* c, int blocks) { IBL_DISPATCH(collide_band_q, blocks); }
 cudaError_t launch_fields(ibl_ctx* c, double* d_rho, double* d_u, double* d_pop) {
   IBL_DISPATCH(fields_q, d_rho, d_u, d_pop);

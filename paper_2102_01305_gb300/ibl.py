@@ -367,7 +367,7 @@ class Context:
         return dict(zip(PHASES, ms.tolist()))
 
     def ibl_set_overlap(self, mode):
-        """-1 automatic, 0 one collide kernel after the IB chain, 1 split step."""
+        """-1 automatic, 0 one collide kernel after the IB chain, 1 split step, 2 serial split."""
         _check(self.h, _lib.ibl_set_overlap(self.h, int(mode)))
 
     def ibl_set_collide_shape(self, bx=64, by=2, pairs=3):

@@ -181,8 +181,9 @@ def _run_mode(ibl, cfg, mode, steps):
 @pytest.mark.parametrize("case", ["wings_fp32", "wings_fp16dev", "wings_bf16dev", "cylinder_fp64"])
 def test_split_step_is_bitwise_identical(ibl, case):
     """The split step (cells outside the IB band collide on a second stream
-    while the IB chain runs; band tiles collide after the spreading) gives
-    bitwise the populations and forces of one collide kernel after the chain.
+    while the IB chain runs; band tiles collide after the spreading) and the
+    serial split (the same two kernels after the chain) give bitwise the
+    populations and forces of one collide kernel after the chain.
     With 16-bit storage and even nx the single kernel takes two cells per
     thread, so this also pins it to the one-cell kernels of the split step."""
     if case.startswith("wings_"):
@@ -191,27 +192,31 @@ def test_split_step_is_bitwise_identical(ibl, case):
     else:
         cfg, steps = W.cylinder_channel(), 200
     a = _run_mode(ibl, cfg, 0, steps)
-    b = _run_mode(ibl, cfg, 1, steps)
-    for x, y in zip(a, b):
-        assert np.array_equal(x, y)
+    for mode in (1, 2):
+        b = _run_mode(ibl, cfg, mode, steps)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
 
 
 def test_split_step_full_size_bitwise(ibl):
-    """The bench's wing box (split by default at this size) against the
-    single-kernel step, 30 steps including the first (no pull) step."""
+    """The bench's wing box (split by default at this size), and the serial
+    split, against the single-kernel step, 30 steps including the first (no
+    pull) step."""
     import bench
     cfg = bench.workload("fp32", 1.0, "wings", 256)
     steps = 30
     ctx0 = ibl.from_workload(cfg)
     ctx0.ibl_set_overlap(0)
     ctx0.ibl_step(steps)
-    ctx1 = ibl.from_workload(cfg)          # automatic: split at 7.9M cells
-    ctx1.ibl_step(steps)
-    for b in range(2):
-        assert np.array_equal(ctx0.ibl_force_history(b, steps), ctx1.ibl_force_history(b, steps))
     u0 = ctx0.ibl_get_field(ibl.IBL_FIELD_U)
-    u1 = ctx1.ibl_get_field(ibl.IBL_FIELD_U)
-    assert np.array_equal(u0, u1)
+    for mode in (-1, 2):                   # automatic: split at 7.9M cells; serial split
+        ctx1 = ibl.from_workload(cfg)
+        ctx1.ibl_set_overlap(mode)
+        ctx1.ibl_step(steps)
+        for b in range(2):
+            assert np.array_equal(ctx0.ibl_force_history(b, steps), ctx1.ibl_force_history(b, steps))
+        assert np.array_equal(u0, ctx1.ibl_get_field(ibl.IBL_FIELD_U))
+        ctx1.close()
 
 
 def test_early_rebuilds_reproducible(ibl):
