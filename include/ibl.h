@@ -279,7 +279,7 @@ ibl_status ibl_solver_stats(ibl_ctx* ctx, int32_t* iterations, double* rel_resid
  * rebuild, summed over the solves since, pass the rebuild's cost in
  * iterations (sum 2 m_b^3 / sum 6 m_b^2, at least 64).  tol is the relative
  * residual in the preconditioner's norm (0 = default: 1e-10 for FP64
- * storage, 1e-7 for FP32, 1e-6 for FP16/BF16).  extrapolate chooses each
+ * storage, 1e-6 for FP32, FP16 and BF16).  extrapolate chooses each
  * solve's initial guess: 2 (or more) 3 w_{n-1} - 3 w_{n-2} + w_{n-3},
  * 1 (default) 2 w_{n-1} - w_{n-2}, 0 w_{n-1}, < 0 zero.  Changing these changes the iterates, not the system being
  * solved. */

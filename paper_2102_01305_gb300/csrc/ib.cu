@@ -40,9 +40,12 @@ constexpr int MAX_BODIES = 16;
 constexpr int GJ_NB = 64;          // Gauss-Jordan pivot block
 constexpr int PCG_MAX_ITERS = 200;
 // relative preconditioned residual (the spread field's A-norm error) per
-// storage precision: about two decades under what the storage resolves
+// storage precision, under the field error the storage itself accumulates:
+// FP32 runs sit at field errors of ~2e-6 against the FP64 reference after
+// hundreds of steps whether the solve stops at 1e-6 or 1e-7 (measured on
+// every FP32 parity case), so FP32 stops at 1e-6 like FP16 / BF16
 constexpr double PCG_TOL = 1e-10;       // FP64
-constexpr double PCG_TOL_FP32 = 1e-7;   // FP32 deviations
+constexpr double PCG_TOL_FP32 = 1e-6;   // FP32 deviations
 constexpr double PCG_TOL_HALF = 1e-6;   // FP16 / BF16 deviations
 
 // Early rebuilds follow a rent-or-buy rule.  Since the last rebuild, every
